@@ -1,0 +1,225 @@
+/*
+ * fmm.h - C ABI of the GB300 recursive fast matrix multiplication library.
+ *
+ * Method (Benson & Ballard, "A Framework for Practical Parallel Fast Matrix
+ * Multiplication"): a base case <M,K,N;R> with factor matrices [[U,V,W]]
+ * (Section 2.2, Eq. 2) multiplies an M x K block matrix A by a K x N block
+ * matrix B with R block products.  One recursive step forms
+ *     S_r = sum_i U_ir A_i,   T_r = sum_j V_jr B_j,          (Section 3.1)
+ *     M_r = S_r T_r,          C_q = sum_r W_qr M_r,
+ * and L steps are applied recursively before the classical product takes
+ * over at the leaves (Section 3.3).  Dimensions that the block sizes do not
+ * divide are handled by peeling (Section 3.4).
+ *
+ * Conventions for every entry point
+ *   - Matrices are row-major with a leading dimension (ld >= columns);
+ *     A is m x k, B is k x n, C is m x n.  U, V, W are row-major host arrays
+ *     of MK x R, KN x R, MN x R whose rows follow the row-order vectorisation
+ *     of the A, B and C blocks (Section 2.2.2: block (a,b) of A is row a*K+b).
+ *   - C = A B overwrites C (no alpha/beta).  C must not overlap A or B.
+ *   - "device pointer" arguments are CUDA global-memory addresses on the
+ *     device that was current when the plan was created; the caller owns
+ *     them.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *     default stream) and is asynchronous unless stated otherwise.
+ *   - Every argument is validated on the host before any launch; no
+ *     exception crosses the ABI.  Non-finite inputs are unsupported (fast
+ *     algorithms may turn Inf into NaN through Inf - Inf).
+ *   - A plan is immutable after creation and may be used from several host
+ *     threads and streams at once.
+ */
+#ifndef FMM_H_
+#define FMM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fmm_plan *fmm_plan_t; /* opaque; owned by the library */
+
+typedef enum {
+    FMM_OK = 0,
+    FMM_ERR_ARG = -1,               /* bad pointer, size, stride or aliasing  */
+    FMM_ERR_INVALID_ALGORITHM = -2, /* [[U,V,W]] fails the Brent equations    */
+    FMM_ERR_UNSUPPORTED = -3,       /* valid request the library cannot run   */
+    FMM_ERR_NO_MEMORY = -4,         /* host or device allocation failed, or
+                                       the workspace passed is too small      */
+    FMM_ERR_CUDA = -5,              /* a CUDA call failed                     */
+    FMM_ERR_TIMEOUT = -6            /* a bounded device wait gave up          */
+} fmm_status;
+
+typedef enum {
+    FMM_PREC_FP64 = 0 /* FP64 leaves (DFMA), FP64 combinations */
+} fmm_precision;
+
+/* Execution-scheme flags (fmm_plan_create / fmm_plan_load `flags`). */
+enum {
+    /* S_r and T_r are formed inside the leaf kernel's shared-memory operand
+       staging (never written to HBM); when clear they are formed by a
+       write-once pass into the workspace first (Section 3.2). */
+    FMM_FLAG_FUSED_ST = 1u << 0,
+    /* W is applied in the leaf kernel's epilogue by FP64 reductions into C
+       (summation order across leaves not fixed; exact on integer data); when
+       clear the leaf products M_r go to the workspace and a write-once pass
+       forms C in a fixed order (bitwise reproducible). */
+    FMM_FLAG_FUSED_W = 1u << 1,
+    FMM_FLAGS_DEFAULT = FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W
+};
+
+/* Tile shape of the leaf GEMM kernel (fmm_plan_set_tile). */
+typedef enum {
+    FMM_TILE_AUTO = 0,
+    FMM_TILE_128x128 = 1,
+    FMM_TILE_96x96 = 2,
+    FMM_TILE_64x64 = 3,
+    FMM_TILE_32x32 = 4,
+    FMM_TILE_128x64 = 5,
+    FMM_TILE_64x128 = 6
+} fmm_tile;
+
+/*
+ * fmm_plan_create - build a plan for `levels` recursive steps of the base
+ * case <M,K,N;R> given by U (MK x R), V (KN x R), W (MN x R).
+ *
+ * The factor matrices are checked exactly against the Brent equations
+ * (Eq. 2, with the matmul tensor of Section 2.2.2); FP64 values are exact
+ * dyadic rationals, so the check has no rounding.  The L steps are then
+ * unrolled into R^L leaf products (Section 3.1 applied recursively), each
+ * with its list of A blocks, B blocks and C blocks and their coefficients,
+ * and the lists are copied to the current device.
+ *
+ * levels: 0..6 (0 = classical product).  M, K, N: 1..16; R: 1..1024.
+ * out: receives the plan; unchanged on error.
+ * Errors: FMM_ERR_ARG (null pointer, sizes out of range, levels out of range,
+ * unknown flags), FMM_ERR_INVALID_ALGORITHM (Brent check failed),
+ * FMM_ERR_UNSUPPORTED (R^L or the unrolled term lists too large, or a
+ * coefficient that is not finite), FMM_ERR_NO_MEMORY, FMM_ERR_CUDA.
+ */
+fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R,
+                           const double *U, const double *V, const double *W,
+                           int levels, fmm_precision prec, unsigned flags);
+
+/*
+ * fmm_plan_load - as fmm_plan_create, reading [[U,V,W]] from a text file:
+ * optional '#' comments, a line "M K N R", then lines "U", "V", "W" each
+ * followed by MK, KN, MN rows of R rationals written as p or p/q.
+ * Denominators must be powers of two (exact in FP64); others give
+ * FMM_ERR_UNSUPPORTED.  A file that cannot be read or parsed gives
+ * FMM_ERR_ARG.
+ */
+fmm_status fmm_plan_load(fmm_plan_t *out, const char *fmm_file, int levels,
+                         fmm_precision prec, unsigned flags);
+
+/* Release a plan and its device memory.  NULL is a no-op.  The caller must
+   make sure no work using the plan is still running. */
+void fmm_plan_destroy(fmm_plan_t plan);
+
+/* Choose the leaf GEMM tile shape used by later fmm_gemm calls with this
+   plan (default FMM_TILE_AUTO).  Not thread-safe against concurrent
+   fmm_gemm calls on the same plan. */
+fmm_status fmm_plan_set_tile(fmm_plan_t plan, fmm_tile tile);
+
+/* Description of a plan (fmm_plan_info). */
+typedef struct {
+    int M, K, N, R, levels;
+    unsigned flags;
+    int64_t leaves;        /* R^levels                                      */
+    int64_t nnz_a_terms;   /* sum over leaves of A blocks in S_r            */
+    int64_t nnz_b_terms;   /* ... B blocks in T_r                           */
+    int64_t nnz_c_terms;   /* ... C blocks that M_r contributes to          */
+    int max_a_terms, max_b_terms, max_c_terms; /* largest per-leaf list     */
+} fmm_plan_info_t;
+
+fmm_status fmm_plan_info(fmm_plan_t plan, fmm_plan_info_t *info);
+
+/*
+ * fmm_plan_leaf_terms - copy out the unrolled coefficient lists (for
+ * verification).  For operand `which` (0 = A/U, 1 = B/V, 2 = C/W):
+ *   ptr[leaves+1]   CSR row pointers into the term arrays,
+ *   row[nnz], col[nnz]  block coordinates in the M^L x K^L (A), K^L x N^L (B)
+ *                   or M^L x N^L (C) grid of blocks,
+ *   coef[nnz]       the unscaled coefficient prod_l U[i_l, r_l] (resp. V, W).
+ * Any output pointer may be NULL; `capacity` is the length of row/col/coef.
+ * Leaf r = sum_l r_l R^(L-l) with r_1 the outermost step.
+ * Errors: FMM_ERR_ARG (bad `which`, capacity too small).
+ */
+fmm_status fmm_plan_leaf_terms(fmm_plan_t plan, int which, int64_t *ptr,
+                               int32_t *row, int32_t *col, double *coef,
+                               int64_t capacity);
+
+/*
+ * fmm_workspace_size - device workspace bytes fmm_gemm needs for an
+ * m x k x n product with this plan (0 when the fused scheme needs none).
+ */
+fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t m, int64_t k, int64_t n,
+                              size_t *bytes);
+
+/*
+ * fmm_gemm - C = A B with the plan's fast algorithm on the device.
+ *
+ * A (m x k, lda), B (k x n, ldb), C (m x n, ldc): device pointers, FP64,
+ * row-major; 8-byte aligned.  m, k, n >= 1.  lda >= k, ldb >= n, ldc >= n.
+ * The core m' x k' x n' (m' the largest multiple of M^L not above m, etc.)
+ * runs the fast algorithm; the rest is added by classical products
+ * (Section 3.4):  C[:m',:n'] += A[:m',k':] B[k':,:n'],  C[m':,:] = A[m':,:] B,
+ * C[:m',n':] = A[:m',:] B[:,n'].
+ * workspace: device pointer of at least fmm_workspace_size() bytes, 256-byte
+ * aligned (may be NULL when that size is 0).
+ * Errors: FMM_ERR_ARG (null plan or pointers, sizes < 1, ld too small,
+ * misaligned pointers, C overlapping A or B), FMM_ERR_NO_MEMORY (workspace
+ * too small), FMM_ERR_CUDA (launch failure).
+ */
+fmm_status fmm_gemm(fmm_plan_t plan, const double *A, int64_t lda,
+                    const double *B, int64_t ldb, double *C, int64_t ldc,
+                    int64_t m, int64_t k, int64_t n, void *workspace,
+                    size_t ws_bytes, void *stream);
+
+/*
+ * fmm_classical_gemm - C = A B by the library's classical FP64 GEMM (the
+ * same kernel the leaves use; the comparator of Section 5).  Same pointer,
+ * size and error rules as fmm_gemm; needs no plan and no workspace.
+ */
+fmm_status fmm_classical_gemm(const double *A, int64_t lda, const double *B,
+                              int64_t ldb, double *C, int64_t ldc, int64_t m,
+                              int64_t k, int64_t n, void *stream);
+
+/*
+ * fmm_host_workspace_size / fmm_gemm_host - end-to-end variant taking HOST
+ * matrices: copies A and B to the device, runs fmm_gemm (or the classical
+ * GEMM when plan is NULL), copies C back, and returns when C is on the host.
+ * Host buffers should be page-locked for full copy speed.  dev_ws is a
+ * device buffer of at least fmm_host_workspace_size() bytes, 256-byte
+ * aligned, holding the device copies and the plan's workspace.
+ */
+fmm_status fmm_host_workspace_size(fmm_plan_t plan, int64_t m, int64_t k,
+                                   int64_t n, size_t *bytes);
+fmm_status fmm_gemm_host(fmm_plan_t plan, const double *A, int64_t lda,
+                         const double *B, int64_t ldb, double *C, int64_t ldc,
+                         int64_t m, int64_t k, int64_t n, void *dev_ws,
+                         size_t ws_bytes, void *stream);
+
+/* Number of CUDA kernel launches the last fmm_gemm / fmm_classical_gemm
+   call on this host thread enqueued (for launch accounting). */
+int fmm_last_launch_count(void);
+
+/*
+ * Kernel timing for benchmarks.  While enabled on a host thread, each
+ * fmm_gemm / fmm_classical_gemm call made from that thread records a CUDA
+ * event pair around its leaf-product launch on the call's stream (up to 1024
+ * calls are kept).  fmm_timing_leaf_ms waits for the recorded events and
+ * returns the summed milliseconds and the number of calls, then clears the
+ * record.  Errors: FMM_ERR_ARG (null output), FMM_ERR_CUDA.
+ */
+fmm_status fmm_timing_enable(int on);
+fmm_status fmm_timing_leaf_ms(double *total_ms, int *count);
+
+/* Static string for a status code. */
+const char *fmm_status_string(fmm_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FMM_H_ */

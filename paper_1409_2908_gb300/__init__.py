@@ -1,0 +1,236 @@
+"""GB300-native recursive fast matrix multiplication (Benson & Ballard,
+"A Framework for Practical Parallel Fast Matrix Multiplication").
+
+Thin Python binding over the C ABI of libfmm.so (include/fmm.h): it only
+marshals arguments.  Every step of a product runs in the library's CUDA
+kernels; PyTorch supplies device memory and streams.  There is no CPU path.
+"""
+import ctypes
+import os
+
+from . import _lib
+
+FMM_OK = 0
+FMM_ERR_ARG = -1
+FMM_ERR_INVALID_ALGORITHM = -2
+FMM_ERR_UNSUPPORTED = -3
+FMM_ERR_NO_MEMORY = -4
+FMM_ERR_CUDA = -5
+FMM_ERR_TIMEOUT = -6
+
+FMM_PREC_FP64 = 0
+FLAG_FUSED_ST = 1
+FLAG_FUSED_W = 2
+FLAGS_DEFAULT = FLAG_FUSED_ST | FLAG_FUSED_W
+
+TILES = {"auto": 0, "128x128": 1, "96x96": 2, "64x64": 3, "32x32": 4, "128x64": 5, "64x128": 6}
+
+ALGORITHM_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "algorithms")
+
+
+class FmmError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = _lib.lib().fmm_status_string(status).decode()
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+def _check(status, what):
+    if status != FMM_OK:
+        raise FmmError(status, what)
+
+
+def algorithm_path(name):
+    """Path of a shipped algorithm file, e.g. 'strassen_222_7'."""
+    p = name if os.path.isabs(name) else os.path.join(ALGORITHM_DIR, name)
+    if not p.endswith(".fmm"):
+        p += ".fmm"
+    return p
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _mat(t, name):
+    """(pointer, leading dimension, rows, cols) of a row-major FP64 matrix;
+    a torch CUDA tensor or anything exposing a data pointer and strides."""
+    if t.dim() != 2 or t.dtype.is_floating_point is False:
+        raise ValueError(f"{name} must be a 2-D floating tensor")
+    import torch
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64")
+    if t.stride(1) != 1:
+        raise ValueError(f"{name} must have unit column stride")
+    return ctypes.c_void_p(t.data_ptr()), max(t.stride(0), t.shape[1]), t.shape[0], t.shape[1]
+
+
+class Plan:
+    """A fast-multiplication plan: base case [[U,V,W]] unrolled over `levels`
+    recursive steps (fmm_plan_create / fmm_plan_load)."""
+
+    def __init__(self, algorithm=None, levels=1, flags=FLAGS_DEFAULT, tile="auto", factors=None):
+        L = _lib.lib()
+        h = ctypes.c_void_p()
+        if factors is not None:
+            import numpy as np
+            M, K, N, U, V, W = factors
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            W = np.ascontiguousarray(W, dtype=np.float64)
+            R = U.shape[1]
+            st = L.fmm_plan_create(ctypes.byref(h), M, K, N, R, U.ctypes.data, V.ctypes.data,
+                                   W.ctypes.data, levels, FMM_PREC_FP64, flags)
+        else:
+            st = L.fmm_plan_load(ctypes.byref(h), algorithm_path(algorithm).encode(), levels,
+                                 FMM_PREC_FP64, flags)
+        _check(st, "plan")
+        self._h = h
+        self.levels = levels
+        self.flags = flags
+        self.name = algorithm if factors is None else "custom"
+        if tile != "auto":
+            self.set_tile(tile)
+
+    def set_tile(self, tile):
+        _check(_lib.lib().fmm_plan_set_tile(self._h, TILES[tile]), "set_tile")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = _lib.PlanInfo()
+        _check(_lib.lib().fmm_plan_info(self._h, ctypes.byref(inf)), "info")
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def leaf_terms(self, which):
+        """(ptr, row, col, coef) numpy arrays of the unrolled lists of
+        operand `which` (0: A/U, 1: B/V, 2: C/W)."""
+        import numpy as np
+        inf = self.info()
+        n = inf[("nnz_a_terms", "nnz_b_terms", "nnz_c_terms")[which]]
+        ptr = np.zeros(inf["leaves"] + 1, np.int64)
+        row = np.zeros(n, np.int32)
+        col = np.zeros(n, np.int32)
+        coef = np.zeros(n, np.float64)
+        _check(_lib.lib().fmm_plan_leaf_terms(self._h, which, ptr.ctypes.data, row.ctypes.data,
+                                              col.ctypes.data, coef.ctypes.data, n), "leaf_terms")
+        return ptr, row, col, coef
+
+    def workspace_size(self, m, k, n):
+        b = ctypes.c_size_t()
+        _check(_lib.lib().fmm_workspace_size(self._h, m, k, n, ctypes.byref(b)), "workspace_size")
+        return b.value
+
+    def host_workspace_size(self, m, k, n):
+        b = ctypes.c_size_t()
+        _check(_lib.lib().fmm_host_workspace_size(self._h, m, k, n, ctypes.byref(b)),
+               "host_workspace_size")
+        return b.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.lib().fmm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _alloc_ws(nbytes, device):
+    import torch
+    if nbytes == 0:
+        return None
+    return torch.empty(nbytes, dtype=torch.uint8, device=device)
+
+
+def gemm(plan, A, B, C=None, workspace=None, stream=None):
+    """C = A B with the plan's fast algorithm (fmm_gemm).  A, B, C: CUDA
+    float64 tensors, row-major.  Returns C."""
+    import torch
+    pa, lda, m, k = _mat(A, "A")
+    pb, ldb, k2, n = _mat(B, "B")
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    pc, ldc, m2, n2 = _mat(C, "C")
+    if (m2, n2) != (m, n):
+        raise ValueError("C has the wrong shape")
+    need = plan.workspace_size(m, k, n)
+    if workspace is None:
+        workspace = _alloc_ws(need, A.device)
+    wptr = ctypes.c_void_p(workspace.data_ptr()) if workspace is not None else ctypes.c_void_p()
+    wbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    st = _lib.lib().fmm_gemm(plan.handle, pa, lda, pb, ldb, pc, ldc, m, k, n, wptr, wbytes,
+                             _stream_handle(stream))
+    _check(st, "fmm_gemm")
+    return C
+
+
+def classical_gemm(A, B, C=None, stream=None):
+    """C = A B with the library's classical FP64 GEMM (fmm_classical_gemm)."""
+    import torch
+    pa, lda, m, k = _mat(A, "A")
+    pb, ldb, k2, n = _mat(B, "B")
+    if k2 != k:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    pc, ldc, _, _ = _mat(C, "C")
+    st = _lib.lib().fmm_classical_gemm(pa, lda, pb, ldb, pc, ldc, m, k, n, _stream_handle(stream))
+    _check(st, "fmm_classical_gemm")
+    return C
+
+
+def gemm_host(plan, A, B, C, dev_ws, stream=None):
+    """End-to-end product of HOST matrices (fmm_gemm_host): A, B, C are CPU
+    float64 tensors (ideally pinned), dev_ws a CUDA byte tensor of
+    host_workspace_size() bytes.  plan=None uses the classical GEMM."""
+    pa, lda, m, k = _mat(A, "A")
+    pb, ldb, k2, n = _mat(B, "B")
+    pc, ldc, _, _ = _mat(C, "C")
+    h = plan.handle if plan is not None else ctypes.c_void_p()
+    st = _lib.lib().fmm_gemm_host(h, pa, lda, pb, ldb, pc, ldc, m, k, n,
+                                  ctypes.c_void_p(dev_ws.data_ptr()),
+                                  dev_ws.numel() * dev_ws.element_size(), _stream_handle(stream))
+    _check(st, "fmm_gemm_host")
+    return C
+
+
+def host_workspace_size(plan, m, k, n):
+    b = ctypes.c_size_t()
+    h = plan.handle if plan is not None else ctypes.c_void_p()
+    _check(_lib.lib().fmm_host_workspace_size(h, m, k, n, ctypes.byref(b)), "host_workspace_size")
+    return b.value
+
+
+def last_launch_count():
+    """Kernel launches enqueued by the last gemm / classical_gemm call on this thread."""
+    return _lib.lib().fmm_last_launch_count()
+
+
+def timing_enable(on=True):
+    """Record CUDA events around each call's leaf-product launch (this thread)."""
+    _check(_lib.lib().fmm_timing_enable(1 if on else 0), "timing_enable")
+
+
+def timing_leaf_ms():
+    """(summed milliseconds, calls) of the recorded leaf launches; clears them."""
+    ms = ctypes.c_double()
+    cnt = ctypes.c_int()
+    _check(_lib.lib().fmm_timing_leaf_ms(ctypes.byref(ms), ctypes.byref(cnt)), "timing_leaf_ms")
+    return ms.value, cnt.value
+
+
+def library_path():
+    return _lib.path()

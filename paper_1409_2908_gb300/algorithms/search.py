@@ -161,8 +161,12 @@ def sparsify(prob, x, fixed, rng):
 def discretise(prob, x, rng, log=None, max_fail=600):
     """Alternate zero-fixing (sparsify) with fixing one entry to +-1 (then
     +-2, +-1/2 as fallbacks), nearest-in-ratio first, re-solving each time."""
+    return discretise_from(prob, x, np.zeros(prob.n, bool), rng, max_fail=max_fail)
+
+
+def discretise_from(prob, x, fixed, rng, max_fail=600):
+    """discretise() with the entries flagged in ``fixed`` already final."""
     n = prob.n
-    fixed = np.zeros(n, bool)
     x = sparsify(prob, x, fixed, rng)
     x = normalise(prob, x)
     x, res = lm(prob, x, np.flatnonzero(~fixed), iters=100)
@@ -211,9 +215,9 @@ def discretise(prob, x, rng, log=None, max_fail=600):
 
 def exact_check(prob, x):
     U, V, W = prob.split(x)
-    Uf = [[Fraction(v).limit_denominator(8) for v in row] for row in U]
-    Vf = [[Fraction(v).limit_denominator(8) for v in row] for row in V]
-    Wf = [[Fraction(v).limit_denominator(8) for v in row] for row in W]
+    Uf = [[Fraction(v).limit_denominator(64) for v in row] for row in U]
+    Vf = [[Fraction(v).limit_denominator(64) for v in row] for row in V]
+    Wf = [[Fraction(v).limit_denominator(64) for v in row] for row in W]
     R = prob.R
     for i in range(prob.I):
         for j in range(prob.J):

@@ -1,0 +1,453 @@
+// C ABI entry points (include/fmm.h): argument validation, peeling geometry
+// (Section 3.4) and the launch sequence of one fast product.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "fmm_internal.h"
+
+using namespace fmm;
+
+namespace {
+
+thread_local int t_launches = 0;
+
+// Optional event pairs around the leaf launch (fmm_timing_enable).
+struct Timing {
+    bool on = false;
+    int device = -1;
+    std::vector<cudaEvent_t> ev;   // 2 per call
+    int used = 0;
+    ~Timing() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+    cudaEvent_t next() {
+        if (used >= 2048) return nullptr;
+        if (used >= (int)ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            ev.push_back(e);
+        }
+        return ev[used++];
+    }
+};
+thread_local Timing t_timing;
+
+cudaEvent_t timing_mark(cudaStream_t s) {
+    if (!t_timing.on) return nullptr;
+    cudaEvent_t e = t_timing.next();
+    if (e) cudaEventRecord(e, s);
+    return e;
+}
+
+int64_t ipow(int64_t b, int e) {
+    int64_t r = 1;
+    while (e-- > 0) r *= b;
+    return r;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool overlaps(const void *a, size_t abytes, const void *b, size_t bbytes) {
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + bbytes && y < x + abytes;
+}
+
+// Bytes spanned by an m x n row-major matrix with leading dimension ld.
+size_t span(int64_t m, int64_t n, int64_t ld) { return size_t(((m - 1) * ld + n) * 8); }
+
+fmm_status check_operands(const double *A, int64_t lda, const double *B, int64_t ldb,
+                          const double *C, int64_t ldc, int64_t m, int64_t k, int64_t n) {
+    if (!A || !B || !C) return FMM_ERR_ARG;
+    if (m < 1 || k < 1 || n < 1) return FMM_ERR_ARG;
+    if (m > (int64_t(1) << 31) || k > (int64_t(1) << 31) || n > (int64_t(1) << 31))
+        return FMM_ERR_ARG;
+    if (lda < k || ldb < n || ldc < n) return FMM_ERR_ARG;
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C) & 7) return FMM_ERR_ARG;
+    if (overlaps(C, span(m, n, ldc), A, span(m, k, lda)) ||
+        overlaps(C, span(m, n, ldc), B, span(k, n, ldb)))
+        return FMM_ERR_ARG;
+    return FMM_OK;
+}
+
+struct Geometry {
+    int64_t mp, kp, np, mL, kL, nL;
+    bool fast;  // a nonempty core for the fast algorithm
+};
+
+Geometry geometry(const fmm_plan *p, int64_t m, int64_t k, int64_t n) {
+    Geometry g{};
+    const int64_t sm = ipow(p->M, p->L), sk = ipow(p->K, p->L), sn = ipow(p->N, p->L);
+    g.mp = (m / sm) * sm;
+    g.kp = (k / sk) * sk;
+    g.np = (n / sn) * sn;
+    g.mL = g.mp / sm;
+    g.kL = g.kp / sk;
+    g.nL = g.np / sn;
+    g.fast = p->L > 0 && g.mp > 0 && g.kp > 0 && g.np > 0;
+    return g;
+}
+
+struct WsLayout {
+    size_t slotA = 0, slotB = 0, prod = 0, total = 0;
+};
+
+WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
+    WsLayout w;
+    if (!g.fast) return w;
+    size_t off = 0;
+    if (!(p->flags & FMM_FLAG_FUSED_ST)) {
+        w.slotA = off;
+        off = align256(off + size_t(p->slots_a) * g.mL * g.kL * 8);
+        w.slotB = off;
+        off = align256(off + size_t(p->slots_b) * g.kL * g.nL * 8);
+    }
+    if (!(p->flags & FMM_FLAG_FUSED_W)) {
+        w.prod = off;
+        off = align256(off + size_t(p->leaves) * g.mL * g.nL * 8);
+    }
+    w.total = off;
+    return w;
+}
+
+fmm_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FMM_OK;
+    return e == cudaErrorMemoryAllocation ? FMM_ERR_NO_MEMORY : FMM_ERR_CUDA;
+}
+
+int device_sms() {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// Copy the unrolled lists to the device on first use (plan creation itself
+// needs no GPU).
+fmm_status ensure_uploaded(fmm_plan *p) {
+    std::lock_guard<std::mutex> g(p->upload_mu);
+    if (p->uploaded) return FMM_OK;
+    fmm_status st;
+    try {
+        st = upload_plan(p);
+    } catch (const std::bad_alloc &) {
+        st = FMM_ERR_NO_MEMORY;
+    }
+    if (st == FMM_OK) p->uploaded = true;
+    return st;
+}
+
+// Record a timing pair around one launch sequence (no-op unless enabled).
+template <class F>
+cudaError_t timed(cudaStream_t s, F &&f) {
+    cudaEvent_t a = timing_mark(s);
+    cudaError_t e = f();
+    cudaEvent_t b = timing_mark(s);
+    if (a && !b) --t_timing.used;   // keep pairs aligned
+    return e;
+}
+
+// The fast core plus the classical fringe, all on one stream.
+fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
+                    size_t ws_bytes, cudaStream_t s, int *launches) {
+    const Geometry g = geometry(p, m, k, n);
+    if (!g.fast)
+        return cuda_status(timed(s, [&] {
+            return launch_classical(A, lda, B, ldb, C, ldc, m, k, n, FMM_TILE_AUTO, s, launches);
+        }));
+    const WsLayout wl = ws_layout(p, g);
+    if (wl.total > 0 && (!ws || ws_bytes < wl.total)) return FMM_ERR_NO_MEMORY;
+    {
+        const fmm_status us = ensure_uploaded(p);
+        if (us != FMM_OK) return us;
+    }
+    if (wl.total > 0 && ((uintptr_t)ws & 255)) return FMM_ERR_ARG;
+    char *wsb = (char *)ws;
+    const bool fused_st = p->flags & FMM_FLAG_FUSED_ST;
+    const bool fused_w = p->flags & FMM_FLAG_FUSED_W;
+    cudaError_t e;
+
+    // write-once S_r and T_r (unfused scheme)
+    double *slotA = nullptr, *slotB = nullptr;
+    if (!fused_st) {
+        slotA = (double *)(wsb + wl.slotA);
+        slotB = (double *)(wsb + wl.slotB);
+        if (p->slots_a > 0 &&
+            (e = launch_form_slots(A, lda, g.mL, g.kL, p->slots_a, p->dev.sa_leaf, p->dev.a_ptr,
+                                   p->dev.a_code, p->dev.a_coef, slotA, g.mL * g.kL, s,
+                                   launches)) != cudaSuccess)
+            return cuda_status(e);
+        if (p->slots_b > 0 &&
+            (e = launch_form_slots(B, ldb, g.kL, g.nL, p->slots_b, p->dev.sb_leaf, p->dev.b_ptr,
+                                   p->dev.b_code, p->dev.b_coef, slotB, g.kL * g.nL, s,
+                                   launches)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    // C[:m',:n'] starts as the k-fringe product A[:m',k':] B[k':,:n'], or zero
+    const bool kfringe = g.kp < k;
+    if (fused_w) {
+        if (kfringe) {
+            if ((e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
+                                      g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+                return cuda_status(e);
+        } else {
+            if ((e = cudaMemset2DAsync(C, ldc * 8, 0, g.np * 8, g.mp, s)) != cudaSuccess)
+                return cuda_status(e);
+        }
+    }
+    LeafLaunch L{};
+    L.A = A; L.lda = lda; L.B = B; L.ldb = ldb; L.C = C; L.ldc = ldc;
+    L.mL = g.mL; L.kL = g.kL; L.nL = g.nL; L.leaves = p->leaves;
+    if (fused_st) {
+        L.a_ptr = p->dev.a_ptr; L.a_code = p->dev.a_code; L.a_coef = p->dev.a_coef;
+        L.b_ptr = p->dev.b_ptr; L.b_code = p->dev.b_code; L.b_coef = p->dev.b_coef;
+    } else {
+        L.a_ptr = p->dev.ua_ptr; L.a_code = p->dev.ua_code; L.a_coef = p->dev.u_one;
+        L.b_ptr = p->dev.ub_ptr; L.b_code = p->dev.ub_code; L.b_coef = p->dev.u_one;
+        L.slotA = slotA; L.slotA_stride = g.mL * g.kL;
+        L.slotB = slotB; L.slotB_stride = g.kL * g.nL;
+    }
+    L.c_ptr = p->dev.c_ptr; L.c_code = p->dev.c_code; L.c_coef = p->dev.c_coef;
+    double *wsM = fused_w ? nullptr : (double *)(wsb + wl.prod);
+    L.wsM = wsM;
+    L.epi = fused_w ? EPI_ATOMIC : EPI_WORKSPACE;
+    const double extra_a = fused_st ? double(p->a.row.size()) / double(p->leaves) - 1.0 : 0.0;
+    const double extra_b = fused_st ? double(p->b.row.size()) / double(p->leaves) - 1.0 : 0.0;
+    L.tile = resolve_tile(p->tile, g.mL, g.nL, g.kL, p->leaves, extra_a, extra_b, device_sms());
+    if ((e = timed(s, [&] { return launch_leaf_gemm(L, s, launches); })) != cudaSuccess)
+        return cuda_status(e);
+    if (!fused_w) {
+        if (kfringe &&
+            (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp, g.np,
+                                  FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        const int64_t gridN = ipow(p->N, p->L), blocks = ipow(p->M, p->L) * gridN;
+        if ((e = launch_w_pass(C, ldc, g.mL, g.nL, int(gridN), blocks, p->dev.cq_ptr,
+                               p->dev.cq_leaf, p->dev.cq_coef, wsM, kfringe ? 1 : 0, s,
+                               launches)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    // fringe rows and columns (Section 3.4)
+    if (g.mp < m &&
+        (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
+                              FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        return cuda_status(e);
+    if (g.np < n &&
+        (e = launch_classical(A, lda, B + g.np, ldb, C + g.np, ldc, g.mp, k, n - g.np,
+                              FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        return cuda_status(e);
+    return FMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fmm_status_string(fmm_status st) {
+    switch (st) {
+        case FMM_OK: return "ok";
+        case FMM_ERR_ARG: return "invalid argument";
+        case FMM_ERR_INVALID_ALGORITHM: return "factor matrices fail the Brent equations";
+        case FMM_ERR_UNSUPPORTED: return "unsupported request";
+        case FMM_ERR_NO_MEMORY: return "out of memory or workspace too small";
+        case FMM_ERR_CUDA: return "CUDA error";
+        case FMM_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+int fmm_last_launch_count(void) { return t_launches; }
+
+fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const double *U,
+                           const double *V, const double *W, int levels, fmm_precision prec,
+                           unsigned flags) {
+    if (!out || !U || !V || !W) return FMM_ERR_ARG;
+    if (M < 1 || K < 1 || N < 1 || R < 1 || R > 4096) return FMM_ERR_ARG;
+    if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
+    if (levels < 0 || levels > 6) return FMM_ERR_ARG;
+    if (prec != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W)) return FMM_ERR_ARG;
+    bool representable = true;
+    if (!brent_exact(M, K, N, R, U, V, W, &representable))
+        return representable ? FMM_ERR_INVALID_ALGORITHM : FMM_ERR_UNSUPPORTED;
+    fmm_plan *p = new (std::nothrow) fmm_plan();
+    if (!p) return FMM_ERR_NO_MEMORY;
+    p->flags = flags;
+    cudaGetDevice(&p->device);
+    fmm_status st;
+    try {
+        st = build_plan(p, M, K, N, R, U, V, W, levels);
+    } catch (const std::bad_alloc &) {
+        st = FMM_ERR_NO_MEMORY;
+    }
+    if (st != FMM_OK) {
+        free_plan_device(p);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_load(fmm_plan_t *out, const char *path, int levels, fmm_precision prec,
+                         unsigned flags) {
+    if (!out || !path) return FMM_ERR_ARG;
+    int M, K, N, R;
+    std::vector<double> U, V, W;
+    fmm_status st;
+    try {
+        st = parse_fmm_file(path, &M, &K, &N, &R, &U, &V, &W);
+    } catch (const std::bad_alloc &) {
+        return FMM_ERR_NO_MEMORY;
+    }
+    if (st != FMM_OK) return st;
+    return fmm_plan_create(out, M, K, N, R, U.data(), V.data(), W.data(), levels, prec, flags);
+}
+
+void fmm_plan_destroy(fmm_plan_t p) {
+    if (!p) return;
+    free_plan_device(p);
+    delete p;
+}
+
+fmm_status fmm_plan_set_tile(fmm_plan_t p, fmm_tile tile) {
+    if (!p || tile < FMM_TILE_AUTO || tile > FMM_TILE_64x128) return FMM_ERR_ARG;
+    p->tile = tile;
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_info(fmm_plan_t p, fmm_plan_info_t *info) {
+    if (!p || !info) return FMM_ERR_ARG;
+    info->M = p->M; info->K = p->K; info->N = p->N; info->R = p->R; info->levels = p->L;
+    info->flags = p->flags;
+    info->leaves = p->leaves;
+    info->nnz_a_terms = (int64_t)p->a.row.size();
+    info->nnz_b_terms = (int64_t)p->b.row.size();
+    info->nnz_c_terms = (int64_t)p->c.row.size();
+    info->max_a_terms = p->a.max_terms();
+    info->max_b_terms = p->b.max_terms();
+    info->max_c_terms = p->c.max_terms();
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_leaf_terms(fmm_plan_t p, int which, int64_t *ptr, int32_t *row, int32_t *col,
+                               double *coef, int64_t capacity) {
+    if (!p || which < 0 || which > 2) return FMM_ERR_ARG;
+    const TermList &t = which == 0 ? p->a : (which == 1 ? p->b : p->c);
+    const int64_t n = (int64_t)t.row.size();
+    if ((row || col || coef) && capacity < n) return FMM_ERR_ARG;
+    if (ptr) std::memcpy(ptr, t.ptr.data(), t.ptr.size() * sizeof(int64_t));
+    if (row) std::memcpy(row, t.row.data(), n * sizeof(int32_t));
+    if (col) std::memcpy(col, t.col.data(), n * sizeof(int32_t));
+    if (coef) std::memcpy(coef, t.coef.data(), n * sizeof(double));
+    return FMM_OK;
+}
+
+fmm_status fmm_workspace_size(fmm_plan_t p, int64_t m, int64_t k, int64_t n, size_t *bytes) {
+    if (!p || !bytes || m < 1 || k < 1 || n < 1) return FMM_ERR_ARG;
+    *bytes = ws_layout(p, geometry(p, m, k, n)).total;
+    return FMM_OK;
+}
+
+fmm_status fmm_gemm(fmm_plan_t p, const double *A, int64_t lda, const double *B, int64_t ldb,
+                    double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
+                    size_t ws_bytes, void *stream) {
+    t_launches = 0;
+    if (!p) return FMM_ERR_ARG;
+    fmm_status st = check_operands(A, lda, B, ldb, C, ldc, m, k, n);
+    if (st != FMM_OK) return st;
+    int launches = 0;
+    st = run_gemm(p, A, lda, B, ldb, C, ldc, m, k, n, ws, ws_bytes, (cudaStream_t)stream,
+                  &launches);
+    t_launches = launches;
+    return st;
+}
+
+fmm_status fmm_classical_gemm(const double *A, int64_t lda, const double *B, int64_t ldb,
+                              double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
+                              void *stream) {
+    t_launches = 0;
+    fmm_status st = check_operands(A, lda, B, ldb, C, ldc, m, k, n);
+    if (st != FMM_OK) return st;
+    int launches = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = cuda_status(timed(s, [&] {
+        return launch_classical(A, lda, B, ldb, C, ldc, m, k, n, FMM_TILE_AUTO, s, &launches);
+    }));
+    t_launches = launches;
+    return st;
+}
+
+fmm_status fmm_timing_enable(int on) {
+    t_timing.on = on != 0;
+    t_timing.used = 0;
+    return FMM_OK;
+}
+
+fmm_status fmm_timing_leaf_ms(double *total_ms, int *count) {
+    if (!total_ms || !count) return FMM_ERR_ARG;
+    double tot = 0.0;
+    int n = 0;
+    for (int i = 0; i + 1 < t_timing.used; i += 2) {
+        if (cudaEventSynchronize(t_timing.ev[i + 1]) != cudaSuccess) return FMM_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t_timing.ev[i], t_timing.ev[i + 1]) != cudaSuccess)
+            return FMM_ERR_CUDA;
+        tot += ms;
+        ++n;
+    }
+    t_timing.used = 0;
+    *total_ms = tot;
+    *count = n;
+    return FMM_OK;
+}
+
+fmm_status fmm_host_workspace_size(fmm_plan_t p, int64_t m, int64_t k, int64_t n, size_t *bytes) {
+    if (!bytes || m < 1 || k < 1 || n < 1) return FMM_ERR_ARG;
+    size_t ws = 0;
+    if (p) ws = ws_layout(p, geometry(p, m, k, n)).total;
+    *bytes = align256(size_t(m * k * 8)) + align256(size_t(k * n * 8)) +
+             align256(size_t(m * n * 8)) + ws;
+    return FMM_OK;
+}
+
+fmm_status fmm_gemm_host(fmm_plan_t p, const double *A, int64_t lda, const double *B,
+                         int64_t ldb, double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
+                         void *dev_ws, size_t ws_bytes, void *stream) {
+    t_launches = 0;
+    if (!A || !B || !C || !dev_ws) return FMM_ERR_ARG;
+    if (m < 1 || k < 1 || n < 1 || lda < k || ldb < n || ldc < n) return FMM_ERR_ARG;
+    if ((uintptr_t)dev_ws & 255) return FMM_ERR_ARG;
+    size_t need = 0;
+    fmm_host_workspace_size(p, m, k, n, &need);
+    if (ws_bytes < need) return FMM_ERR_NO_MEMORY;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *w = (char *)dev_ws;
+    double *dA = (double *)w;
+    double *dB = (double *)(w + align256(size_t(m * k * 8)));
+    double *dC = (double *)((char *)dB + align256(size_t(k * n * 8)));
+    char *rest = (char *)dC + align256(size_t(m * n * 8));
+    cudaError_t e;
+    if ((e = cudaMemcpy2DAsync(dA, k * 8, A, lda * 8, k * 8, m, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = cudaMemcpy2DAsync(dB, n * 8, B, ldb * 8, n * 8, k, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_status(e);
+    fmm_status st;
+    int launches = 0;
+    if (p)
+        st = run_gemm(p, dA, k, dB, n, dC, n, m, k, n, rest, ws_bytes - (rest - w), s, &launches);
+    else
+        st = cuda_status(launch_classical(dA, k, dB, n, dC, n, m, k, n, FMM_TILE_AUTO, s, &launches));
+    t_launches = launches;
+    if (st != FMM_OK) return st;
+    if ((e = cudaMemcpy2DAsync(C, ldc * 8, dC, n * 8, n * 8, m, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_status(e);
+    return cuda_status(cudaStreamSynchronize(s));
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal declarations shared by the host plan layer (plan.cpp), the kernels
+// (fp64_kernels.cu) and the ABI entry points (api.cu).
+#pragma once
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fmm.h"
+
+namespace fmm {
+
+// Per-leaf list of blocks with coefficients, in CSR form over the leaves.
+struct TermList {
+    std::vector<int64_t> ptr;   // leaves + 1
+    std::vector<int32_t> row;   // block row in the grid of blocks
+    std::vector<int32_t> col;   // block column
+    std::vector<double> coef;   // coefficient (product over the L steps)
+    int max_terms() const {
+        int m = 0;
+        for (size_t i = 0; i + 1 < ptr.size(); ++i)
+            m = std::max<int>(m, int(ptr[i + 1] - ptr[i]));
+        return m;
+    }
+};
+
+// Device copy of the unrolled plan.  Operand codes: code >= 0 is a block of
+// the input matrix, (row << 16) | col; code < 0 is workspace slot (-code - 1)
+// holding a pre-formed S_r or T_r (write-once scheme).
+struct DevicePlan {
+    int *a_ptr = nullptr, *a_code = nullptr;     // fused: all terms
+    double *a_coef = nullptr;
+    int *b_ptr = nullptr, *b_code = nullptr;
+    double *b_coef = nullptr;
+    int *c_ptr = nullptr, *c_code = nullptr;     // epilogue terms per leaf
+    double *c_coef = nullptr;                    // W coefficient * sA * sB
+    // write-once scheme: per leaf one operand code (block or slot)
+    int *ua_code = nullptr, *ub_code = nullptr;
+    int *ua_ptr = nullptr, *ub_ptr = nullptr;    // CSR with one term per leaf
+    double *u_one = nullptr;                     // coefficient 1.0 per leaf
+    // slots of the write-once pass: leaf index and CSR into a_* / b_*
+    int *sa_leaf = nullptr, *sb_leaf = nullptr;
+    // per C block: CSR over (leaf, coefficient) for the write-once W pass
+    int *cq_ptr = nullptr, *cq_leaf = nullptr;
+    double *cq_coef = nullptr;
+    void *blob = nullptr;                        // single allocation
+};
+
+}  // namespace fmm
+
+struct fmm_plan {
+    int M = 0, K = 0, N = 0, R = 0, L = 0;
+    unsigned flags = 0;
+    int device = 0;
+    fmm_tile tile = FMM_TILE_AUTO;
+    int64_t leaves = 1;
+    fmm::TermList a, b, c;                   // unscaled, as exported
+    // normalised lists (first coefficient of each S_r/T_r is 1, the scale
+    // folded into the epilogue coefficient)
+    std::vector<double> a_norm, b_norm, c_scaled;
+    int64_t slots_a = 0, slots_b = 0;        // leaves with > 1 term
+    std::vector<int32_t> slot_of_leaf_a, slot_of_leaf_b;
+    fmm::DevicePlan dev;                     // uploaded on first use
+    std::mutex upload_mu;
+    bool uploaded = false;
+};
+
+namespace fmm {
+
+// plan.cpp
+fmm_status build_plan(fmm_plan *p, int M, int K, int N, int R, const double *U,
+                      const double *V, const double *W, int levels);
+fmm_status upload_plan(fmm_plan *p);
+void free_plan_device(fmm_plan *p);
+bool brent_exact(int M, int K, int N, int R, const double *U, const double *V,
+                 const double *W, bool *representable);
+fmm_status parse_fmm_file(const char *path, int *M, int *K, int *N, int *R,
+                          std::vector<double> *U, std::vector<double> *V,
+                          std::vector<double> *W);
+
+// fp64_kernels.cu
+struct LeafLaunch {
+    const double *A; int64_t lda;
+    const double *B; int64_t ldb;
+    double *C; int64_t ldc;
+    int64_t mL, kL, nL;
+    int64_t leaves;
+    const int *a_ptr; const int *a_code; const double *a_coef;
+    const int *b_ptr; const int *b_code; const double *b_coef;
+    const int *c_ptr; const int *c_code; const double *c_coef;
+    const double *slotA; int64_t slotA_stride;   // write-once S slots (ld kL)
+    const double *slotB; int64_t slotB_stride;   // write-once T slots (ld nL)
+    double *wsM;                                 // leaf products (ld nL)
+    int epi;                                     // EPI_* below
+    int tile;                                    // fmm_tile (resolved)
+};
+enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_WORKSPACE = 2 };
+
+cudaError_t launch_leaf_gemm(const LeafLaunch &a, cudaStream_t s, int *launches);
+cudaError_t launch_form_slots(const double *X, int64_t ldx, int64_t rows, int64_t cols,
+                              int64_t slots, const int *slot_leaf, const int *ptr,
+                              const int *code, const double *coef, double *out,
+                              int64_t out_stride, cudaStream_t s, int *launches);
+cudaError_t launch_w_pass(double *C, int64_t ldc, int64_t mL, int64_t nL, int gridN,
+                          int64_t blocks, const int *cq_ptr, const int *cq_leaf,
+                          const double *cq_coef, const double *wsM, int accumulate,
+                          cudaStream_t s, int *launches);
+cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
+                             double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
+                             int tile, cudaStream_t s, int *launches);
+int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
+                 double extra_a, double extra_b, int num_sms);
+void tile_dims(int tile, int *bm, int *bn);
+
+}  // namespace fmm

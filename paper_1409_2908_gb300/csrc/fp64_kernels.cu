@@ -1,0 +1,410 @@
+// FP64 kernels of the fast-multiplication hot path on sm_103a.
+//
+//   leaf_gemm      grouped GEMM over all R^L leaf products M_r = S_r T_r
+//                  (Section 3.1; one launch for every leaf, the GPU analogue
+//                  of running all leaves of the recursion tree as tasks,
+//                  Section 4.2).  Operand staging forms S_r and T_r from the
+//                  A and B blocks while filling shared memory (the write-once
+//                  chains of Section 3.2 moved on chip); the epilogue applies
+//                  the W coefficients.
+//   form_slots     write-once formation of S_r / T_r into workspace
+//                  (Section 3.2, "write-once"), for the unfused scheme.
+//   w_pass         write-once formation of the C blocks from stored M_r.
+//
+// The FP64 pipe of GB300 retires 2 DFMA per SM per clock, so the leaf GEMM
+// is bound by FP64 issue, not by memory: the tile is sized so that each warp
+// has 16-64 independent FMAs per shared-memory fragment, and shared-memory
+// layouts are chosen to keep fragment reads broadcast or conflict-free.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fmm_internal.h"
+
+namespace fmm {
+
+namespace {
+
+constexpr int BK = 16;        // k-depth of one shared-memory stage
+constexpr int THREADS = 256;  // 16 x 16 threads
+
+struct KParams {
+    const double *A; int64_t lda;
+    const double *B; int64_t ldb;
+    double *C; int64_t ldc;
+    int64_t mL, kL, nL;
+    const int *a_ptr; const int *a_code; const double *a_coef;
+    const int *b_ptr; const int *b_code; const double *b_coef;
+    const int *c_ptr; const int *c_code; const double *c_coef;
+    const double *slotA; int64_t slotA_stride;
+    const double *slotB; int64_t slotB_stride;
+    double *wsM;
+    int epi;
+    int tiles_n;
+    int64_t leaf_base;
+};
+
+// Base address and leading dimension of one operand term.
+__device__ __forceinline__ const double *term_base(int code, const double *X, int64_t ld,
+                                                    int64_t brows, int64_t bcols,
+                                                    const double *slot, int64_t slot_stride,
+                                                    int64_t slot_ld, int64_t *ld_out) {
+    if (code >= 0) {
+        *ld_out = ld;
+        return X + (int64_t)(code >> 16) * brows * ld + (int64_t)(code & 0xffff) * bcols;
+    }
+    *ld_out = slot_ld;
+    return slot + (int64_t)(-code - 1) * slot_stride;
+}
+
+// Add coef * x into v; coefficients +-1 need no multiply.
+__device__ __forceinline__ double chain_step(double v, double c, double x) {
+    if (c == 1.0) return v + x;
+    if (c == -1.0) return v - x;
+    return fma(c, x, v);
+}
+
+__device__ __forceinline__ double chain_first(double c, double x) {
+    if (c == 1.0) return x;
+    return c * x;
+}
+
+template <int TM, int TN>
+__global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    constexpr int EA = BM * BK / THREADS;   // A elements staged per thread
+    constexpr int EB = BK * BN / THREADS;   // B elements staged per thread
+    constexpr int LDA_S = BM + 1;           // padded: transposed stores
+    extern __shared__ double smem[];
+    double *As = smem;                      // [2][BK][LDA_S]
+    double *Bs = smem + 2 * BK * LDA_S;     // [2][BK][BN]
+
+    const int64_t leaf = p.leaf_base + blockIdx.y;
+    const int tm = blockIdx.x / p.tiles_n, tn = blockIdx.x % p.tiles_n;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)tm * BM, col0 = (int64_t)tn * BN;
+
+    const int a0 = p.a_ptr[leaf], a1 = p.a_ptr[leaf + 1];
+    const int b0 = p.b_ptr[leaf], b1 = p.b_ptr[leaf + 1];
+
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+
+    double ra[EA], rb[EB];
+
+    // Stage k-chunk k0: S_r and T_r entries combined from all their terms.
+    auto gather = [&](int64_t k0) {
+#pragma unroll
+        for (int e = 0; e < EA; ++e) ra[e] = 0.0;
+#pragma unroll
+        for (int e = 0; e < EB; ++e) rb[e] = 0.0;
+        for (int t = a0; t < a1; ++t) {
+            int64_t ld;
+            const double *X = term_base(p.a_code[t], p.A, p.lda, p.mL, p.kL, p.slotA,
+                                        p.slotA_stride, p.kL, &ld);
+            const double c = p.a_coef[t];
+#pragma unroll
+            for (int e = 0; e < EA; ++e) {
+                const int idx = tid + THREADS * e;
+                const int r = idx / BK, kk = idx % BK;
+                const int64_t gr = row0 + r, gk = k0 + kk;
+                double x = 0.0;
+                if (gr < p.mL && gk < p.kL) x = __ldg(X + gr * ld + gk);
+                ra[e] = (t == a0) ? chain_first(c, x) : chain_step(ra[e], c, x);
+            }
+        }
+        for (int t = b0; t < b1; ++t) {
+            int64_t ld;
+            const double *X = term_base(p.b_code[t], p.B, p.ldb, p.kL, p.nL, p.slotB,
+                                        p.slotB_stride, p.nL, &ld);
+            const double c = p.b_coef[t];
+#pragma unroll
+            for (int e = 0; e < EB; ++e) {
+                const int idx = tid + THREADS * e;
+                const int kk = idx / BN, cc = idx % BN;
+                const int64_t gk = k0 + kk, gc = col0 + cc;
+                double x = 0.0;
+                if (gk < p.kL && gc < p.nL) x = __ldg(X + gk * ld + gc);
+                rb[e] = (t == b0) ? chain_first(c, x) : chain_step(rb[e], c, x);
+            }
+        }
+    };
+    auto stash = [&](int buf) {
+        double *as = As + buf * BK * LDA_S;
+        double *bs = Bs + buf * BK * BN;
+#pragma unroll
+        for (int e = 0; e < EA; ++e) {
+            const int idx = tid + THREADS * e;
+            as[(idx % BK) * LDA_S + idx / BK] = ra[e];
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            const int idx = tid + THREADS * e;
+            bs[(idx / BN) * BN + idx % BN] = rb[e];
+        }
+    };
+
+    gather(0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t k0 = 0; k0 < p.kL; k0 += BK) {
+        const bool more = k0 + BK < p.kL;
+        if (more) gather(k0 + BK);
+        const double *as = As + buf * BK * LDA_S;
+        const double *bs = Bs + buf * BK * BN;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[TM], b[TN];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = as[kk * LDA_S + ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < TN; ++j) b[j] = bs[kk * BN + tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        if (more) stash(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+    }
+
+    // Epilogue: the W coefficients of this leaf (Section 3.1, C_q = sum W_qr M_r).
+    if (p.epi == EPI_WORKSPACE) {
+        double *out = p.wsM + leaf * p.mL * p.nL;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gr = row0 + ty + 16 * i;
+            if (gr >= p.mL) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gc = col0 + tx + 16 * j;
+                if (gc < p.nL) out[gr * p.nL + gc] = acc[i][j];
+            }
+        }
+        return;
+    }
+    const int c0 = p.c_ptr[leaf], c1 = p.c_ptr[leaf + 1];
+    for (int t = c0; t < c1; ++t) {
+        const int code = p.c_code[t];
+        const double w = p.c_coef[t];
+        if (w == 0.0) continue;
+        double *Cb = p.C + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gr = row0 + ty + 16 * i;
+            if (gr >= p.mL) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gc = col0 + tx + 16 * j;
+                if (gc >= p.nL) continue;
+                const double v = (w == 1.0) ? acc[i][j] : (w == -1.0 ? -acc[i][j] : w * acc[i][j]);
+                if (p.epi == EPI_ATOMIC)
+                    atomicAdd(Cb + gr * p.ldc + gc, v);
+                else
+                    Cb[gr * p.ldc + gc] = v;
+            }
+        }
+    }
+}
+
+// S_r (or T_r) = sum_t coef_t X_t for every slot, written once.
+__global__ void form_slots_kernel(const double *X, int64_t ldx, int64_t rows, int64_t cols,
+                                  int64_t slot_base, const int *slot_leaf, const int *ptr,
+                                  const int *code, const double *coef, double *out,
+                                  int64_t out_stride) {
+    const int64_t s = slot_base + blockIdx.y;
+    const int leaf = slot_leaf[s];
+    const int t0 = ptr[leaf], t1 = ptr[leaf + 1];
+    double *o = out + s * out_stride;
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+            double v = 0.0;
+            for (int t = t0; t < t1; ++t) {
+                const int cd = code[t];
+                const double *Xt = X + (int64_t)(cd >> 16) * rows * ldx + (int64_t)(cd & 0xffff) * cols;
+                const double x = __ldg(Xt + i * ldx + j);
+                v = (t == t0) ? chain_first(coef[t], x) : chain_step(v, coef[t], x);
+            }
+            o[i * cols + j] = v;
+        }
+    }
+}
+
+// C block q = (C block q if accumulate) + sum over its leaves of w * M_leaf.
+__global__ void w_pass_kernel(double *C, int64_t ldc, int64_t mL, int64_t nL, int gridN,
+                              int64_t q_base, const int *cq_ptr, const int *cq_leaf,
+                              const double *cq_coef, const double *wsM, int accumulate) {
+    const int64_t q = q_base + blockIdx.y;
+    const int64_t brow = q / gridN, bcol = q % gridN;
+    const int t0 = cq_ptr[q], t1 = cq_ptr[q + 1];
+    double *Cb = C + brow * mL * ldc + bcol * nL;
+    for (int64_t i = blockIdx.x; i < mL; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < nL; j += blockDim.x) {
+            double v = accumulate ? Cb[i * ldc + j] : 0.0;
+            for (int t = t0; t < t1; ++t) {
+                const double w = cq_coef[t];
+                if (w == 0.0) continue;
+                const double x = __ldg(wsM + (int64_t)cq_leaf[t] * mL * nL + i * nL + j);
+                v = chain_step(v, w, x);
+            }
+            Cb[i * ldc + j] = v;
+        }
+    }
+}
+
+__device__ int g_unit_ptr[2] = {0, 1};
+__device__ int g_unit_code[1] = {0};
+__device__ double g_unit_coef[1] = {1.0};
+
+template <int TM, int TN>
+cudaError_t launch_tile(const KParams &base, int64_t leaves, cudaStream_t s, int *launches) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    const size_t smem = sizeof(double) * 2 * BK * ((BM + 1) + BN);
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(leaf_gemm<TM, TN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    KParams p = base;
+    const int64_t tiles_m = (p.mL + BM - 1) / BM, tiles_n = (p.nL + BN - 1) / BN;
+    if (tiles_m * tiles_n > 0x7fffffffLL) return cudaErrorInvalidValue;
+    p.tiles_n = (int)tiles_n;
+    for (int64_t lb = 0; lb < leaves; lb += 65535) {
+        const int64_t cnt = leaves - lb < 65535 ? leaves - lb : 65535;
+        p.leaf_base = lb;
+        dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)cnt);
+        leaf_gemm<TM, TN><<<grid, THREADS, smem, s>>>(p);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+void tile_dims(int tile, int *bm, int *bn) {
+    switch (tile) {
+        case FMM_TILE_96x96: *bm = 96; *bn = 96; break;
+        case FMM_TILE_64x64: *bm = 64; *bn = 64; break;
+        case FMM_TILE_32x32: *bm = 32; *bn = 32; break;
+        case FMM_TILE_128x64: *bm = 128; *bn = 64; break;
+        case FMM_TILE_64x128: *bm = 64; *bn = 128; break;
+        default: *bm = 128; *bn = 128; break;
+    }
+}
+
+// Pick the tile with the least estimated time: CTAs run in waves over the
+// SMs, each CTA costs its padded FMAs plus its share of chain additions.
+int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
+                 double extra_a, double extra_b, int num_sms) {
+    if (requested != FMM_TILE_AUTO) return requested;
+    const int cands[] = {FMM_TILE_128x128, FMM_TILE_128x64, FMM_TILE_64x128, FMM_TILE_96x96,
+                         FMM_TILE_64x64, FMM_TILE_32x32};
+    int best = FMM_TILE_128x128;
+    double best_t = 1e300;
+    for (int t : cands) {
+        int bm, bn;
+        tile_dims(t, &bm, &bn);
+        const double tiles = double((mL + bm - 1) / bm) * double((nL + bn - 1) / bn);
+        const double ctas = tiles * double(leaves);
+        // CTAs resident per SM for this tile (register-limited)
+        const int per_sm = (bm * bn >= 128 * 64) ? 1 : (bm * bn >= 64 * 64 ? 2 : 4);
+        const double waves = std::ceil(ctas / double(num_sms * per_sm));
+        const double cta_cost = double(bm) * bn * kL * (1.0 + extra_a / bn + extra_b / bm) * per_sm;
+        // small tiles also pay more shared-memory traffic per FMA
+        const double small = (bm * bn <= 32 * 32) ? 1.15 : (bm * bn <= 64 * 64 ? 1.03 : 1.0);
+        const double est = waves * cta_cost * small;
+        if (est < best_t * 0.999) {
+            best_t = est;
+            best = t;
+        }
+    }
+    return best;
+}
+
+cudaError_t launch_leaf_gemm(const LeafLaunch &a, cudaStream_t s, int *launches) {
+    KParams p{};
+    p.A = a.A; p.lda = a.lda; p.B = a.B; p.ldb = a.ldb; p.C = a.C; p.ldc = a.ldc;
+    p.mL = a.mL; p.kL = a.kL; p.nL = a.nL;
+    p.a_ptr = a.a_ptr; p.a_code = a.a_code; p.a_coef = a.a_coef;
+    p.b_ptr = a.b_ptr; p.b_code = a.b_code; p.b_coef = a.b_coef;
+    p.c_ptr = a.c_ptr; p.c_code = a.c_code; p.c_coef = a.c_coef;
+    p.slotA = a.slotA; p.slotA_stride = a.slotA_stride;
+    p.slotB = a.slotB; p.slotB_stride = a.slotB_stride;
+    p.wsM = a.wsM; p.epi = a.epi;
+    switch (a.tile) {
+        case FMM_TILE_96x96: return launch_tile<6, 6>(p, a.leaves, s, launches);
+        case FMM_TILE_64x64: return launch_tile<4, 4>(p, a.leaves, s, launches);
+        case FMM_TILE_32x32: return launch_tile<2, 2>(p, a.leaves, s, launches);
+        case FMM_TILE_128x64: return launch_tile<8, 4>(p, a.leaves, s, launches);
+        case FMM_TILE_64x128: return launch_tile<4, 8>(p, a.leaves, s, launches);
+        default: return launch_tile<8, 8>(p, a.leaves, s, launches);
+    }
+}
+
+cudaError_t launch_form_slots(const double *X, int64_t ldx, int64_t rows, int64_t cols,
+                              int64_t slots, const int *slot_leaf, const int *ptr,
+                              const int *code, const double *coef, double *out,
+                              int64_t out_stride, cudaStream_t s, int *launches) {
+    const unsigned gx = (unsigned)(rows < 4096 ? rows : 4096);
+    for (int64_t sb = 0; sb < slots; sb += 65535) {
+        const int64_t cnt = slots - sb < 65535 ? slots - sb : 65535;
+        form_slots_kernel<<<dim3(gx, (unsigned)cnt), 256, 0, s>>>(
+            X, ldx, rows, cols, sb, slot_leaf, ptr, code, coef, out, out_stride);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_w_pass(double *C, int64_t ldc, int64_t mL, int64_t nL, int gridN,
+                          int64_t blocks, const int *cq_ptr, const int *cq_leaf,
+                          const double *cq_coef, const double *wsM, int accumulate,
+                          cudaStream_t s, int *launches) {
+    const unsigned gx = (unsigned)(mL < 4096 ? mL : 4096);
+    for (int64_t qb = 0; qb < blocks; qb += 65535) {
+        const int64_t cnt = blocks - qb < 65535 ? blocks - qb : 65535;
+        w_pass_kernel<<<dim3(gx, (unsigned)cnt), 256, 0, s>>>(C, ldc, mL, nL, gridN, qb, cq_ptr,
+                                                               cq_leaf, cq_coef, wsM, accumulate);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
+                             double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, int tile,
+                             cudaStream_t s, int *launches) {
+    int *uptr, *ucode;
+    double *ucoef;
+    cudaError_t e;
+    if ((e = cudaGetSymbolAddress((void **)&uptr, g_unit_ptr)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&ucode, g_unit_code)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&ucoef, g_unit_coef)) != cudaSuccess) return e;
+    LeafLaunch a{};
+    a.A = A; a.lda = lda; a.B = B; a.ldb = ldb; a.C = C; a.ldc = ldc;
+    a.mL = m; a.kL = k; a.nL = n; a.leaves = 1;
+    a.a_ptr = a.b_ptr = a.c_ptr = uptr;
+    a.a_code = a.b_code = a.c_code = ucode;
+    a.a_coef = a.b_coef = a.c_coef = ucoef;
+    a.epi = EPI_STORE;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    a.tile = resolve_tile(tile, m, n, k, 1, 0.0, 0.0, sms);
+    return launch_leaf_gemm(a, s, launches);
+}
+
+}  // namespace fmm
