@@ -42,6 +42,9 @@ WORKLOADS = {
     "tall16384": dict(m=16384, k=2048, n=2048, desc="fp64 tall-skinny 16384x2048x2048, uniform[-1,1]",
                       cands=[("fmm_423_20", 1), ("fmm_323_15", 1), ("fmm_423_20", 2),
                              ("fmm_323_15", 2), ("strassen_222_7", 1), ("strassen_222_7", 2)]),
+    # profiling case: inputs above L2 (128 MiB each) but small enough for a full ncu capture
+    "square4096": dict(m=4096, k=4096, n=4096, desc="fp64 square 4096x4096x4096, uniform[-1,1]",
+                       cands=[("strassen_222_7", 1), ("strassen_222_7", 2)]),
     "strassen512": dict(m=512, k=512, n=512, desc="fp64 square 512x512x512, uniform[-1,1]",
                         cands=[("strassen_222_7", 1)]),
 }

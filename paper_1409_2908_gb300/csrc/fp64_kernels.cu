@@ -212,6 +212,188 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
     }
 }
 
+// Warp-specialised variant: PRODUCERS gather and combine S_r / T_r chunks
+// into a STAGES-deep shared-memory ring while CONSUMERS run the DFMA loop, so
+// the load latency of multi-term chains never idles the FP64 pipe.  Stage
+// hand-off uses hardware named barriers (FULL: producers arrive, consumers
+// wait; EMPTY: consumers arrive, producers wait); every thread takes part in
+// the same number of phases, so each barrier completes.
+constexpr int WS_CONSUMERS = 256;
+constexpr int WS_PRODUCERS = 128;
+constexpr int WS_THREADS = WS_CONSUMERS + WS_PRODUCERS;
+constexpr int WS_STAGES = 4;
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+template <int TM, int TN>
+__global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    constexpr int LDA_S = BM + 1;
+    constexpr int STAGE = BK * LDA_S + BK * BN;      // doubles per stage
+    constexpr int PA = BM * BK / WS_PRODUCERS;       // A elements per producer thread
+    constexpr int PB = BK * BN / WS_PRODUCERS;       // B elements per producer thread
+    extern __shared__ double smem[];
+
+    const int64_t leaf = p.leaf_base + blockIdx.y;
+    const int tm = blockIdx.x / p.tiles_n, tn = blockIdx.x % p.tiles_n;
+    const int64_t row0 = (int64_t)tm * BM, col0 = (int64_t)tn * BN;
+    const int64_t nchunks = (p.kL + BK - 1) / BK;
+    const int tid = threadIdx.x;
+
+    if (tid >= WS_CONSUMERS) {
+        // ---------------- producers ----------------
+        const int pt = tid - WS_CONSUMERS;
+        const int a0 = p.a_ptr[leaf], a1 = p.a_ptr[leaf + 1];
+        const int b0 = p.b_ptr[leaf], b1 = p.b_ptr[leaf + 1];
+        // elements gathered per batch (bounded registers)
+        constexpr int PBATCH = (PA % 8 == 0 && PB % 8 == 0) ? 8 : 4;
+        static_assert(PA % PBATCH == 0 && PB % PBATCH == 0, "producer batching");
+        for (int64_t c = 0; c < nchunks; ++c) {
+            const int st = int(c % WS_STAGES);
+            const int64_t k0 = c * BK;
+            if (c >= WS_STAGES) named_sync(1 + WS_STAGES + st, WS_THREADS);   // EMPTY[st]
+            double *as = smem + st * STAGE;
+            double *bs = as + BK * LDA_S;
+            for (int eb = 0; eb < PA; eb += PBATCH) {
+                double v[PBATCH];
+#pragma unroll 2
+                for (int t = a0; t < a1; ++t) {
+                    int64_t ld;
+                    const double *X = term_base(p.a_code[t], p.A, p.lda, p.mL, p.kL, p.slotA,
+                                                p.slotA_stride, p.kL, &ld);
+                    const double cf = p.a_coef[t];
+                    double x[PBATCH];
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e) {
+                        const int idx = pt + WS_PRODUCERS * (eb + e);
+                        const int64_t gr = row0 + idx / BK, gk = k0 + idx % BK;
+                        x[e] = (gr < p.mL && gk < p.kL) ? __ldg(X + gr * ld + gk) : 0.0;
+                    }
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e)
+                        v[e] = (t == a0) ? chain_first(cf, x[e]) : chain_step(v[e], cf, x[e]);
+                }
+                if (a0 == a1) {
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e) v[e] = 0.0;
+                }
+#pragma unroll
+                for (int e = 0; e < PBATCH; ++e) {
+                    const int idx = pt + WS_PRODUCERS * (eb + e);
+                    as[(idx % BK) * LDA_S + idx / BK] = v[e];
+                }
+            }
+            for (int eb = 0; eb < PB; eb += PBATCH) {
+                double v[PBATCH];
+#pragma unroll 2
+                for (int t = b0; t < b1; ++t) {
+                    int64_t ld;
+                    const double *X = term_base(p.b_code[t], p.B, p.ldb, p.kL, p.nL, p.slotB,
+                                                p.slotB_stride, p.nL, &ld);
+                    const double cf = p.b_coef[t];
+                    double x[PBATCH];
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e) {
+                        const int idx = pt + WS_PRODUCERS * (eb + e);
+                        const int64_t gk = k0 + idx / BN, gc = col0 + idx % BN;
+                        x[e] = (gk < p.kL && gc < p.nL) ? __ldg(X + gk * ld + gc) : 0.0;
+                    }
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e)
+                        v[e] = (t == b0) ? chain_first(cf, x[e]) : chain_step(v[e], cf, x[e]);
+                }
+                if (b0 == b1) {
+#pragma unroll
+                    for (int e = 0; e < PBATCH; ++e) v[e] = 0.0;
+                }
+#pragma unroll
+                for (int e = 0; e < PBATCH; ++e) {
+                    const int idx = pt + WS_PRODUCERS * (eb + e);
+                    bs[(idx / BN) * BN + idx % BN] = v[e];
+                }
+            }
+            __threadfence_block();
+            named_arrive(1 + st, WS_THREADS);                                  // FULL[st]
+        }
+        return;
+    }
+
+    // ---------------- consumers ----------------
+    const int tx = tid & 15, ty = tid >> 4;
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int st = int(c % WS_STAGES);
+        named_sync(1 + st, WS_THREADS);                                        // FULL[st]
+        const double *as = smem + st * STAGE + ty;
+        const double *bs = smem + st * STAGE + BK * LDA_S + tx;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[TM];
+#pragma unroll
+            for (int i = 0; i < TM; ++i) a[i] = as[kk * LDA_S + 16 * i];
+            // B fragment in halves keeps the live register set small
+#pragma unroll
+            for (int jh = 0; jh < TN; jh += TN / 2) {
+                double b[TN / 2];
+#pragma unroll
+                for (int j = 0; j < TN / 2; ++j) b[j] = bs[kk * BN + 16 * (jh + j)];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN / 2; ++j)
+                        acc[i][jh + j] = fma(a[i], b[j], acc[i][jh + j]);
+            }
+        }
+        if (c + WS_STAGES < nchunks) named_arrive(1 + WS_STAGES + st, WS_THREADS);  // EMPTY[st]
+    }
+
+    if (p.epi == EPI_WORKSPACE) {
+        double *out = p.wsM + leaf * p.mL * p.nL;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gr = row0 + ty + 16 * i;
+            if (gr >= p.mL) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gc = col0 + tx + 16 * j;
+                if (gc < p.nL) out[gr * p.nL + gc] = acc[i][j];
+            }
+        }
+        return;
+    }
+    const int c0 = p.c_ptr[leaf], c1 = p.c_ptr[leaf + 1];
+    for (int t = c0; t < c1; ++t) {
+        const int code = p.c_code[t];
+        const double w = p.c_coef[t];
+        if (w == 0.0) continue;
+        double *Cb = p.C + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t gr = row0 + ty + 16 * i;
+            if (gr >= p.mL) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t gc = col0 + tx + 16 * j;
+                if (gc >= p.nL) continue;
+                const double v = (w == 1.0) ? acc[i][j] : (w == -1.0 ? -acc[i][j] : w * acc[i][j]);
+                if (p.epi == EPI_ATOMIC)
+                    atomicAdd(Cb + gr * p.ldc + gc, v);
+                else
+                    Cb[gr * p.ldc + gc] = v;
+            }
+        }
+    }
+}
+
 // S_r (or T_r) = sum_t coef_t X_t for every slot, written once.
 __global__ void form_slots_kernel(const double *X, int64_t ldx, int64_t rows, int64_t cols,
                                   int64_t slot_base, const int *slot_leaf, const int *ptr,
@@ -261,16 +443,23 @@ __device__ int g_unit_ptr[2] = {0, 1};
 __device__ int g_unit_code[1] = {0};
 __device__ double g_unit_coef[1] = {1.0};
 
-template <int TM, int TN>
+template <int TM, int TN, bool WS>
 cudaError_t launch_tile(const KParams &base, int64_t leaves, cudaStream_t s, int *launches) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
-    const size_t smem = sizeof(double) * 2 * BK * ((BM + 1) + BN);
+    const size_t smem = WS ? sizeof(double) * WS_STAGES * BK * ((BM + 1) + BN)
+                           : sizeof(double) * 2 * BK * ((BM + 1) + BN);
+    void (*kern)(const KParams);
+    if constexpr (WS)
+        kern = leaf_gemm_ws<TM, TN>;
+    else
+        kern = leaf_gemm<TM, TN>;
+    const int threads = WS ? WS_THREADS : THREADS;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !configured[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(leaf_gemm<TM, TN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
@@ -282,7 +471,7 @@ cudaError_t launch_tile(const KParams &base, int64_t leaves, cudaStream_t s, int
         const int64_t cnt = leaves - lb < 65535 ? leaves - lb : 65535;
         p.leaf_base = lb;
         dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)cnt);
-        leaf_gemm<TM, TN><<<grid, THREADS, smem, s>>>(p);
+        kern<<<grid, threads, smem, s>>>(p);
         ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -343,12 +532,12 @@ cudaError_t launch_leaf_gemm(const LeafLaunch &a, cudaStream_t s, int *launches)
     p.slotB = a.slotB; p.slotB_stride = a.slotB_stride;
     p.wsM = a.wsM; p.epi = a.epi;
     switch (a.tile) {
-        case FMM_TILE_96x96: return launch_tile<6, 6>(p, a.leaves, s, launches);
-        case FMM_TILE_64x64: return launch_tile<4, 4>(p, a.leaves, s, launches);
-        case FMM_TILE_32x32: return launch_tile<2, 2>(p, a.leaves, s, launches);
-        case FMM_TILE_128x64: return launch_tile<8, 4>(p, a.leaves, s, launches);
-        case FMM_TILE_64x128: return launch_tile<4, 8>(p, a.leaves, s, launches);
-        default: return launch_tile<8, 8>(p, a.leaves, s, launches);
+        case FMM_TILE_96x96: return launch_tile<6, 6, true>(p, a.leaves, s, launches);
+        case FMM_TILE_64x64: return launch_tile<4, 4, false>(p, a.leaves, s, launches);
+        case FMM_TILE_32x32: return launch_tile<2, 2, false>(p, a.leaves, s, launches);
+        case FMM_TILE_128x64: return launch_tile<8, 4, true>(p, a.leaves, s, launches);
+        case FMM_TILE_64x128: return launch_tile<4, 8, true>(p, a.leaves, s, launches);
+        default: return launch_tile<8, 8, true>(p, a.leaves, s, launches);
     }
 }
 

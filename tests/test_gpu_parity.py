@@ -156,7 +156,7 @@ def test_leading_dimensions_and_views():
 def test_side_stream_and_launch_count():
     import torch
     p = fmm.Plan("strassen_222_7", levels=1)
-    A, B = synth.operands(258, 258, 258, 12, kind="integer")
+    A, B = synth.operands(259, 257, 261, 12, kind="integer")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         Ad, Bd = to_dev(A), to_dev(B)
