@@ -215,6 +215,7 @@ def main():
     ap.add_argument("--plan", default=None, help="NAME:LEVELS to skip the candidate trial")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--quick", action="store_true", help="small CPU sample, no e2e")
+    ap.add_argument("--fused-only", action="store_true", help="only the fused scheme as candidates")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -252,14 +253,16 @@ def main():
         return float(np.linalg.norm(got - Cs) / np.linalg.norm(Cs))
 
     # candidates (algorithm files that exist), plus the classical comparator
-    cands = [(a, L) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))]
+    schemes = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "wo_st": fmm.FLAG_FUSED_W}
+    cands = [(a, L, sc) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
+             for sc in (schemes if not args.fused_only else ["fused"])]
     if args.plan:
-        a, L = args.plan.split(":")
-        cands = [(a, int(L))]
+        parts = args.plan.split(":")
+        cands = [(parts[0], int(parts[1]), parts[2] if len(parts) > 2 else "fused")]
     plans = {}
     results = []
-    for a, L in cands:
-        p = fmm.Plan(a, levels=L)
+    for a, L, sc in cands:
+        p = fmm.Plan(a, levels=L, flags=schemes[sc])
         wsz = p.workspace_size(m, k, n)
         wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
         f = (lambda p=p, wsb=wsb: fmm.gemm(p, Ad, Bd, C=Cd, workspace=wsb, stream=stream))
@@ -267,8 +270,11 @@ def main():
         torch.cuda.synchronize()
         ms = time_steps(torch, f, 1, stream)
         err = rel_err_rows(Cd)
-        plans[(a, L)] = (p, wsb, f)
-        results.append({"plan": f"{a} L{L}", "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err})
+        label = f"{a} L{L} {sc}"
+        plans[label] = p
+        results.append({"plan": label, "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err,
+                        "workspace_bytes": wsz})
+        del f, wsb
     fc = (lambda: fmm.classical_gemm(Ad, Bd, C=Cd, stream=stream))
     fc()
     torch.cuda.synchronize()
@@ -278,8 +284,11 @@ def main():
     best = min((r for r in results if r["plan"] != "classical"), key=lambda r: r["ms"], default=None)
     if best is None:
         raise SystemExit("no fast-algorithm plan available for this workload")
-    a, L = best["plan"].rsplit(" L", 1)
-    p, wsb, f = plans[(a, int(L))]
+    p = plans[best["plan"]]
+    plans.clear()
+    wsz = p.workspace_size(m, k, n)
+    wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+    f = (lambda: fmm.gemm(p, Ad, Bd, C=Cd, workspace=wsb, stream=stream))
 
     # ---- timed region: K steps of the headline plan
     for _ in range(args.warmup):
@@ -343,7 +352,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic uniform[-1,1] (PCG64 seed 1410)",
             "config": {"workload": wl["desc"], "m": m, "k": k, "n": n, "plan": best["plan"],
-                       "scheme": "fused S/T staging + fused W epilogue", "leaf_tile": "auto",
+                       "scheme": ("S/T fused into operand staging" if p.flags & fmm.FLAG_FUSED_ST
+                                  else "S/T written once to workspace")
+                                 + ", W fused into the epilogue", "leaf_tile": "auto",
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "rel_err_F": err, "rel_err_note": "e_F over the cpu_baseline's sampled rows vs the FP64 oracle",

@@ -6,9 +6,8 @@ tensor and recovering discrete coefficients.  Here the discrete structure
 comes first: a random walk over schemes modulo 2 (a flip rewrites two terms
 sharing a factor, x(y1)(z1) + x(y2)(z2) = x(y1+y2)(z1) + x(y2)(z1+z2) mod 2;
 a reduction merges two terms sharing two factors; terms with a zero factor
-vanish) from the classical scheme until the rank is R.  The support of that
-scheme is then handed to the damped least-squares solver of ``search.py``
-is lifted from GF(2) to the 2-adic integers (Hensel lifting: one linear solve
+vanish) from the classical scheme until the rank is R.  The scheme is then
+lifted from GF(2) to the 2-adic integers (Hensel lifting: one linear solve
 over GF(2) per bit) and each coefficient is read back as a small rational by
 rational reconstruction; the result is checked exactly against Eq. (2).
 
@@ -195,10 +194,31 @@ def attempt(args):
     terms, info = walk_mod2(M, K, N, R, seed, steps, plateau)
     if terms is None:
         return seed, None, "no mod-2 scheme"
-    ex = lift(M, K, N, terms, seed)
-    if ex is None:
-        return seed, None, f"mod-2 rank {len(terms)} after {info} steps, lift failed"
-    return seed, ex, f"mod-2 rank {len(terms)} after {info} steps, lifted"
+    # not every mod-2 scheme lifts; keep flipping at rank R and retry the lift
+    # (a short lift favours small coefficients, a long one general rationals)
+    rng = random.Random(seed + 1)
+    for tries in range(40):
+        for bits in (8, 40):
+            ex = lift(M, K, N, terms, bits=bits)
+            if ex is not None:
+                return seed, ex, f"mod-2 rank {len(terms)} after {info} steps, lifted (try {tries})"
+        for _ in range(2000):
+            groups = {}
+            for idx, t in enumerate(terms):
+                for mode in range(3):
+                    groups.setdefault((mode, t[mode]), []).append(idx)
+            pairs = [(k[0], v) for k, v in groups.items() if len(v) >= 2]
+            if not pairs:
+                break
+            mode, members = rng.choice(pairs)
+            i, j = rng.sample(members, 2)
+            p_, q_ = [m for m in range(3) if m != mode]
+            if rng.random() < 0.5:
+                p_, q_ = q_, p_
+            terms[i][p_] ^= terms[j][p_]
+            terms[j][q_] ^= terms[i][q_]
+            terms = reduce_mod2(terms)
+    return seed, None, f"mod-2 rank {len(terms)} after {info} steps, lift failed"
 
 
 def main():
