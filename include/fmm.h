@@ -200,6 +200,38 @@ fmm_status fmm_gemm_host(fmm_plan_t plan, const double *A, int64_t lda,
                          int64_t m, int64_t k, int64_t n, void *dev_ws,
                          size_t ws_bytes, void *stream);
 
+/*
+ * fmm_gemm_noalloc - C = A B like fmm_gemm, for callers that cannot allocate
+ * device memory when they need a product (no counterpart in the paper).
+ *
+ * Who needs it: code that runs while a CUDA graph is being captured, hosts
+ * whose device memory is reserved up front by another allocator, and paths
+ * that cannot afford the implicit device synchronisation of cudaMalloc.  The
+ * call allocates nothing and takes no workspace: it runs the plan's stored-
+ * product scheme (leaf products M_r kept, then C formed in a fixed order,
+ * bitwise reproducible) with S_r/T_r formed in the leaf kernel, and keeps the
+ * unrolled plan lists and the leaf products in one file-scope device array of
+ * FMM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
+ * the process exits.  The plan's own scheme flags are ignored.
+ *
+ * Limit: the lists plus R^L * (m'/M^L) * (n'/N^L) * 8 bytes of products must
+ * fit in FMM_NOALLOC_SCRATCH_BYTES; larger problems return
+ * FMM_ERR_UNSUPPORTED before anything is enqueued.  Products that take the
+ * classical path (no fast core) need no scratch.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call reuses the same array (its contents are whatever the last call left;
+ * each call rewrites all of it that it reads), so calls whose GPU work
+ * overlaps - on different streams or host threads - race and must be
+ * serialised by the caller.  The lists are copied from host memory on
+ * `stream` each call.  Pointer, size and error rules are those of fmm_gemm.
+ */
+#define FMM_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+fmm_status fmm_gemm_noalloc(fmm_plan_t plan, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, double *C, int64_t ldc,
+                            int64_t m, int64_t k, int64_t n, void *stream);
+
 /* Number of CUDA kernel launches the last fmm_gemm / fmm_classical_gemm
    call on this host thread enqueued (for launch accounting). */
 int fmm_last_launch_count(void);

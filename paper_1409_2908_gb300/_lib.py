@@ -52,6 +52,8 @@ def _declare(L):
     L.fmm_gemm_host.argtypes = [c_p, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64,
                                 c_p, ctypes.c_size_t, c_p]
     L.fmm_gemm_host.restype = st
+    L.fmm_gemm_noalloc.argtypes = [c_p, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64, c_p]
+    L.fmm_gemm_noalloc.restype = st
     L.fmm_last_launch_count.argtypes = []
     L.fmm_last_launch_count.restype = ctypes.c_int
     L.fmm_timing_enable.argtypes = [ctypes.c_int]
