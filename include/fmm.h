@@ -65,6 +65,13 @@ enum {
        clear the leaf products M_r go to the workspace and a write-once pass
        forms C in a fixed order (bitwise reproducible). */
     FMM_FLAG_FUSED_W = 1u << 1,
+    /* With FUSED_ST and/or FUSED_W clear: form the unfused parts one
+       recursive level at a time, as the recursion of Section 3.1 does (the
+       S_r of level l are combinations of the level l-1 S_r, and C blocks of
+       level l-1 are combined from the level-l products), instead of from the
+       fully unrolled per-leaf chains.  Needs more workspace, but the addition
+       count grows like sum_l R^(l-1) nnz rather than nnz^L. */
+    FMM_FLAG_LEVELWISE = 1u << 2,
     FMM_FLAGS_DEFAULT = FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W
 };
 

@@ -21,6 +21,7 @@ FMM_ERR_TIMEOUT = -6
 FMM_PREC_FP64 = 0
 FLAG_FUSED_ST = 1
 FLAG_FUSED_W = 2
+FLAG_LEVELWISE = 4
 FLAGS_DEFAULT = FLAG_FUSED_ST | FLAG_FUSED_W
 
 TILES = {"auto": 0, "128x128": 1, "96x96": 2, "64x64": 3, "32x32": 4, "128x64": 5, "64x128": 6}

@@ -94,21 +94,49 @@ Geometry geometry(const fmm_plan *p, int64_t m, int64_t k, int64_t n) {
 
 struct WsLayout {
     size_t slotA = 0, slotB = 0, prod = 0, total = 0;
+    // level-by-level scheme: offsets of each level's S, T and product buffers
+    std::vector<size_t> lvS, lvT, lvP;
 };
 
 WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     WsLayout w;
     if (!g.fast) return w;
     size_t off = 0;
+    const bool lw = p->flags & FMM_FLAG_LEVELWISE;
     if (!(p->flags & FMM_FLAG_FUSED_ST)) {
-        w.slotA = off;
-        off = align256(off + size_t(p->slots_a) * g.mL * g.kL * 8);
-        w.slotB = off;
-        off = align256(off + size_t(p->slots_b) * g.kL * g.nL * 8);
+        if (lw) {
+            int64_t cnt = 1;
+            for (int l = 1; l <= p->L; ++l) {
+                cnt *= p->R;
+                w.lvS.push_back(off);
+                off = align256(off + size_t(cnt) * (g.mp / ipow(p->M, l)) * (g.kp / ipow(p->K, l)) * 8);
+            }
+            cnt = 1;
+            for (int l = 1; l <= p->L; ++l) {
+                cnt *= p->R;
+                w.lvT.push_back(off);
+                off = align256(off + size_t(cnt) * (g.kp / ipow(p->K, l)) * (g.np / ipow(p->N, l)) * 8);
+            }
+        } else {
+            w.slotA = off;
+            off = align256(off + size_t(p->slots_a) * g.mL * g.kL * 8);
+            w.slotB = off;
+            off = align256(off + size_t(p->slots_b) * g.kL * g.nL * 8);
+        }
     }
     if (!(p->flags & FMM_FLAG_FUSED_W)) {
-        w.prod = off;
-        off = align256(off + size_t(p->leaves) * g.mL * g.nL * 8);
+        if (lw) {
+            int64_t cnt = 1;
+            for (int l = 1; l <= p->L; ++l) {
+                cnt *= p->R;
+                w.lvP.push_back(off);
+                off = align256(off + size_t(cnt) * (g.mp / ipow(p->M, l)) * (g.np / ipow(p->N, l)) * 8);
+            }
+            w.prod = w.lvP.back();
+        } else {
+            w.prod = off;
+            off = align256(off + size_t(p->leaves) * g.mL * g.nL * 8);
+        }
     }
     w.total = off;
     return w;
@@ -172,9 +200,30 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
     const bool fused_w = p->flags & FMM_FLAG_FUSED_W;
     cudaError_t e;
 
+    const bool lw = p->flags & FMM_FLAG_LEVELWISE;
     // write-once S_r and T_r (unfused scheme)
     double *slotA = nullptr, *slotB = nullptr;
-    if (!fused_st) {
+    if (!fused_st && lw) {
+        // one recursive level at a time: level l forms R^l operands from R^(l-1)
+        const double *pa = A, *pb = B;
+        int64_t pld_a = lda, pld_b = ldb, pst_a = 0, pst_b = 0, parents = 1;
+        for (int l = 1; l <= p->L; ++l) {
+            const int64_t ml = g.mp / ipow(p->M, l), kl = g.kp / ipow(p->K, l), nl = g.np / ipow(p->N, l);
+            double *oa = (double *)(wsb + wl.lvS[l - 1]);
+            double *ob = (double *)(wsb + wl.lvT[l - 1]);
+            if ((e = launch_level_form(pa, pld_a, pst_a, parents, ml, kl, p->R, p->dev.lu_ptr,
+                                       p->dev.lu_code, p->dev.lu_coef, oa, s, launches)) != cudaSuccess)
+                return cuda_status(e);
+            if ((e = launch_level_form(pb, pld_b, pst_b, parents, kl, nl, p->R, p->dev.lv_ptr,
+                                       p->dev.lv_code, p->dev.lv_coef, ob, s, launches)) != cudaSuccess)
+                return cuda_status(e);
+            pa = oa; pld_a = kl; pst_a = ml * kl;
+            pb = ob; pld_b = nl; pst_b = kl * nl;
+            parents *= p->R;
+        }
+        slotA = (double *)(wsb + wl.lvS.back());
+        slotB = (double *)(wsb + wl.lvT.back());
+    } else if (!fused_st) {
         slotA = (double *)(wsb + wl.slotA);
         slotB = (double *)(wsb + wl.slotB);
         if (p->slots_a > 0 &&
@@ -203,16 +252,31 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
     LeafLaunch L{};
     L.A = A; L.lda = lda; L.B = B; L.ldb = ldb; L.C = C; L.ldc = ldc;
     L.mL = g.mL; L.kL = g.kL; L.nL = g.nL; L.leaves = p->leaves;
+    // Operand chains and the epilogue coefficient must agree: normalised
+    // chains (first coefficient 1) pair with W * sA * sB; true-valued
+    // operands (level-wise slots, or raw chains feeding level-wise W) pair
+    // with the plain W.
+    bool raw_values = false;
     if (fused_st) {
-        L.a_ptr = p->dev.a_ptr; L.a_code = p->dev.a_code; L.a_coef = p->dev.a_coef;
-        L.b_ptr = p->dev.b_ptr; L.b_code = p->dev.b_code; L.b_coef = p->dev.b_coef;
+        raw_values = lw && !fused_w;
+        L.a_ptr = p->dev.a_ptr; L.a_code = p->dev.a_code;
+        L.a_coef = raw_values ? p->dev.a_coef_raw : p->dev.a_coef;
+        L.b_ptr = p->dev.b_ptr; L.b_code = p->dev.b_code;
+        L.b_coef = raw_values ? p->dev.b_coef_raw : p->dev.b_coef;
+    } else if (lw) {
+        raw_values = true;
+        L.a_ptr = p->dev.ua_ptr; L.a_code = p->dev.leaf_slot; L.a_coef = p->dev.u_one;
+        L.b_ptr = p->dev.ub_ptr; L.b_code = p->dev.leaf_slot; L.b_coef = p->dev.u_one;
+        L.slotA = slotA; L.slotA_stride = g.mL * g.kL;
+        L.slotB = slotB; L.slotB_stride = g.kL * g.nL;
     } else {
         L.a_ptr = p->dev.ua_ptr; L.a_code = p->dev.ua_code; L.a_coef = p->dev.u_one;
         L.b_ptr = p->dev.ub_ptr; L.b_code = p->dev.ub_code; L.b_coef = p->dev.u_one;
         L.slotA = slotA; L.slotA_stride = g.mL * g.kL;
         L.slotB = slotB; L.slotB_stride = g.kL * g.nL;
     }
-    L.c_ptr = p->dev.c_ptr; L.c_code = p->dev.c_code; L.c_coef = p->dev.c_coef;
+    L.c_ptr = p->dev.c_ptr; L.c_code = p->dev.c_code;
+    L.c_coef = raw_values ? p->dev.c_coef_raw : p->dev.c_coef;
     double *wsM = fused_w ? nullptr : (double *)(wsb + wl.prod);
     L.wsM = wsM;
     L.epi = fused_w ? EPI_ATOMIC : EPI_WORKSPACE;
@@ -226,11 +290,28 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
             (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp, g.np,
                                   FMM_TILE_AUTO, s, launches)) != cudaSuccess)
             return cuda_status(e);
-        const int64_t gridN = ipow(p->N, p->L), blocks = ipow(p->M, p->L) * gridN;
-        if ((e = launch_w_pass(C, ldc, g.mL, g.nL, int(gridN), blocks, p->dev.cq_ptr,
-                               p->dev.cq_leaf, p->dev.cq_coef, wsM, kfringe ? 1 : 0, s,
-                               launches)) != cudaSuccess)
-            return cuda_status(e);
+        if (lw) {
+            // combine level by level, from the leaf products up to C
+            int64_t parents = ipow(p->R, p->L - 1);
+            for (int l = p->L; l >= 1; --l) {
+                const int64_t ml = g.mp / ipow(p->M, l), nl = g.np / ipow(p->N, l);
+                const double *child = (const double *)(wsb + wl.lvP[l - 1]);
+                double *parent = l == 1 ? C : (double *)(wsb + wl.lvP[l - 2]);
+                const int64_t pld = l == 1 ? ldc : nl * p->N;
+                const int64_t pst = l == 1 ? 0 : (ml * p->M) * (nl * p->N);
+                if ((e = launch_level_w(child, ml, nl, p->R, p->N, p->M * p->N, parent, pld, pst,
+                                        parents, p->dev.lw_ptr, p->dev.lw_r, p->dev.lw_coef,
+                                        (l == 1 && kfringe) ? 1 : 0, s, launches)) != cudaSuccess)
+                    return cuda_status(e);
+                parents /= p->R;
+            }
+        } else {
+            const int64_t gridN = ipow(p->N, p->L), blocks = ipow(p->M, p->L) * gridN;
+            if ((e = launch_w_pass(C, ldc, g.mL, g.nL, int(gridN), blocks, p->dev.cq_ptr,
+                                   p->dev.cq_leaf, p->dev.cq_coef, wsM, kfringe ? 1 : 0, s,
+                                   launches)) != cudaSuccess)
+                return cuda_status(e);
+        }
     }
     // fringe rows and columns (Section 3.4)
     if (g.mp < m &&
@@ -271,7 +352,7 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
     if (levels < 0 || levels > 6) return FMM_ERR_ARG;
     if (prec != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
-    if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W)) return FMM_ERR_ARG;
+    if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE)) return FMM_ERR_ARG;
     bool representable = true;
     if (!brent_exact(M, K, N, R, U, V, W, &representable))
         return representable ? FMM_ERR_INVALID_ALGORITHM : FMM_ERR_UNSUPPORTED;

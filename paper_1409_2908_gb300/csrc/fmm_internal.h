@@ -44,6 +44,16 @@ struct DevicePlan {
     // per C block: CSR over (leaf, coefficient) for the write-once W pass
     int *cq_ptr = nullptr, *cq_leaf = nullptr;
     double *cq_coef = nullptr;
+    // level-by-level scheme: the base [[U,V,W]] as lists
+    int *lu_ptr = nullptr, *lu_code = nullptr;   // per r: A blocks (a<<16|b)
+    double *lu_coef = nullptr;
+    int *lv_ptr = nullptr, *lv_code = nullptr;   // per r: B blocks
+    double *lv_coef = nullptr;
+    int *lw_ptr = nullptr, *lw_r = nullptr;      // per C block q: (r, W_qr)
+    double *lw_coef = nullptr;
+    int *leaf_slot = nullptr;                    // code -(r+1) for every leaf
+    double *c_coef_raw = nullptr;                // unscaled flattened W
+    double *a_coef_raw = nullptr, *b_coef_raw = nullptr;  // unnormalised chains
     void *blob = nullptr;                        // single allocation
 };
 
@@ -56,6 +66,7 @@ struct fmm_plan {
     fmm_tile tile = FMM_TILE_AUTO;
     int64_t leaves = 1;
     fmm::TermList a, b, c;                   // unscaled, as exported
+    std::vector<double> U, V, W;             // the base case, row-major
     // normalised lists (first coefficient of each S_r/T_r is 1, the scale
     // folded into the epilogue coefficient)
     std::vector<double> a_norm, b_norm, c_scaled;
@@ -106,6 +117,14 @@ cudaError_t launch_w_pass(double *C, int64_t ldc, int64_t mL, int64_t nL, int gr
                           int64_t blocks, const int *cq_ptr, const int *cq_leaf,
                           const double *cq_coef, const double *wsM, int accumulate,
                           cudaStream_t s, int *launches);
+cudaError_t launch_level_form(const double *parent, int64_t parent_ld, int64_t parent_stride,
+                              int64_t parents, int64_t rows, int64_t cols, int R, const int *ptr,
+                              const int *code, const double *coef, double *out, cudaStream_t s,
+                              int *launches);
+cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int R, int gridN,
+                           int MN, double *parent, int64_t parent_ld, int64_t parent_stride,
+                           int64_t parents, const int *w_ptr, const int *w_r, const double *w_coef,
+                           int accumulate, cudaStream_t s, int *launches);
 cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
                              double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                              int tile, cudaStream_t s, int *launches);

@@ -439,6 +439,59 @@ __global__ void w_pass_kernel(double *C, int64_t ldc, int64_t mL, int64_t nL, in
     }
 }
 
+// One recursive level of S (or T) formation, write-once: output o = s*R + r
+// is sum_i U_ir (parent s)_i, where block i = (a, b) of parent s starts at
+// row a*rows, column b*cols.  Parents are A itself (level 1) or the previous
+// level's outputs, stored contiguously with leading dimension cols*K.
+__global__ void level_form_kernel(const double *parent, int64_t pld, int64_t pstride, int64_t rows,
+                                  int64_t cols, int R, int64_t o_base, const int *ptr,
+                                  const int *code, const double *coef, double *out) {
+    const int64_t o = o_base + blockIdx.y;
+    const int64_t s = o / R;
+    const int r = int(o % R);
+    const double *P = parent + s * pstride;
+    const int t0 = ptr[r], t1 = ptr[r + 1];
+    double *O = out + o * rows * cols;
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+            double v = 0.0;
+            for (int t = t0; t < t1; ++t) {
+                const int cd = code[t];
+                const double x = __ldg(P + ((int64_t)(cd >> 16) * rows + i) * pld +
+                                       (int64_t)(cd & 0xffff) * cols + j);
+                v = (t == t0) ? chain_first(coef[t], x) : chain_step(v, coef[t], x);
+            }
+            O[i * cols + j] = v;
+        }
+    }
+}
+
+// One recursive level of the W combination: parent s, block q = (a, c) of
+// its M x N grid = (its old value if accumulate) + sum_r W_qr child_{s*R+r}.
+__global__ void level_w_kernel(const double *child, int64_t rows, int64_t cols, int R, int gridN,
+                               int MN, double *parent, int64_t pld, int64_t pstride, int64_t o_base,
+                               const int *w_ptr, const int *w_r, const double *w_coef,
+                               int accumulate) {
+    const int64_t o = o_base + blockIdx.y;
+    const int64_t s = o / MN;
+    const int q = int(o % MN);
+    const int a = q / gridN, c = q % gridN;
+    double *Pout = parent + s * pstride + (int64_t)a * rows * pld + (int64_t)c * cols;
+    const int t0 = w_ptr[q], t1 = w_ptr[q + 1];
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        for (int64_t j = threadIdx.x; j < cols; j += blockDim.x) {
+            double v = accumulate ? Pout[i * pld + j] : 0.0;
+            bool first = !accumulate;
+            for (int t = t0; t < t1; ++t) {
+                const double x = __ldg(child + ((s * R + w_r[t]) * rows + i) * cols + j);
+                v = first ? chain_first(w_coef[t], x) : chain_step(v, w_coef[t], x);
+                first = false;
+            }
+            Pout[i * pld + j] = v;
+        }
+    }
+}
+
 __device__ int g_unit_ptr[2] = {0, 1};
 __device__ int g_unit_code[1] = {0};
 __device__ double g_unit_coef[1] = {1.0};
@@ -566,6 +619,43 @@ cudaError_t launch_w_pass(double *C, int64_t ldc, int64_t mL, int64_t nL, int gr
         const int64_t cnt = blocks - qb < 65535 ? blocks - qb : 65535;
         w_pass_kernel<<<dim3(gx, (unsigned)cnt), 256, 0, s>>>(C, ldc, mL, nL, gridN, qb, cq_ptr,
                                                                cq_leaf, cq_coef, wsM, accumulate);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_level_form(const double *parent, int64_t parent_ld, int64_t parent_stride,
+                              int64_t parents, int64_t rows, int64_t cols, int R, const int *ptr,
+                              const int *code, const double *coef, double *out, cudaStream_t s,
+                              int *launches) {
+    const int64_t outs = parents * R;
+    const unsigned gx = (unsigned)(rows < 1024 ? rows : 1024);
+    const unsigned bx = cols >= 256 ? 256 : (cols >= 128 ? 128 : 64);
+    for (int64_t ob = 0; ob < outs; ob += 65535) {
+        const int64_t cnt = outs - ob < 65535 ? outs - ob : 65535;
+        level_form_kernel<<<dim3(gx, (unsigned)cnt), bx, 0, s>>>(parent, parent_ld, parent_stride,
+                                                                 rows, cols, R, ob, ptr, code, coef, out);
+        ++*launches;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int R, int gridN,
+                           int MN, double *parent, int64_t parent_ld, int64_t parent_stride,
+                           int64_t parents, const int *w_ptr, const int *w_r, const double *w_coef,
+                           int accumulate, cudaStream_t s, int *launches) {
+    const int64_t outs = parents * MN;
+    const unsigned gx = (unsigned)(rows < 1024 ? rows : 1024);
+    const unsigned bx = cols >= 256 ? 256 : (cols >= 128 ? 128 : 64);
+    for (int64_t ob = 0; ob < outs; ob += 65535) {
+        const int64_t cnt = outs - ob < 65535 ? outs - ob : 65535;
+        level_w_kernel<<<dim3(gx, (unsigned)cnt), bx, 0, s>>>(child, rows, cols, R, gridN, MN, parent,
+                                                              parent_ld, parent_stride, ob, w_ptr,
+                                                              w_r, w_coef, accumulate);
         ++*launches;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

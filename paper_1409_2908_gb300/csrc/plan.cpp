@@ -194,6 +194,9 @@ fmm_status build_plan(fmm_plan *p, int M, int K, int N, int R, const double *U,
         if (side > 32768) return FMM_ERR_UNSUPPORTED;
     }
     p->leaves = leaves;
+    p->U.assign(U, U + (size_t)M * K * R);
+    p->V.assign(V, V + (size_t)K * N * R);
+    p->W.assign(W, W + (size_t)M * N * R);
     unroll(U, M, K, R, L, &p->a);
     unroll(V, K, N, R, L, &p->b);
     unroll(W, M, N, R, L, &p->c);
@@ -287,6 +290,41 @@ fmm_status upload_plan(fmm_plan *p) {
             for (int64_t t = p->c.ptr[r]; t < p->c.ptr[r + 1]; ++t) c_coef_dev[t] = 0.0;
     }
 
+    // level-by-level scheme: base lists of U and V by column, W by row
+    const int R = p->R, MK = p->M * p->K, KN = p->K * p->N, MN = p->M * p->N;
+    std::vector<int> lu_ptr(R + 1, 0), lv_ptr(R + 1, 0), lw_ptr(MN + 1, 0), lu_code, lv_code, lw_r;
+    std::vector<double> lu_coef, lv_coef, lw_coef;
+    for (int r = 0; r < R; ++r) {
+        for (int i = 0; i < MK; ++i)
+            if (p->U[(size_t)i * R + r] != 0.0) {
+                lu_code.push_back(((i / p->K) << 16) | (i % p->K));
+                lu_coef.push_back(p->U[(size_t)i * R + r]);
+            }
+        lu_ptr[r + 1] = int(lu_code.size());
+        for (int j = 0; j < KN; ++j)
+            if (p->V[(size_t)j * R + r] != 0.0) {
+                lv_code.push_back(((j / p->N) << 16) | (j % p->N));
+                lv_coef.push_back(p->V[(size_t)j * R + r]);
+            }
+        lv_ptr[r + 1] = int(lv_code.size());
+    }
+    for (int q = 0; q < MN; ++q) {
+        for (int r = 0; r < R; ++r)
+            if (p->W[(size_t)q * R + r] != 0.0) {
+                lw_r.push_back(r);
+                lw_coef.push_back(p->W[(size_t)q * R + r]);
+            }
+        lw_ptr[q + 1] = int(lw_r.size());
+    }
+    std::vector<int> leaf_slot(leaves);
+    for (int64_t r = 0; r < leaves; ++r) leaf_slot[r] = -int(r + 1);
+    std::vector<double> c_coef_raw(p->c.coef);
+    for (int64_t r = 0; r < leaves; ++r) {
+        const bool live = p->a.ptr[r + 1] > p->a.ptr[r] && p->b.ptr[r + 1] > p->b.ptr[r];
+        if (!live)
+            for (int64_t t = p->c.ptr[r]; t < p->c.ptr[r + 1]; ++t) c_coef_raw[t] = 0.0;
+    }
+
     Blob bl;
     const size_t o_a_ptr = bl.add<int>(leaves + 1), o_a_code = bl.add<int>(na), o_a_coef = bl.add<double>(na);
     const size_t o_b_ptr = bl.add<int>(leaves + 1), o_b_code = bl.add<int>(nb), o_b_coef = bl.add<double>(nb);
@@ -295,6 +333,14 @@ fmm_status upload_plan(fmm_plan *p) {
     const size_t o_one = bl.add<double>(leaves);
     const size_t o_sa = bl.add<int>(sa_leaf.size()), o_sb = bl.add<int>(sb_leaf.size());
     const size_t o_cq_ptr = bl.add<int>(cblocks + 1), o_cq_leaf = bl.add<int>(nc), o_cq_coef = bl.add<double>(nc);
+    const size_t o_lu_ptr = bl.add<int>(R + 1), o_lu_code = bl.add<int>(lu_code.size() + 1),
+                 o_lu_coef = bl.add<double>(lu_coef.size() + 1);
+    const size_t o_lv_ptr = bl.add<int>(R + 1), o_lv_code = bl.add<int>(lv_code.size() + 1),
+                 o_lv_coef = bl.add<double>(lv_coef.size() + 1);
+    const size_t o_lw_ptr = bl.add<int>(MN + 1), o_lw_r = bl.add<int>(lw_r.size() + 1),
+                 o_lw_coef = bl.add<double>(lw_coef.size() + 1);
+    const size_t o_leaf_slot = bl.add<int>(leaves), o_c_raw = bl.add<double>(nc);
+    const size_t o_a_raw = bl.add<double>(na), o_b_raw = bl.add<double>(nb);
 
     std::vector<unsigned char> host(bl.bytes, 0);
     auto put = [&](size_t off, const void *src, size_t n) { if (n) std::memcpy(host.data() + off, src, n); };
@@ -316,6 +362,19 @@ fmm_status upload_plan(fmm_plan *p) {
     put(o_cq_ptr, cq_ptr.data(), cq_ptr.size() * 4);
     put(o_cq_leaf, cq_leaf.data(), cq_leaf.size() * 4);
     put(o_cq_coef, cq_coef.data(), cq_coef.size() * 8);
+    put(o_lu_ptr, lu_ptr.data(), lu_ptr.size() * 4);
+    put(o_lu_code, lu_code.data(), lu_code.size() * 4);
+    put(o_lu_coef, lu_coef.data(), lu_coef.size() * 8);
+    put(o_lv_ptr, lv_ptr.data(), lv_ptr.size() * 4);
+    put(o_lv_code, lv_code.data(), lv_code.size() * 4);
+    put(o_lv_coef, lv_coef.data(), lv_coef.size() * 8);
+    put(o_lw_ptr, lw_ptr.data(), lw_ptr.size() * 4);
+    put(o_lw_r, lw_r.data(), lw_r.size() * 4);
+    put(o_lw_coef, lw_coef.data(), lw_coef.size() * 8);
+    put(o_leaf_slot, leaf_slot.data(), leaf_slot.size() * 4);
+    put(o_c_raw, c_coef_raw.data(), c_coef_raw.size() * 8);
+    put(o_a_raw, p->a.coef.data(), p->a.coef.size() * 8);
+    put(o_b_raw, p->b.coef.data(), p->b.coef.size() * 8);
 
     void *blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, bl.bytes);
@@ -339,6 +398,11 @@ fmm_status upload_plan(fmm_plan *p) {
     d.u_one = (double *)(b + o_one);
     d.sa_leaf = (int *)(b + o_sa); d.sb_leaf = (int *)(b + o_sb);
     d.cq_ptr = (int *)(b + o_cq_ptr); d.cq_leaf = (int *)(b + o_cq_leaf); d.cq_coef = (double *)(b + o_cq_coef);
+    d.lu_ptr = (int *)(b + o_lu_ptr); d.lu_code = (int *)(b + o_lu_code); d.lu_coef = (double *)(b + o_lu_coef);
+    d.lv_ptr = (int *)(b + o_lv_ptr); d.lv_code = (int *)(b + o_lv_code); d.lv_coef = (double *)(b + o_lv_coef);
+    d.lw_ptr = (int *)(b + o_lw_ptr); d.lw_r = (int *)(b + o_lw_r); d.lw_coef = (double *)(b + o_lw_coef);
+    d.leaf_slot = (int *)(b + o_leaf_slot); d.c_coef_raw = (double *)(b + o_c_raw);
+    d.a_coef_raw = (double *)(b + o_a_raw); d.b_coef_raw = (double *)(b + o_b_raw);
     return FMM_OK;
 }
 

@@ -135,6 +135,12 @@ def test_workspace_sizes():
     assert p.workspace_size(512, 512, 512) == (5 + 5 + 7) * 256 * 256 * 8
     p = fmm.Plan("strassen_222_7", levels=2, flags=fmm.FLAG_FUSED_ST)
     assert p.workspace_size(1024, 1024, 1024) == 49 * 256 * 256 * 8
+    # level by level: every level's S, T and products are kept
+    p = fmm.Plan("strassen_222_7", levels=2, flags=fmm.FLAG_LEVELWISE)
+    per_operand = 7 * 512 * 512 * 8 + 49 * 256 * 256 * 8
+    assert p.workspace_size(1024, 1024, 1024) == 3 * per_operand
+    p = fmm.Plan("strassen_222_7", levels=2, flags=fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W)
+    assert p.workspace_size(1024, 1024, 1024) == 2 * per_operand
 
 
 def test_gemm_argument_errors_before_launch():

@@ -27,7 +27,10 @@ pytestmark = pytest.mark.gpu
 TOL_F = 1e-11
 ALGS = sorted(os.path.basename(p)[:-4] for p in glob.glob(os.path.join(fmm.ALGORITHM_DIR, "*.fmm")))
 SCHEMES = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "write_once": 0,
-           "fused_st_only": fmm.FLAG_FUSED_ST, "fused_w_only": fmm.FLAG_FUSED_W}
+           "fused_st_only": fmm.FLAG_FUSED_ST, "fused_w_only": fmm.FLAG_FUSED_W,
+           "levelwise": fmm.FLAG_LEVELWISE,
+           "levelwise_fused_w": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W,
+           "levelwise_fused_st": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_ST}
 
 
 def run(plan, A, B):
@@ -98,11 +101,12 @@ def test_fast_integer_exact_ragged(name, levels, scheme):
 
 @pytest.mark.parametrize("name", ALGS)
 @pytest.mark.parametrize("levels", [1, 2, 3])
-def test_fast_uniform_tolerance(name, levels):
+@pytest.mark.parametrize("scheme", ["fused", "levelwise", "levelwise_fused_w"])
+def test_fast_uniform_tolerance(name, levels, scheme):
     M, K, N, R = base_case(name)
     if R ** levels > 20000:
         pytest.skip("too many leaves for this size")
-    p = fmm.Plan(name, levels=levels)
+    p = fmm.Plan(name, levels=levels, flags=SCHEMES[scheme])
     m, k, n = M ** levels * 40 + 5, K ** levels * 40 + 1, N ** levels * 40 + 7
     A, B = synth.operands(m, k, n, 2000 + levels)
     C = oracle.gemm(A, B)
@@ -110,8 +114,9 @@ def test_fast_uniform_tolerance(name, levels):
     assert e <= TOL_F, e
 
 
-def test_write_once_w_is_deterministic():
-    p = fmm.Plan("strassen_222_7", levels=2, flags=fmm.FLAG_FUSED_ST)
+@pytest.mark.parametrize("flags", [fmm.FLAG_FUSED_ST, fmm.FLAG_LEVELWISE, 0])
+def test_stored_product_schemes_are_deterministic(flags):
+    p = fmm.Plan("strassen_222_7", levels=2, flags=flags)
     A, B = synth.operands(600, 520, 610, 9)
     c1 = run(p, A, B)
     c2 = run(p, A, B)
