@@ -62,9 +62,21 @@ def scheme_desc(flags, fmm):
     return st + "; " + w
 
 
+def measured_bf16_peak():
+    """Sustained dense bf16 TFLOP/s measured on this machine (the residue GEMM
+    runs inside a longer step), else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback sustained bf16 1.7 PFLOP/s (of fallback)"
+
+
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1409_2908_gb300 import replicas
+    return replicas.env()
 
 
 class ClockSampler:
@@ -124,20 +136,15 @@ class ClockSampler:
 
 
 def sync_all(torch, ws):
+    from paper_1409_2908_gb300 import replicas
     torch.cuda.synchronize()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
 
 
 def max_over_ranks(torch, ws, x):
-    if ws == 1:
-        return x
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_1409_2908_gb300 import replicas
+    return replicas.max_over_ranks(x, device="cuda")
 
 
 def time_steps(torch, fn, steps, stream):
@@ -225,6 +232,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--quick", action="store_true", help="small CPU sample, no e2e")
     ap.add_argument("--fused-only", action="store_true", help="only the fused scheme as candidates")
+    ap.add_argument("--moduli", type=int, default=15, help="moduli of the emulated-FP64 variant")
+    ap.add_argument("--precisions", default="fp64",
+                    help="comma list of leaf precisions to try: fp64, ozaki_bf16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -264,18 +274,29 @@ def main():
     # candidates (algorithm files that exist), plus the classical comparator
     schemes = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "wo_st": fmm.FLAG_FUSED_W,
                "lw_st": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W, "lw": fmm.FLAG_LEVELWISE}
-    cands = [(a, L, sc) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
-             for sc in (schemes if not args.fused_only else ["fused"])]
+    precs = args.precisions.split(",")
+    cands = []
+    for prec in precs:
+        if prec == "fp64":
+            cands += [(a, L, sc, prec) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
+                      for sc in (schemes if not args.fused_only else ["fused"])]
+        else:
+            # emulated FP64: the classical product (0 levels) and the fast plans, level by level
+            cands += [("strassen_222_7", 0, "lw", prec)]
+            cands += [(a, L, "lw", prec) for a, L in wl["cands"]
+                      if os.path.exists(fmm.algorithm_path(a)) and L <= 2]
     if args.plan:
         parts = args.plan.split(":")
-        cands = [(parts[0], int(parts[1]), parts[2] if len(parts) > 2 else "fused")]
+        cands = [(parts[0], int(parts[1]), parts[2] if len(parts) > 2 else "fused",
+                  parts[3] if len(parts) > 3 else "fp64")]
     plans = {}
     results = []
-    for a, L, sc in cands:
-        p = fmm.Plan(a, levels=L, flags=schemes[sc])
+    for a, L, sc, prec in cands:
+        p = fmm.Plan(a, levels=L, flags=schemes[sc], precision=prec,
+                     moduli=args.moduli if prec != "fp64" else None)
         inf = p.info()
         chain = (inf["nnz_a_terms"] + inf["nnz_b_terms"]) / (2.0 * inf["leaves"])
-        if sc in ("fused", "wo_st") and chain > 8 and len(cands) > 1:
+        if prec == "fp64" and sc in ("fused", "wo_st") and chain > 8 and len(cands) > 1:
             # unrolled chains this long are known to lose to the level-wise scheme
             continue
         wsz = p.workspace_size(m, k, n)
@@ -285,7 +306,7 @@ def main():
         torch.cuda.synchronize()
         ms = time_steps(torch, f, 1, stream)
         err = rel_err_rows(Cd)
-        label = f"{a} L{L} {sc}"
+        label = f"{a} L{L} {sc}" + ("" if prec == "fp64" else f" {prec}")
         plans[label] = p
         results.append({"plan": label, "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err,
                         "workspace_bytes": wsz})
@@ -328,19 +349,31 @@ def main():
     sync_all(torch, ws)
     ms_c = max_over_ranks(torch, ws, time_steps(torch, fc, args.steps, stream)) / args.steps
 
-    # roofline of the dominant kernel (the grouped leaf GEMM)
+    # roofline of the dominant kernel
     mL = (m // info["M"] ** info["levels"])
     kL = (k // info["K"] ** info["levels"])
     nL = (n // info["N"] ** info["levels"])
-    leaf_flops = 2.0 * info["leaves"] * mL * kL * nL
     leaf_avg = leaf_ms / max(leaf_n, 1)
-    achieved = leaf_flops / leaf_avg / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-            "kernel": "leaf_gemm (grouped FP64 DFMA GEMM over all R^L leaves)",
-            "peak_source": "FP64 DFMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clocks)",
-            "algorithmic_flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg,
-            "leaf_share_of_step": leaf_avg / ms_step}
+    if p.precision == "fp64":
+        leaf_flops = 2.0 * info["leaves"] * mL * kL * nL
+        achieved = leaf_flops / leaf_avg / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "leaf_gemm (grouped FP64 DFMA GEMM over all R^L leaves)",
+                "peak_source": "FP64 DFMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clocks)",
+                "algorithmic_flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg,
+                "leaf_share_of_step": leaf_avg / ms_step}
+    else:
+        nmod = args.moduli
+        kpad = -(-kL // 64) * 64
+        leaf_flops = 2.0 * info["leaves"] * nmod * mL * kpad * nL
+        achieved = leaf_flops / leaf_avg / 1e9
+        peak, src = measured_bf16_peak()
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"residue_gemm (tcgen05 kind::f16, bf16 residues x {nmod} moduli, all leaves)",
+                "peak_source": src, "algorithmic_flops_per_launch": leaf_flops,
+                "leaf_ms_avg": leaf_avg, "leaf_share_of_step": leaf_avg / ms_step}
 
     # end to end through the host entry point (pinned buffers, copies timed)
     e2e = None
@@ -365,7 +398,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic uniform[-1,1] (PCG64 seed 1410)",
+            "vs_baseline": None,
+            "dtype": "f64" if p.precision == "fp64" else f"bf16 residues x {args.moduli} (CRT-emulated f64)",
+            "data": "synthetic uniform[-1,1] (PCG64 seed 1410)",
             "config": {"workload": wl["desc"], "m": m, "k": k, "n": n, "plan": best["plan"],
                        "scheme": scheme_desc(p.flags, fmm), "leaf_tile": "auto",
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",

@@ -51,7 +51,16 @@ typedef enum {
 } fmm_status;
 
 typedef enum {
-    FMM_PREC_FP64 = 0 /* FP64 leaves (DFMA), FP64 combinations */
+    FMM_PREC_FP64 = 0,       /* FP64 leaves (DFMA), FP64 combinations */
+    /* Leaf products emulated to FP64 accuracy on the tensor cores: each leaf
+       operand is scaled per row (S) / column (T) to beta-bit integers, the
+       integer product is computed exactly modulo N pairwise coprime moduli
+       <= 256 with bfloat16 residues and FP32 accumulation (tcgen05), and
+       rebuilt by the Chinese remainder theorem in FP64.  S/T formation, the W
+       combination and the fringe stay FP64.  Error: truncation of the
+       scaled operands to beta bits, beta = floor((log2 prod p - 1 -
+       log2 k_L)/2) (about 51 bits for N = 15, k_L = 16384). */
+    FMM_PREC_OZAKI_BF16 = 3
 } fmm_precision;
 
 /* Execution-scheme flags (fmm_plan_create / fmm_plan_load `flags`). */
@@ -123,6 +132,18 @@ fmm_status fmm_plan_load(fmm_plan_t *out, const char *fmm_file, int levels,
    make sure no work using the plan is still running. */
 void fmm_plan_destroy(fmm_plan_t plan);
 
+/* Number of moduli N (3..16, default 15) of an FMM_PREC_OZAKI_BF16 plan;
+   more moduli give more bits (beta grows by about 4 per modulus) and cost
+   one more residue GEMM each.  FMM_ERR_ARG outside the range or for an FP64
+   plan.  Not thread-safe against concurrent fmm_gemm calls on the plan. */
+fmm_status fmm_plan_set_moduli(fmm_plan_t plan, int n_moduli);
+
+/* Synchronise the current device and report whether any bounded device-side
+   wait of this library gave up since the last call (FMM_ERR_TIMEOUT; the
+   flag is then cleared), FMM_OK otherwise, FMM_ERR_CUDA if the device
+   reports an error. */
+fmm_status fmm_check_device_error(void);
+
 /* Choose the leaf GEMM tile shape used by later fmm_gemm calls with this
    plan (default FMM_TILE_AUTO).  Not thread-safe against concurrent
    fmm_gemm calls on the same plan. */
@@ -182,6 +203,28 @@ fmm_status fmm_gemm(fmm_plan_t plan, const double *A, int64_t lda,
                     const double *B, int64_t ldb, double *C, int64_t ldc,
                     int64_t m, int64_t k, int64_t n, void *workspace,
                     size_t ws_bytes, void *stream);
+
+/*
+ * fmm_gemm_batched - `count` independent products C_b = A_b B_b of one shape
+ * with one plan, all R^L leaves of all products in ONE grouped leaf launch
+ * (S/T formed in the leaf kernel, W applied by FP64 reductions into C,
+ * whatever the plan's scheme flags say; FP64 plans only).
+ *
+ * A, B, C: HOST arrays of `count` device pointers (each as in fmm_gemm,
+ * sharing lda, ldb, ldc); count 1..65535.  C_b may not overlap any A or B.
+ * workspace: at least fmm_workspace_size_batched() bytes, 256-byte aligned;
+ * it receives a device copy of the pointer arrays.  Fringe products of
+ * shapes the block sizes do not divide are launched per product.
+ * Errors: as fmm_gemm; FMM_ERR_UNSUPPORTED for an emulated-precision plan.
+ */
+fmm_status fmm_workspace_size_batched(fmm_plan_t plan, int64_t count, int64_t m,
+                                      int64_t k, int64_t n, size_t *bytes);
+fmm_status fmm_gemm_batched(fmm_plan_t plan, int64_t count,
+                            const double *const *A, int64_t lda,
+                            const double *const *B, int64_t ldb,
+                            double *const *C, int64_t ldc, int64_t m, int64_t k,
+                            int64_t n, void *workspace, size_t ws_bytes,
+                            void *stream);
 
 /*
  * fmm_classical_gemm - C = A B by the library's classical FP64 GEMM (the

@@ -8,8 +8,8 @@ implements, in plain integer arithmetic.
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Definition (our reading, fixed here):
-  * beta = floor((log2 P - 1 - log2 k) / 2) with P the product of the moduli:
-    the largest integer width for which |A'B'| < P/2 is guaranteed;
+  * beta = the largest width (at most 62) with k 2^(2 beta + 1) < P, P the
+    product of the moduli: then |A'B'| < P/2 is guaranteed;
   * row exponents s_i = beta - 1 - floor(log2 max_j |A_ij|) (0 for a zero row),
     A'_ij = trunc(A_ij 2^s_i); column exponents t_j and B'_ij likewise;
   * Z = A' B' exactly (integers); residues Z mod p for each modulus p are what
@@ -33,8 +33,13 @@ def moduli(n):
 
 
 def beta_bits(n, k):
+    """Largest beta (at most 62) with k 2^(2 beta + 1) < P, i.e. every
+    |A'B'| <= k (2^beta)^2 stays below P/2."""
     P = math.prod(moduli(n))
-    return int(math.floor((math.log2(P) - 1 - math.log2(k)) / 2))
+    beta = 62
+    while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
+        beta -= 1
+    return beta
 
 
 def balanced(x, p):

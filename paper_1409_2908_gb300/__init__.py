@@ -19,6 +19,8 @@ FMM_ERR_CUDA = -5
 FMM_ERR_TIMEOUT = -6
 
 FMM_PREC_FP64 = 0
+FMM_PREC_OZAKI_BF16 = 3
+PRECISIONS = {"fp64": FMM_PREC_FP64, "ozaki_bf16": FMM_PREC_OZAKI_BF16}
 FLAG_FUSED_ST = 1
 FLAG_FUSED_W = 2
 FLAG_LEVELWISE = 4
@@ -75,8 +77,10 @@ class Plan:
     """A fast-multiplication plan: base case [[U,V,W]] unrolled over `levels`
     recursive steps (fmm_plan_create / fmm_plan_load)."""
 
-    def __init__(self, algorithm=None, levels=1, flags=FLAGS_DEFAULT, tile="auto", factors=None):
+    def __init__(self, algorithm=None, levels=1, flags=FLAGS_DEFAULT, tile="auto", factors=None,
+                 precision="fp64", moduli=None):
         L = _lib.lib()
+        prec = PRECISIONS[precision]
         h = ctypes.c_void_p()
         if factors is not None:
             import numpy as np
@@ -86,17 +90,20 @@ class Plan:
             W = np.ascontiguousarray(W, dtype=np.float64)
             R = U.shape[1]
             st = L.fmm_plan_create(ctypes.byref(h), M, K, N, R, U.ctypes.data, V.ctypes.data,
-                                   W.ctypes.data, levels, FMM_PREC_FP64, flags)
+                                   W.ctypes.data, levels, prec, flags)
         else:
             st = L.fmm_plan_load(ctypes.byref(h), algorithm_path(algorithm).encode(), levels,
-                                 FMM_PREC_FP64, flags)
+                                 prec, flags)
         _check(st, "plan")
         self._h = h
         self.levels = levels
         self.flags = flags
         self.name = algorithm if factors is None else "custom"
+        self.precision = precision
         if tile != "auto":
             self.set_tile(tile)
+        if moduli is not None:
+            _check(L.fmm_plan_set_moduli(self._h, int(moduli)), "set_moduli")
 
     def set_tile(self, tile):
         _check(_lib.lib().fmm_plan_set_tile(self._h, TILES[tile]), "set_tile")
@@ -178,6 +185,41 @@ def gemm(plan, A, B, C=None, workspace=None, stream=None):
     return C
 
 
+def gemm_batched(plan, As, Bs, Cs=None, workspace=None, stream=None):
+    """C_b = A_b B_b for equally shaped CUDA float64 tensors, all leaves of all
+    products in one grouped launch (fmm_gemm_batched).  Returns the C list."""
+    import torch
+    count = len(As)
+    if count != len(Bs) or count == 0:
+        raise ValueError("need equally many A and B")
+    mats = [_mat(a, "A") for a in As]
+    matsb = [_mat(b, "B") for b in Bs]
+    m, k = mats[0][2], mats[0][3]
+    n = matsb[0][3]
+    if Cs is None:
+        Cs = [torch.empty((m, n), dtype=torch.float64, device=As[0].device) for _ in range(count)]
+    matsc = [_mat(c, "C") for c in Cs]
+    lda, ldb, ldc = mats[0][1], matsb[0][1], matsc[0][1]
+    if any(x[1] != lda or x[2:] != (m, k) for x in mats) or any(x[1] != ldb or x[2:] != (k, n) for x in matsb) \
+            or any(x[1] != ldc or x[2:] != (m, n) for x in matsc):
+        raise ValueError("batched operands must share shape and leading dimension")
+    arr = ctypes.c_void_p * count
+    pa = arr(*[x[0].value for x in mats])
+    pb = arr(*[x[0].value for x in matsb])
+    pc = arr(*[x[0].value for x in matsc])
+    need = ctypes.c_size_t()
+    _check(_lib.lib().fmm_workspace_size_batched(plan.handle, count, m, k, n, ctypes.byref(need)),
+           "workspace_size_batched")
+    if workspace is None:
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=As[0].device)
+    st = _lib.lib().fmm_gemm_batched(plan.handle, count, pa, lda, pb, ldb, pc, ldc, m, k, n,
+                                     ctypes.c_void_p(workspace.data_ptr()),
+                                     workspace.numel() * workspace.element_size(),
+                                     _stream_handle(stream))
+    _check(st, "fmm_gemm_batched")
+    return Cs
+
+
 def classical_gemm(A, B, C=None, stream=None):
     """C = A B with the library's classical FP64 GEMM (fmm_classical_gemm)."""
     import torch
@@ -218,6 +260,11 @@ def host_workspace_size(plan, m, k, n):
 def last_launch_count():
     """Kernel launches enqueued by the last gemm / classical_gemm call on this thread."""
     return _lib.lib().fmm_last_launch_count()
+
+
+def check_device_error():
+    """Raise FmmError(FMM_ERR_TIMEOUT) if a bounded device wait gave up."""
+    _check(_lib.lib().fmm_check_device_error(), "device")
 
 
 def timing_enable(on=True):

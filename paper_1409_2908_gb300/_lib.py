@@ -54,6 +54,15 @@ def _declare(L):
     L.fmm_gemm_host.restype = st
     L.fmm_gemm_noalloc.argtypes = [c_p, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64, c_p]
     L.fmm_gemm_noalloc.restype = st
+    L.fmm_workspace_size_batched.argtypes = [c_p, c_i64, c_i64, c_i64, c_i64, ctypes.POINTER(ctypes.c_size_t)]
+    L.fmm_workspace_size_batched.restype = st
+    L.fmm_gemm_batched.argtypes = [c_p, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64,
+                                   c_p, ctypes.c_size_t, c_p]
+    L.fmm_gemm_batched.restype = st
+    L.fmm_plan_set_moduli.argtypes = [c_p, ctypes.c_int]
+    L.fmm_plan_set_moduli.restype = st
+    L.fmm_check_device_error.argtypes = []
+    L.fmm_check_device_error.restype = st
     L.fmm_last_launch_count.argtypes = []
     L.fmm_last_launch_count.restype = ctypes.c_int
     L.fmm_timing_enable.argtypes = [ctypes.c_int]

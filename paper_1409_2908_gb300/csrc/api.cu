@@ -37,12 +37,21 @@ struct Timing {
 };
 thread_local Timing t_timing;
 
+}  // namespace
+
+namespace fmm {
 cudaEvent_t timing_mark(cudaStream_t s) {
     if (!t_timing.on) return nullptr;
     cudaEvent_t e = t_timing.next();
     if (e) cudaEventRecord(e, s);
     return e;
 }
+void timing_unmark() {
+    if (t_timing.used > 0) --t_timing.used;
+}
+}  // namespace fmm
+
+namespace {
 
 int64_t ipow(int64_t b, int e) {
     int64_t r = 1;
@@ -89,21 +98,31 @@ Geometry geometry(const fmm_plan *p, int64_t m, int64_t k, int64_t n) {
     g.kL = g.kp / sk;
     g.nL = g.np / sn;
     g.fast = p->L > 0 && g.mp > 0 && g.kp > 0 && g.np > 0;
+    if (p->L == 0) {
+        g.mp = m; g.kp = k; g.np = n; g.mL = m; g.kL = k; g.nL = n;
+    }
     return g;
 }
 
 struct WsLayout {
-    size_t slotA = 0, slotB = 0, prod = 0, total = 0;
+    size_t slotA = 0, slotB = 0, prod = 0, oz = 0, total = 0;
     // level-by-level scheme: offsets of each level's S, T and product buffers
     std::vector<size_t> lvS, lvT, lvP;
 };
 
 WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     WsLayout w;
+    const bool oz = p->prec == FMM_PREC_OZAKI_BF16;
+    if (oz && p->L == 0) {
+        // the whole product is one emulated leaf
+        w.oz = 0;
+        w.total = ozaki_workspace(1, p->nmod, g.mp, g.kp, g.np);
+        return w;
+    }
     if (!g.fast) return w;
     size_t off = 0;
-    const bool lw = p->flags & FMM_FLAG_LEVELWISE;
-    if (!(p->flags & FMM_FLAG_FUSED_ST)) {
+    const bool lw = oz || (p->flags & FMM_FLAG_LEVELWISE);
+    if (oz || !(p->flags & FMM_FLAG_FUSED_ST)) {
         if (lw) {
             int64_t cnt = 1;
             for (int l = 1; l <= p->L; ++l) {
@@ -124,7 +143,7 @@ WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
             off = align256(off + size_t(p->slots_b) * g.kL * g.nL * 8);
         }
     }
-    if (!(p->flags & FMM_FLAG_FUSED_W)) {
+    if (oz || !(p->flags & FMM_FLAG_FUSED_W)) {
         if (lw) {
             int64_t cnt = 1;
             for (int l = 1; l <= p->L; ++l) {
@@ -137,6 +156,10 @@ WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
             w.prod = off;
             off = align256(off + size_t(p->leaves) * g.mL * g.nL * 8);
         }
+    }
+    if (oz) {
+        w.oz = off;
+        off = align256(off + ozaki_workspace(p->leaves, p->nmod, g.mL, g.kL, g.nL));
     }
     w.total = off;
     return w;
@@ -175,8 +198,69 @@ cudaError_t timed(cudaStream_t s, F &&f) {
     cudaEvent_t a = timing_mark(s);
     cudaError_t e = f();
     cudaEvent_t b = timing_mark(s);
-    if (a && !b) --t_timing.used;   // keep pairs aligned
+    if (a && !b) timing_unmark();   // keep pairs aligned
     return e;
+}
+
+// Emulated-FP64 leaves: FP64 level-by-level S/T, tensor-core residue
+// products, FP64 level-by-level W; classical FP64 fringe.
+fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, const double *A,
+                          int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
+                          int64_t m, int64_t k, int64_t n, char *wsb, cudaStream_t s,
+                          int *launches) {
+    cudaError_t e;
+    // (the timing pair, when enabled, brackets the residue GEMM inside)
+    if (p->L == 0)
+        return cuda_status(ozaki_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n, p->nmod,
+                                          wsb + wl.oz, s, launches));
+    const double *pa = A, *pb = B;
+    int64_t pld_a = lda, pld_b = ldb, pst_a = 0, pst_b = 0, parents = 1;
+    for (int l = 1; l <= p->L; ++l) {
+        const int64_t ml = g.mp / ipow(p->M, l), kl = g.kp / ipow(p->K, l), nl = g.np / ipow(p->N, l);
+        double *oa = (double *)(wsb + wl.lvS[l - 1]);
+        double *ob = (double *)(wsb + wl.lvT[l - 1]);
+        if ((e = launch_level_form(pa, pld_a, pst_a, parents, ml, kl, p->R, p->dev.lu_ptr,
+                                   p->dev.lu_code, p->dev.lu_coef, oa, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = launch_level_form(pb, pld_b, pst_b, parents, kl, nl, p->R, p->dev.lv_ptr,
+                                   p->dev.lv_code, p->dev.lv_coef, ob, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        pa = oa; pld_a = kl; pst_a = ml * kl;
+        pb = ob; pld_b = nl; pst_b = kl * nl;
+        parents *= p->R;
+    }
+    double *prod = (double *)(wsb + wl.lvP.back());
+    if ((e = ozaki_products(pa, g.kL, g.mL * g.kL, pb, g.nL, g.kL * g.nL, prod, g.nL,
+                            g.mL * g.nL, p->leaves, g.mL, g.kL, g.nL, p->nmod, wsb + wl.oz, s,
+                            launches)) != cudaSuccess)
+        return cuda_status(e);
+    const bool kfringe = g.kp < k;
+    if (kfringe &&
+        (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp, g.np,
+                              FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        return cuda_status(e);
+    int64_t lparents = ipow(p->R, p->L - 1);
+    for (int l = p->L; l >= 1; --l) {
+        const int64_t ml = g.mp / ipow(p->M, l), nl = g.np / ipow(p->N, l);
+        const double *child = (const double *)(wsb + wl.lvP[l - 1]);
+        double *parent = l == 1 ? C : (double *)(wsb + wl.lvP[l - 2]);
+        const int64_t pld = l == 1 ? ldc : nl * p->N;
+        const int64_t pst = l == 1 ? 0 : (ml * p->M) * (nl * p->N);
+        if ((e = launch_level_w(child, ml, nl, p->R, p->N, p->M * p->N, parent, pld, pst, lparents,
+                                p->dev.lw_ptr, p->dev.lw_r, p->dev.lw_coef, (l == 1 && kfringe) ? 1 : 0,
+                                s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        lparents /= p->R;
+    }
+    if (g.mp < m &&
+        (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
+                              FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        return cuda_status(e);
+    if (g.np < n &&
+        (e = launch_classical(A, lda, B + g.np, ldb, C + g.np, ldc, g.mp, k, n - g.np,
+                              FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        return cuda_status(e);
+    return FMM_OK;
 }
 
 // The fast core plus the classical fringe, all on one stream.
@@ -184,6 +268,16 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
                     size_t ws_bytes, cudaStream_t s, int *launches) {
     const Geometry g = geometry(p, m, k, n);
+    if (p->prec == FMM_PREC_OZAKI_BF16 && (p->L == 0 || g.fast)) {
+        // int32 drain sums stay below 2^31 for k_L <= 65536 (2^23 per 512-chunk)
+        if (g.kL > 65536) return FMM_ERR_UNSUPPORTED;
+        const WsLayout wl = ws_layout(p, g);
+        if (wl.total > 0 && (!ws || ws_bytes < wl.total)) return FMM_ERR_NO_MEMORY;
+        if (wl.total > 0 && ((uintptr_t)ws & 255)) return FMM_ERR_ARG;
+        const fmm_status us = ensure_uploaded(p);
+        if (us != FMM_OK) return us;
+        return run_gemm_ozaki(p, g, wl, A, lda, B, ldb, C, ldc, m, k, n, (char *)ws, s, launches);
+    }
     if (!g.fast)
         return cuda_status(timed(s, [&] {
             return launch_classical(A, lda, B, ldb, C, ldc, m, k, n, FMM_TILE_AUTO, s, launches);
@@ -351,7 +445,7 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (M < 1 || K < 1 || N < 1 || R < 1 || R > 4096) return FMM_ERR_ARG;
     if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
     if (levels < 0 || levels > 6) return FMM_ERR_ARG;
-    if (prec != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16) return FMM_ERR_UNSUPPORTED;
     if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE)) return FMM_ERR_ARG;
     bool representable = true;
     if (!brent_exact(M, K, N, R, U, V, W, &representable))
@@ -359,6 +453,7 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     fmm_plan *p = new (std::nothrow) fmm_plan();
     if (!p) return FMM_ERR_NO_MEMORY;
     p->flags = flags;
+    p->prec = prec;
     cudaGetDevice(&p->device);
     fmm_status st;
     try {
@@ -400,6 +495,18 @@ fmm_status fmm_plan_set_tile(fmm_plan_t p, fmm_tile tile) {
     if (!p || tile < FMM_TILE_AUTO || tile > FMM_TILE_64x128) return FMM_ERR_ARG;
     p->tile = tile;
     return FMM_OK;
+}
+
+fmm_status fmm_plan_set_moduli(fmm_plan_t p, int n_moduli) {
+    if (!p || p->prec != FMM_PREC_OZAKI_BF16 || n_moduli < 3 || n_moduli > 16) return FMM_ERR_ARG;
+    p->nmod = n_moduli;
+    return FMM_OK;
+}
+
+fmm_status fmm_check_device_error(void) {
+    int flag = 0;
+    if (read_device_error(&flag, true) != cudaSuccess) return FMM_ERR_CUDA;
+    return flag ? FMM_ERR_TIMEOUT : FMM_OK;
 }
 
 fmm_status fmm_plan_info(fmm_plan_t p, fmm_plan_info_t *info) {
@@ -447,6 +554,99 @@ fmm_status fmm_gemm(fmm_plan_t p, const double *A, int64_t lda, const double *B,
                   &launches);
     t_launches = launches;
     return st;
+}
+
+fmm_status fmm_workspace_size_batched(fmm_plan_t p, int64_t count, int64_t m, int64_t k,
+                                      int64_t n, size_t *bytes) {
+    if (!p || !bytes || count < 1 || m < 1 || k < 1 || n < 1) return FMM_ERR_ARG;
+    *bytes = align256(size_t(count) * 3 * sizeof(void *));
+    return FMM_OK;
+}
+
+fmm_status fmm_gemm_batched(fmm_plan_t p, int64_t count, const double *const *A, int64_t lda,
+                            const double *const *B, int64_t ldb, double *const *C, int64_t ldc,
+                            int64_t m, int64_t k, int64_t n, void *ws, size_t ws_bytes,
+                            void *stream) {
+    t_launches = 0;
+    if (!p || !A || !B || !C || count < 1 || count > 65535) return FMM_ERR_ARG;
+    if (p->prec != FMM_PREC_FP64) return FMM_ERR_UNSUPPORTED;
+    for (int64_t b = 0; b < count; ++b) {
+        fmm_status st = check_operands(A[b], lda, B[b], ldb, C[b], ldc, m, k, n);
+        if (st != FMM_OK) return st;
+        for (int64_t o = 0; o < count; ++o)
+            if (overlaps(C[b], span(m, n, ldc), A[o], span(m, k, lda)) ||
+                overlaps(C[b], span(m, n, ldc), B[o], span(k, n, ldb)))
+                return FMM_ERR_ARG;
+    }
+    const size_t need = align256(size_t(count) * 3 * sizeof(void *));
+    if (!ws || ws_bytes < need) return FMM_ERR_NO_MEMORY;
+    if ((uintptr_t)ws & 255) return FMM_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    cudaError_t e;
+    const Geometry g = geometry(p, m, k, n);
+    if (!g.fast) {
+        for (int64_t b = 0; b < count; ++b)
+            if ((e = launch_classical(A[b], lda, B[b], ldb, C[b], ldc, m, k, n, FMM_TILE_AUTO, s,
+                                      &launches)) != cudaSuccess) {
+                t_launches = launches;
+                return cuda_status(e);
+            }
+        t_launches = launches;
+        return FMM_OK;
+    }
+    {
+        const fmm_status us = ensure_uploaded(p);
+        if (us != FMM_OK) return us;
+    }
+    // pointer arrays to the device (pageable source: copied before return)
+    std::vector<const void *> host(size_t(count) * 3);
+    for (int64_t b = 0; b < count; ++b) {
+        host[b] = A[b];
+        host[count + b] = B[b];
+        host[2 * count + b] = C[b];
+    }
+    if ((e = cudaMemcpyAsync(ws, host.data(), host.size() * sizeof(void *), cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess)
+        return cuda_status(e);
+    const bool kfringe = g.kp < k;
+    for (int64_t b = 0; b < count; ++b) {
+        if (kfringe)
+            e = launch_classical(A[b] + g.kp, lda, B[b] + g.kp * ldb, ldb, C[b], ldc, g.mp, k - g.kp,
+                                 g.np, FMM_TILE_AUTO, s, &launches);
+        else
+            e = cudaMemset2DAsync(C[b], ldc * 8, 0, g.np * 8, g.mp, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    LeafLaunch L{};
+    L.lda = lda; L.ldb = ldb; L.ldc = ldc;
+    L.mL = g.mL; L.kL = g.kL; L.nL = g.nL; L.leaves = p->leaves;
+    L.a_ptr = p->dev.a_ptr; L.a_code = p->dev.a_code; L.a_coef = p->dev.a_coef;
+    L.b_ptr = p->dev.b_ptr; L.b_code = p->dev.b_code; L.b_coef = p->dev.b_coef;
+    L.c_ptr = p->dev.c_ptr; L.c_code = p->dev.c_code; L.c_coef = p->dev.c_coef;
+    L.epi = EPI_ATOMIC;
+    L.Ab = (const double *const *)ws;
+    L.Bb = (const double *const *)ws + count;
+    L.Cb = (double *const *)ws + 2 * count;
+    L.batch = count;
+    const double extra_a = double(p->a.row.size()) / double(p->leaves) - 1.0;
+    const double extra_b = double(p->b.row.size()) / double(p->leaves) - 1.0;
+    L.tile = resolve_tile(p->tile, g.mL, g.nL, g.kL, p->leaves * count, extra_a, extra_b,
+                          device_sms());
+    if ((e = timed(s, [&] { return launch_leaf_gemm(L, s, &launches); })) != cudaSuccess)
+        return cuda_status(e);
+    for (int64_t b = 0; b < count; ++b) {
+        if (g.mp < m &&
+            (e = launch_classical(A[b] + g.mp * lda, lda, B[b], ldb, C[b] + g.mp * ldc, ldc, m - g.mp,
+                                  k, n, FMM_TILE_AUTO, s, &launches)) != cudaSuccess)
+            return cuda_status(e);
+        if (g.np < n &&
+            (e = launch_classical(A[b], lda, B[b] + g.np, ldb, C[b] + g.np, ldc, g.mp, k, n - g.np,
+                                  FMM_TILE_AUTO, s, &launches)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    t_launches = launches;
+    return FMM_OK;
 }
 
 fmm_status fmm_classical_gemm(const double *A, int64_t lda, const double *B, int64_t ldb,

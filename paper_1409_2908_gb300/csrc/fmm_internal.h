@@ -75,6 +75,8 @@ struct fmm_plan {
     fmm::DevicePlan dev;                     // uploaded on first use
     std::mutex upload_mu;
     bool uploaded = false;
+    fmm_precision prec = FMM_PREC_FP64;
+    int nmod = 15;                           // moduli of the emulated-FP64 variant
 };
 
 namespace fmm {
@@ -105,6 +107,11 @@ struct LeafLaunch {
     double *wsM;                                 // leaf products (ld nL)
     int epi;                                     // EPI_* below
     int tile;                                    // fmm_tile (resolved)
+    // batched products (grid z): device arrays of per-product bases, or null
+    const double *const *Ab = nullptr;
+    const double *const *Bb = nullptr;
+    double *const *Cb = nullptr;
+    int64_t batch = 1;
 };
 enum { EPI_STORE = 0, EPI_ATOMIC = 1, EPI_WORKSPACE = 2 };
 
@@ -128,6 +135,20 @@ cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int 
 cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
                              double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                              int tile, cudaStream_t s, int *launches);
+// api.cu: CUDA event pairs around the dominant launch (fmm_timing_enable)
+cudaEvent_t timing_mark(cudaStream_t s);
+void timing_unmark();
+
+// ozaki.cu
+extern const int kOzakiModuli[20];
+int ozaki_beta(int nmod, int64_t k);
+size_t ozaki_workspace(int64_t leaves, int nmod, int64_t m, int64_t k, int64_t n);
+cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
+                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
+                           int64_t m, int64_t k, int64_t n, int nmod, void *ws, cudaStream_t s,
+                           int *launches);
+cudaError_t read_device_error(int *flag, bool clear);
+
 int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
                  double extra_a, double extra_b, int num_sms);
 void tile_dims(int tile, int *bm, int *bn);

@@ -42,6 +42,8 @@ struct KParams {
     int epi;
     int tiles_n;
     int64_t leaf_base;
+    // batched products: per blockIdx.z operand bases (device arrays) or null
+    const double *const *Ab; const double *const *Bb; double *const *Cb;
 };
 
 // Base address and leading dimension of one operand term.
@@ -83,6 +85,9 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
     const int tm = blockIdx.x / p.tiles_n, tn = blockIdx.x % p.tiles_n;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)tm * BM, col0 = (int64_t)tn * BN;
+    const double *opA = p.Ab ? p.Ab[blockIdx.z] : p.A;
+    const double *opB = p.Bb ? p.Bb[blockIdx.z] : p.B;
+    double *opC = p.Cb ? p.Cb[blockIdx.z] : p.C;
 
     const int a0 = p.a_ptr[leaf], a1 = p.a_ptr[leaf + 1];
     const int b0 = p.b_ptr[leaf], b1 = p.b_ptr[leaf + 1];
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
         for (int e = 0; e < EB; ++e) rb[e] = 0.0;
         for (int t = a0; t < a1; ++t) {
             int64_t ld;
-            const double *X = term_base(p.a_code[t], p.A, p.lda, p.mL, p.kL, p.slotA,
+            const double *X = term_base(p.a_code[t], opA, p.lda, p.mL, p.kL, p.slotA,
                                         p.slotA_stride, p.kL, &ld);
             const double c = p.a_coef[t];
 #pragma unroll
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
         }
         for (int t = b0; t < b1; ++t) {
             int64_t ld;
-            const double *X = term_base(p.b_code[t], p.B, p.ldb, p.kL, p.nL, p.slotB,
+            const double *X = term_base(p.b_code[t], opB, p.ldb, p.kL, p.nL, p.slotB,
                                         p.slotB_stride, p.nL, &ld);
             const double c = p.b_coef[t];
 #pragma unroll
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
         const int code = p.c_code[t];
         const double w = p.c_coef[t];
         if (w == 0.0) continue;
-        double *Cb = p.C + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
+        double *Cb = opC + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int64_t gr = row0 + ty + 16 * i;
@@ -244,6 +249,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
     const int64_t row0 = (int64_t)tm * BM, col0 = (int64_t)tn * BN;
     const int64_t nchunks = (p.kL + BK - 1) / BK;
     const int tid = threadIdx.x;
+    const double *opA = p.Ab ? p.Ab[blockIdx.z] : p.A;
+    const double *opB = p.Bb ? p.Bb[blockIdx.z] : p.B;
+    double *opC = p.Cb ? p.Cb[blockIdx.z] : p.C;
 
     if (tid >= WS_CONSUMERS) {
         // ---------------- producers ----------------
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
 #pragma unroll 2
                 for (int t = a0; t < a1; ++t) {
                     int64_t ld;
-                    const double *X = term_base(p.a_code[t], p.A, p.lda, p.mL, p.kL, p.slotA,
+                    const double *X = term_base(p.a_code[t], opA, p.lda, p.mL, p.kL, p.slotA,
                                                 p.slotA_stride, p.kL, &ld);
                     const double cf = p.a_coef[t];
                     double x[PBATCH];
@@ -293,7 +301,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
 #pragma unroll 2
                 for (int t = b0; t < b1; ++t) {
                     int64_t ld;
-                    const double *X = term_base(p.b_code[t], p.B, p.ldb, p.kL, p.nL, p.slotB,
+                    const double *X = term_base(p.b_code[t], opB, p.ldb, p.kL, p.nL, p.slotB,
                                                 p.slotB_stride, p.nL, &ld);
                     const double cf = p.b_coef[t];
                     double x[PBATCH];
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
         const int code = p.c_code[t];
         const double w = p.c_coef[t];
         if (w == 0.0) continue;
-        double *Cb = p.C + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
+        double *Cb = opC + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
             const int64_t gr = row0 + ty + 16 * i;
@@ -497,7 +505,8 @@ __device__ int g_unit_code[1] = {0};
 __device__ double g_unit_coef[1] = {1.0};
 
 template <int TM, int TN, bool WS>
-cudaError_t launch_tile(const KParams &base, int64_t leaves, cudaStream_t s, int *launches) {
+cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cudaStream_t s,
+                        int *launches) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     const size_t smem = WS ? sizeof(double) * WS_STAGES * BK * ((BM + 1) + BN)
                            : sizeof(double) * 2 * BK * ((BM + 1) + BN);
@@ -523,7 +532,7 @@ cudaError_t launch_tile(const KParams &base, int64_t leaves, cudaStream_t s, int
     for (int64_t lb = 0; lb < leaves; lb += 65535) {
         const int64_t cnt = leaves - lb < 65535 ? leaves - lb : 65535;
         p.leaf_base = lb;
-        dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)cnt);
+        dim3 grid((unsigned)(tiles_m * tiles_n), (unsigned)cnt, (unsigned)batch);
         kern<<<grid, threads, smem, s>>>(p);
         ++*launches;
         cudaError_t e = cudaGetLastError();
@@ -584,13 +593,16 @@ cudaError_t launch_leaf_gemm(const LeafLaunch &a, cudaStream_t s, int *launches)
     p.slotA = a.slotA; p.slotA_stride = a.slotA_stride;
     p.slotB = a.slotB; p.slotB_stride = a.slotB_stride;
     p.wsM = a.wsM; p.epi = a.epi;
+    p.Ab = a.Ab; p.Bb = a.Bb; p.Cb = a.Cb;
+    const int64_t batch = a.batch > 0 ? a.batch : 1;
+    if (batch > 65535) return cudaErrorInvalidValue;
     switch (a.tile) {
-        case FMM_TILE_96x96: return launch_tile<6, 6, true>(p, a.leaves, s, launches);
-        case FMM_TILE_64x64: return launch_tile<4, 4, false>(p, a.leaves, s, launches);
-        case FMM_TILE_32x32: return launch_tile<2, 2, false>(p, a.leaves, s, launches);
-        case FMM_TILE_128x64: return launch_tile<8, 4, true>(p, a.leaves, s, launches);
-        case FMM_TILE_64x128: return launch_tile<4, 8, true>(p, a.leaves, s, launches);
-        default: return launch_tile<8, 8, true>(p, a.leaves, s, launches);
+        case FMM_TILE_96x96: return launch_tile<6, 6, true>(p, a.leaves, batch, s, launches);
+        case FMM_TILE_64x64: return launch_tile<4, 4, false>(p, a.leaves, batch, s, launches);
+        case FMM_TILE_32x32: return launch_tile<2, 2, false>(p, a.leaves, batch, s, launches);
+        case FMM_TILE_128x64: return launch_tile<8, 4, true>(p, a.leaves, batch, s, launches);
+        case FMM_TILE_64x128: return launch_tile<4, 8, true>(p, a.leaves, batch, s, launches);
+        default: return launch_tile<8, 8, true>(p, a.leaves, batch, s, launches);
     }
 }
 

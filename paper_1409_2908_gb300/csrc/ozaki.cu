@@ -1,0 +1,573 @@
+// Emulated-FP64 leaf products on the tensor cores (precision variant
+// FMM_PREC_OZAKI_BF16).  For each leaf product S T (FP64):
+//
+//   1. split   scale row i of S by 2^s_i and column j of T by 2^t_j so the
+//              entries truncate to integers of beta bits, and write their
+//              balanced residues modulo each of N pairwise coprime moduli
+//              p <= 256 as bfloat16 (|r| <= 128: exact), K-major;
+//   2. gemm    Z_p = S'_p T'_p mod p on tcgen05 (kind::f16, FP32 accumulator in
+//              TMEM).  Products are < 2^14, so a k-chunk of 512 sums exactly in
+//              FP32; each chunk is drained into int32 registers through four
+//              rotating TMEM buffers while the next chunk is multiplied;
+//   3. crt     mixed-radix (Garner) digits of Z from its N residues, evaluated
+//              in FP64 by Horner's rule and scaled by 2^-(s_i + t_j).
+//
+// Operand tiles reach shared memory by TMA (128-byte swizzle) through a
+// 4-stage mbarrier ring; one thread issues the MMAs, one thread the loads,
+// four warps drain TMEM.  Every mbarrier wait is bounded: on timeout the CTA
+// records an error, stops issuing work and frees its TMEM.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "fmm_internal.h"
+
+namespace fmm {
+
+const int kOzakiModuli[20] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227,
+                              223, 217, 211, 199, 197, 193, 191, 181, 179, 173};
+
+__device__ int g_device_error = 0;   // set when a bounded wait gives up
+
+namespace {
+
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 4;
+constexpr int OZ_CHUNK_KB = 8;          // 8 x 64 = 512 k per exact FP32 chunk
+constexpr int OZ_TBUF = 4;              // TMEM accumulators of 128 columns
+constexpr int OZ_THREADS = 192;         // warps 0-3 drain, 4 loads, 5 issues MMAs
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2, OZ_B_BYTES = OZ_BN * OZ_BK * 2;
+constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
+constexpr int OZ_MAX_MOD = 20;
+
+__constant__ int c_mod[OZ_MAX_MOD];                       // moduli
+__constant__ int c_wmod[OZ_MAX_MOD][OZ_MAX_MOD];          // (prod_{l<i} p_l) mod p_j
+__constant__ int c_winv[OZ_MAX_MOD];                      // inverse of (prod_{l<j} p_l) mod p_j
+__constant__ unsigned c_magic[OZ_MAX_MOD];                // floor(2^32 / p)
+__constant__ unsigned c_r32[OZ_MAX_MOD];                  // 2^32 mod p
+
+// x mod p for any 32-bit x: quotient estimate from floor(2^32/p) is at most
+// one short, so one conditional subtraction finishes it.
+__device__ __forceinline__ unsigned mod_u32(unsigned x, int q) {
+    const unsigned p = (unsigned)c_mod[q];
+    unsigned r = x - __umulhi(x, c_magic[q]) * p;
+    return r >= p ? r - p : r;
+}
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t cnt) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(cnt) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+    const uint32_t a = su32(b);
+    for (long long i = 0; i < OZ_WAIT_LIMIT; ++i) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                 ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(su32(bar)) : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte
+// swizzle, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
+
+// Balanced residue of x (|x| < 2^31) modulo p.
+__device__ __forceinline__ int bal_mod(int x, int p) {
+    int r = x % p;
+    if (r < 0) r += p;
+    return r >= (p + 1) / 2 ? r - p : r;
+}
+
+// Z[z][row][col] (int8 balanced residues), z = leaf * nmod + modulus index.
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+             int8_t *Z, int64_t m, int64_t n, int kblocks, int nmod, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
+    uint64_t *empty = full + OZ_STAGES;
+    uint64_t *tfull = empty + OZ_STAGES;
+    uint64_t *tempty = tfull + OZ_TBUF;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + OZ_TBUF);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
+    const int p = c_mod[z % nmod];
+    const int nchunks = (kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < OZ_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 128); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(su32(tmem_slot)), "r"(OZ_TBUF * OZ_BN) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            for (int kb = 0; kb < kblocks; ++kb) {
+                const int s = kb % OZ_STAGES;
+                if (kb >= OZ_STAGES && !mbar_wait(&empty[s], ((kb / OZ_STAGES) - 1) & 1)) {
+                    atomicExch(err, 1);
+                    break;
+                }
+                unsigned char *sa = smem + s * OZ_STAGE_BYTES, *sb = sa + OZ_A_BYTES;
+                mbar_expect_tx(&full[s], OZ_STAGE_BYTES);
+                tma_load_3d(sa, &tmA, kb * OZ_BK, tm * OZ_BM, z, &full[s]);
+                tma_load_3d(sb, &tmB, kb * OZ_BK, tn * OZ_BN, z, &full[s]);
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                   ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
+            bool ok = true;
+            int kb = 0;
+            for (int c = 0; c < nchunks && ok; ++c) {
+                const int b = c % OZ_TBUF;
+                if (c >= OZ_TBUF && !mbar_wait(&tempty[b], ((c / OZ_TBUF) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc_tmem = tmem + (uint32_t)(b * OZ_BN);
+                const int kend = min(kblocks, (c + 1) * OZ_CHUNK_KB);
+                for (int first = 1; kb < kend; ++kb, first = 0) {
+                    const int s = kb % OZ_STAGES;
+                    if (!mbar_wait(&full[s], (kb / OZ_STAGES) & 1)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = su32(smem + s * OZ_STAGE_BYTES), b0 = a0 + OZ_A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < OZ_BK / 16; ++kk)
+                        mma_bf16(acc_tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                 (first && kk == 0) ? 0u : 1u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicExch(err, 1);
+        }
+    } else {
+        // warps 0-3: TMEM lanes 32*warp .. +31 hold rows of the tile
+        int acc[OZ_BN];
+#pragma unroll
+        for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c % OZ_TBUF;
+            if (!mbar_wait(&tfull[b], (c / OZ_TBUF) & 1)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * OZ_BN);
+#pragma unroll
+            for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+                uint32_t r[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                             : "r"(base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[c0 + j] += __float2int_rn(__uint_as_float(r[j]));
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[b]);
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(err, 1);
+        } else {
+            const int64_t row = (int64_t)tm * OZ_BM + warp * 32 + lane;
+            if (row < m) {
+                int8_t *out = Z + ((int64_t)z * m + row) * n + (int64_t)tn * OZ_BN;
+                const int64_t cols = min((int64_t)OZ_BN, n - (int64_t)tn * OZ_BN);
+#pragma unroll
+                for (int j = 0; j < OZ_BN; ++j)
+                    if (j < cols) out[j] = (int8_t)bal_mod(acc[j], p);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TBUF * OZ_BN) : "memory");
+}
+
+// Exponent e with 2^e <= |x| < 2^(e+1) for normal x; subnormals go through
+// frexp.
+__device__ __forceinline__ int ilog2_abs(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int be = int((b >> 52) & 0x7ff);
+    if (be != 0) return be - 1023;
+    int e;
+    frexp(x, &e);
+    return e - 1;
+}
+
+// trunc(x * 2^s) as an integer, by shifting the significand (no FP64 ops).
+__device__ __forceinline__ long long scaled_trunc(double x, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int be = int((b >> 52) & 0x7ff);
+    if (be == 0) return 0;   // subnormal or zero: far below 2^-beta of its row maximum
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = 52 - (be - 1023) - s;       // value = mant * 2^-sh
+    long long v;
+    if (sh >= 64) v = 0;
+    else if (sh >= 0) v = (long long)(mant >> sh);
+    else v = (long long)(mant << (-sh));       // beta > 53 (short k): still < 2^beta <= 2^62
+    return (b >> 63) ? -v : v;
+}
+
+// Balanced residue of a beta-bit integer v modulo moduli[q], from its 32-bit
+// halves: v = hi 2^32 + lo, so v mod p = (hi mod p)(2^32 mod p) + lo mod p.
+__device__ __forceinline__ float residue_bf16(long long v, int q) {
+    const unsigned long long u = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+    const int p = c_mod[q];
+    int r = (int)mod_u32(mod_u32(hi, q) * c_r32[q] + mod_u32(lo, q), q);
+    if (v < 0 && r != 0) r = p - r;
+    return (float)(r >= (p + 1) / 2 ? r - p : r);
+}
+
+// Row exponents and residue planes of X (rows x cols per leaf), K-major.
+// One warp per (leaf, row).  out[(leaf*nmod + q) * rows + row][0..kpad).
+__global__ void split_rows_kernel(const double *X, int64_t ldx, int64_t leaf_stride, int64_t rows,
+                                  int64_t cols, int64_t kpad, int64_t leaves, int beta, int nmod,
+                                  __nv_bfloat16 *out, int *exps) {
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (gw >= leaves * rows) return;
+    const int64_t leaf = gw / rows, row = gw % rows;
+    const double *x = X + leaf * leaf_stride + row * ldx;
+    double mx = 0.0;
+    for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int s = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+    if (lane == 0) exps[leaf * rows + row] = s;
+    for (int64_t j = lane; j < kpad; j += 32) {
+        const long long v = j < cols ? scaled_trunc(x[j], s) : 0;
+        for (int q = 0; q < nmod; ++q)
+            out[((leaf * nmod + q) * rows + row) * kpad + j] = __float2bfloat16_rn(residue_bf16(v, q));
+    }
+}
+
+// Column exponents of Y (rows x cols per leaf, row-major): one thread per column.
+__global__ void col_exp_kernel(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
+                               int64_t cols, int64_t leaves, int beta, int *exps) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= leaves * cols) return;
+    const int64_t leaf = g / cols, col = g % cols;
+    const double *y = Y + leaf * leaf_stride + col;
+    double mx = 0.0;
+    for (int64_t i = 0; i < rows; ++i) mx = fmax(mx, fabs(y[i * ldy]));
+    exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+}
+
+// Residue planes of Y^T (cols x kpad per plane) through a 32x32 tile
+// transpose in shared memory.  grid: (ceil(kpad/32), ceil(cols/32), leaves).
+__global__ void split_cols_kernel(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
+                                  int64_t cols, int64_t kpad, int nmod, const int *exps,
+                                  __nv_bfloat16 *out) {
+    __shared__ long long tile[32][33];
+    const int64_t leaf = blockIdx.z;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const double *y = Y + leaf * leaf_stride;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        long long v = 0;
+        if (i < rows && j < cols) v = scaled_trunc(y[i * ldy + j], exps[leaf * cols + j]);
+        tile[r][tx] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + r, i = i0 + tx;       // output row j (a column of Y), col i
+        if (j >= cols || i >= kpad) continue;
+        const long long v = tile[tx][r];
+        for (int q = 0; q < nmod; ++q)
+            out[((leaf * nmod + q) * cols + j) * kpad + i] = __float2bfloat16_rn(residue_bf16(v, q));
+    }
+}
+
+// Correctly rounded conversion of a 128-bit integer to FP64: the top 64
+// significant bits with every lower bit folded into a sticky bit round like
+// the full value.
+__device__ __forceinline__ double int128_to_double(__int128 x) {
+    const bool neg = x < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
+    const unsigned long long hi = (unsigned long long)(u >> 64);
+    double d;
+    if (hi == 0) {
+        d = __ull2double_rn((unsigned long long)u);
+    } else {
+        const int sh = 64 - __clzll((long long)hi);              // bits above the low 64
+        unsigned long long top = (unsigned long long)(u >> sh);
+        if ((u & (((unsigned __int128)1 << sh) - 1)) != 0) top |= 1ull;
+        d = ldexp(__ull2double_rn(top), sh);
+    }
+    return neg ? -d : d;
+}
+
+// C[leaf][i][j] = (Z from its residues) * 2^-(sa_i + sb_j).
+__global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves, int nmod,
+                           const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride) {
+    const int64_t total = leaves * m * n;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t leaf = g / (m * n), rem = g % (m * n), i = rem / n, j = rem % n;
+        // mixed-radix digits v_q of Z (balanced): Z = sum_q v_q prod_{l<q} p_l
+        int v[OZ_MAX_MOD];
+#pragma unroll
+        for (int q = 0; q < OZ_MAX_MOD; ++q) {
+            if (q >= nmod) break;
+            const int p = c_mod[q];
+            const int z = Z[((leaf * nmod + q) * m + i) * n + j];
+            int sum = z;
+#pragma unroll
+            for (int l = 0; l < OZ_MAX_MOD; ++l) {
+                if (l >= q) break;
+                sum -= v[l] * c_wmod[l][q];
+            }
+            // sum lies in (-2^20, 2^20): shift it positive, reduce, scale by the inverse
+            const unsigned t = mod_u32((unsigned)(sum + (p << 13)), q);
+            const int d = (int)mod_u32(t * (unsigned)c_winv[q], q);
+            v[q] = d >= (p + 1) / 2 ? d - p : d;
+        }
+        // Z = sum_q v_q prod_{l<q} p_l by Horner's rule in exact 128-bit
+        // integers (|Z| < P/2 < 2^127 for N <= 16), then one correct rounding
+        __int128 x = v[nmod - 1];
+        for (int q = nmod - 2; q >= 0; --q) x = x * c_mod[q] + v[q];
+        const int e = -(sa[leaf * m + i] + sb[leaf * n + j]);
+        C[leaf * leaf_stride + i * ldc + j] = ldexp(int128_to_double(x), e);
+    }
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                             CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                             CUtensorMapFloatOOBfill);
+
+std::mutex g_oz_mu;
+EncodeFn g_encode = nullptr;
+bool g_tables[64] = {};
+int g_tables_n[64] = {};
+
+cudaError_t encode_fn(EncodeFn *out) {
+    std::lock_guard<std::mutex> g(g_oz_mu);
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+        g_encode = (EncodeFn)fn;
+    }
+    *out = g_encode;
+    return cudaSuccess;
+}
+
+long long mod_pow_inv(long long a, long long p) {
+    // inverse of a modulo p (a, p coprime) by the extended Euclidean algorithm
+    long long t = 0, nt = 1, r = p, nr = a % p;
+    while (nr != 0) {
+        const long long q = r / nr;
+        long long tmp = t - q * nt; t = nt; nt = tmp;
+        tmp = r - q * nr; r = nr; nr = tmp;
+    }
+    return t < 0 ? t + p : t;
+}
+
+cudaError_t ensure_tables(int nmod) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> g(g_oz_mu);
+    if (dev < 64 && g_tables[dev] && g_tables_n[dev] == nmod) return cudaSuccess;
+    int mods[OZ_MAX_MOD] = {}, wmod[OZ_MAX_MOD][OZ_MAX_MOD] = {}, winv[OZ_MAX_MOD] = {};
+    unsigned magic[OZ_MAX_MOD] = {}, r32[OZ_MAX_MOD] = {};
+    for (int i = 0; i < nmod; ++i) {
+        mods[i] = kOzakiModuli[i];
+        magic[i] = (unsigned)((1ull << 32) / (unsigned long long)mods[i]);
+        r32[i] = (unsigned)((1ull << 32) % (unsigned long long)mods[i]);
+    }
+    for (int j = 0; j < nmod; ++j) {
+        long long w = 1 % mods[j];
+        for (int i = 0; i < j; ++i) {
+            wmod[i][j] = int(w);
+            w = (w * mods[i]) % mods[j];
+        }
+        winv[j] = int(mod_pow_inv(w, mods[j]));   // w = (prod_{l<j} p_l) mod p_j
+    }
+    if ((e = cudaMemcpyToSymbol(c_mod, mods, sizeof(mods))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_wmod, wmod, sizeof(wmod))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_winv, winv, sizeof(winv))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_magic, magic, sizeof(magic))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_r32, r32, sizeof(r32))) != cudaSuccess) return e;
+    if (dev < 64) { g_tables[dev] = true; g_tables_n[dev] = nmod; }
+    return cudaSuccess;
+}
+
+cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int64_t planes,
+                       int box_rows) {
+    EncodeFn enc;
+    cudaError_t e = encode_fn(&enc);
+    if (e != cudaSuccess) return e;
+    cuuint64_t gdim[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t gstr[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(kpad * rows * 2)};
+    cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, gdim, gstr, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t read_device_error(int *flag, bool clear) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return e;
+    if ((e = cudaMemcpyFromSymbol(flag, g_device_error, sizeof(int))) != cudaSuccess) return e;
+    if (clear && *flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
+    }
+    return e;
+}
+
+// Largest beta <= 62 with k 2^(2 beta + 1) < P (P = product of the moduli,
+// < 2^127 for N <= 16), so that |S'T'| < P/2 and the CRT is unambiguous.
+int ozaki_beta(int nmod, int64_t k) {
+    unsigned __int128 P = 1;
+    for (int i = 0; i < nmod; ++i) P *= (unsigned)kOzakiModuli[i];
+    for (int beta = 62; beta > 0; --beta) {
+        const int sh = 2 * beta + 1;
+        // k 2^sh < P  <=>  k 2^sh <= P - 1  <=>  k <= floor((P - 1) / 2^sh)
+        if (sh < 128 && (unsigned __int128)k <= ((P - 1) >> sh)) return beta;
+    }
+    return 0;
+}
+
+size_t ozaki_workspace(int64_t leaves, int nmod, int64_t m, int64_t k, int64_t n) {
+    const int64_t kpad = (k + OZ_BK - 1) / OZ_BK * OZ_BK;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return al(size_t(leaves) * nmod * m * kpad * 2) + al(size_t(leaves) * nmod * n * kpad * 2) +
+           al(size_t(leaves) * m * 4) + al(size_t(leaves) * n * 4) + al(size_t(leaves) * nmod * m * n);
+}
+
+// Leaf products Out[leaf] (m x n, ld ldo, leaf stride) = S[leaf] T[leaf]
+// emulated in FP64 with nmod moduli.  S: m x k (lds, stride ss); T: k x n
+// (ldt, stride ts).  ws: ozaki_workspace() bytes, 256-aligned.
+cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
+                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
+                           int64_t m, int64_t k, int64_t n, int nmod, void *ws,
+                           cudaStream_t s, int *launches) {
+    int *err = nullptr;
+    cudaError_t e0 = cudaGetSymbolAddress((void **)&err, g_device_error);
+    if (e0 != cudaSuccess) return e0;
+    cudaError_t e = ensure_tables(nmod);
+    if (e != cudaSuccess) return e;
+    const int64_t kpad = (k + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const int beta = ozaki_beta(nmod, k);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char *w = (char *)ws;
+    __nv_bfloat16 *ra = (__nv_bfloat16 *)w;
+    w += al(size_t(leaves) * nmod * m * kpad * 2);
+    __nv_bfloat16 *rb = (__nv_bfloat16 *)w;
+    w += al(size_t(leaves) * nmod * n * kpad * 2);
+    int *ea = (int *)w;
+    w += al(size_t(leaves) * m * 4);
+    int *eb = (int *)w;
+    w += al(size_t(leaves) * n * 4);
+    int8_t *Z = (int8_t *)w;
+
+    {
+        const int64_t warps = leaves * m;
+        const unsigned blocks = (unsigned)((warps + 7) / 8);
+        split_rows_kernel<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, beta, nmod, ra, ea);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        const int64_t th = leaves * n;
+        col_exp_kernel<<<(unsigned)((th + 255) / 256), 256, 0, s>>>(T, ldt, ts, k, n, leaves, beta, eb);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
+        split_cols_kernel<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, nmod, eb, rb);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        CUtensorMap ta, tb;
+        if ((e = make_map3d(&ta, ra, kpad, m, leaves * nmod, OZ_BM)) != cudaSuccess) return e;
+        if ((e = make_map3d(&tb, rb, kpad, n, leaves * nmod, OZ_BN)) != cudaSuccess) return e;
+        static bool configured[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !configured[dev]) {
+            if ((e = cudaFuncSetAttribute(residue_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          OZ_SMEM)) != cudaSuccess)
+                return e;
+            configured[dev] = true;
+        }
+        const int64_t planes = leaves * nmod;
+        const int64_t tn = (n + OZ_BN - 1) / OZ_BN, tmb = (m + OZ_BM - 1) / OZ_BM;
+        if (planes > 65535 || tmb > 65535) return cudaErrorInvalidValue;
+        cudaEvent_t t0 = timing_mark(s);
+        residue_gemm<<<dim3((unsigned)tn, (unsigned)tmb, (unsigned)planes), OZ_THREADS, OZ_SMEM, s>>>(
+            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, err);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (t0 && !timing_mark(s)) timing_unmark();
+    }
+    {
+        const int64_t total = leaves * m * n;
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        crt_kernel<<<blocks, 256, 0, s>>>(Z, m, n, leaves, nmod, ea, eb, Out, ldo, os);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace fmm

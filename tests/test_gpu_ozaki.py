@@ -1,0 +1,64 @@
+"""GPU parity of the emulated-FP64 precision variant (tensor-core residue
+products + CRT) against the oracle: exact on integer inputs (the scaled
+operands are not truncated, so the CRT rebuilds A B exactly), within the
+truncation bound and close to the oracle's own emulation on random inputs,
+and combined with the fast recursion."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import norms, ozaki
+import paper_1409_2908_gb300 as fmm
+from paper_1409_2908_gb300 import synth
+from tests.gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run(plan, A, B):
+    import torch
+    C = fmm.gemm(plan, to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    fmm.check_device_error()
+    return C.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,k,n", [(128, 64, 128), (1, 1, 1), (200, 300, 100), (257, 1100, 129), (96, 2048, 300)])
+def test_classical_emulated_integer_exact(m, k, n):
+    p = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16")
+    A, B = synth.operands(m, k, n, 41, kind="integer")
+    assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
+
+
+@pytest.mark.parametrize("nmod", [15, 12, 8])
+@pytest.mark.parametrize("m,k,n", [(130, 200, 70), (256, 1500, 256)])
+def test_classical_emulated_matches_oracle_emulation(nmod, m, k, n):
+    p = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=nmod)
+    A, B = synth.operands(m, k, n, 42)
+    C = run(p, A, B)
+    Coz = ozaki.emulated_gemm(A, B, nmod)
+    # same scaled integers, the exact integer product, one correct rounding
+    assert np.array_equal(C, Coz)
+    e = norms.rel_frobenius(C, oracle.gemm(A, B, precision="ld"))
+    assert e <= (1e-14 if nmod == 15 else 1e-7 if nmod == 12 else 1e-2)
+
+
+def test_classical_emulated_loguniform():
+    p = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=16)
+    A, B = synth.operands(128, 512, 128, 43, kind="loguniform")
+    assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, 16))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 1), ("strassen_222_7", 2), ("fmm_323_15", 1)])
+def test_fast_emulated_integer_exact(name, levels):
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16")
+    A, B = synth.operands(261, 517, 259, 44, kind="integer")
+    assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 2), ("fmm_333_23", 1)])
+def test_fast_emulated_uniform(name, levels):
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16")
+    A, B = synth.operands(300, 700, 290, 45)
+    e = norms.rel_frobenius(run(p, A, B), oracle.gemm(A, B))
+    assert e <= 1e-13

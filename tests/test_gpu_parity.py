@@ -207,3 +207,22 @@ def test_full_size_8192_sampled(name, levels):
     gi = Ci[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
     ei64, _ = oracle.gemm_entries(np.rint(4 * A), np.rint(4 * B), rows, cols)
     assert np.array_equal(gi, ei64)
+
+
+@pytest.mark.parametrize("name,levels,shape", [("strassen_222_7", 2, (256, 512, 384)),
+                                                ("strassen_222_7", 1, (257, 131, 199)),
+                                                ("fmm_323_15", 1, (300, 200, 303))])
+def test_batched_one_grouped_launch(name, levels, shape):
+    import torch
+    m, k, n = shape
+    p = fmm.Plan(name, levels=levels)
+    ins = [synth.operands(m, k, n, 500 + b, kind="integer") for b in range(5)]
+    As = [to_dev(a) for a, _ in ins]
+    Bs = [to_dev(b) for _, b in ins]
+    Cs = fmm.gemm_batched(p, As, Bs)
+    torch.cuda.synchronize()
+    for (A, B), C in zip(ins, Cs):
+        assert np.array_equal(C.cpu().numpy(), oracle.gemm(A, B))
+    if m % 2 ** levels == 0 and n % 2 ** levels == 0 and k % 2 ** levels == 0 and name == "strassen_222_7":
+        # no fringe: one memset per product, then a single leaf launch for all products
+        assert fmm.last_launch_count() == 1

@@ -37,8 +37,10 @@ def test_beta_keeps_product_below_half_modulus():
     for n in (8, 12, 15, 18):
         for k in (64, 1000, 16384):
             b = ozaki.beta_bits(n, k)
-            assert k * (2 ** b) ** 2 < math.prod(ozaki.moduli(n)) // 2
-            assert k * (2 ** (b + 1)) ** 2 >= math.prod(ozaki.moduli(n)) // 2 // 4
+            P = math.prod(ozaki.moduli(n))
+            assert 2 * k * (2 ** b) ** 2 < P
+            if b < 62:   # maximal: one more bit would break the bound
+                assert 2 * k * (2 ** (b + 1)) ** 2 >= P
 
 
 def test_residue_product_matches_exact_product():
