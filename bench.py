@@ -221,25 +221,82 @@ def run_reference(args):
     return 0
 
 
+def run_serving(args):
+    """Serving: Poisson arrivals of GEMMs with m, k, n log-uniform in
+    [256, 8192] at ~80 % of the classical capacity, served by the continuous-
+    batching loop with autotuned plans, then again with classical plans only."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1409_2908_gb300 import autotune, serve
+    count = args.requests
+    precs = tuple(args.precisions.split(","))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(1409)
+    pool = torch.rand(2 * 8192 * 8192, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
+    shapes = serve.request_shapes(count, seed=1409)
+    mean_flops = float(np.mean([2.0 * m * k * n for m, k, n in shapes]))
+    # classical capacity at this precision on a mid-size product
+    cl = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False, max_levels=0)
+    p = cl.plan(4096, 4096, 4096)
+    A = pool[:4096 * 4096].view(4096, 4096)
+    C = torch.empty((4096, 4096), dtype=torch.float64, device="cuda")
+    wsz = p.workspace_size(4096, 4096, 4096)
+    wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+    for _ in range(2):
+        fmm.gemm(p, A, A, C=C, workspace=wsb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(3):
+        fmm.gemm(p, A, A, C=C, workspace=wsb)
+    torch.cuda.synchronize()
+    cap = 3 * 2.0 * 4096 ** 3 / (time.perf_counter() - t0)
+    rate = 0.8 * cap / mean_flops
+    out = {}
+    for label, max_levels in (("autotuned", 3), ("classical", 0)):
+        tuner = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False, max_levels=max_levels)
+        reqs = serve.poisson_requests(count, rate, seed=1409, pool=pool)
+        srv = serve.Server(tuner, memory_budget_bytes=64 << 30, slots=4, use_graphs=True)
+        out[label] = srv.run(reqs)
+    line = {"metric": METRIC + " (serving)", "value": out["autotuned"]["effective_tflops"], "unit": "TFLOP/s",
+            "n_gpus": ws, "steps": count, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 or CRT-emulated f64 per autotuned plan",
+            "data": "synthetic uniform[-1,1] pool, Poisson arrivals",
+            "config": {"workload": f"serving: {count} GEMMs, m,k,n log-uniform in [256, 8192], "
+                                   f"Poisson rate {rate:.1f}/s (80% of classical capacity {cap/1e12:.1f} TFLOP/s)",
+                       "precisions": list(precs), "accuracy_target": 1e-11},
+            "p50_ms": out["autotuned"]["p50_ms"], "p99_ms": out["autotuned"]["p99_ms"],
+            "autotuned": out["autotuned"], "classical": out["classical"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
-    ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
     ap.add_argument("--plan", default=None, help="NAME:LEVELS to skip the candidate trial")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work")
     ap.add_argument("--quick", action="store_true", help="small CPU sample, no e2e")
     ap.add_argument("--fused-only", action="store_true", help="only the fused scheme as candidates")
     ap.add_argument("--moduli", type=int, default=15, help="moduli of the emulated-FP64 variant")
-    ap.add_argument("--precisions", default="fp64",
+    ap.add_argument("--tol", type=float, default=1e-11, help="accuracy target (e_F vs the oracle)")
+    ap.add_argument("--all-schemes", action="store_true", help="try every FP64 execution scheme")
+    ap.add_argument("--precisions", default="fp64,ozaki_bf16",
                     help="comma list of leaf precisions to try: fp64, ozaki_bf16")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import numpy as np
     import torch
@@ -275,11 +332,12 @@ def main():
     schemes = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "wo_st": fmm.FLAG_FUSED_W,
                "lw_st": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W, "lw": fmm.FLAG_LEVELWISE}
     precs = args.precisions.split(",")
+    fp64_schemes = list(schemes) if args.all_schemes else ["fused", "lw"]
     cands = []
     for prec in precs:
         if prec == "fp64":
             cands += [(a, L, sc, prec) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
-                      for sc in (schemes if not args.fused_only else ["fused"])]
+                      for sc in (fp64_schemes if not args.fused_only else ["fused"])]
         else:
             # emulated FP64: the classical product (0 levels) and the fast plans, level by level
             cands += [("strassen_222_7", 0, "lw", prec)]
@@ -317,9 +375,15 @@ def main():
     ms_c1 = time_steps(torch, fc, 1, stream)
     err_c = rel_err_rows(Cd)
     results.append({"plan": "classical", "tflops": flops / ms_c1 / 1e9, "ms": ms_c1, "rel_err_F": err_c})
-    best = min((r for r in results if r["plan"] != "classical"), key=lambda r: r["ms"], default=None)
+    # the headline is the fastest FAST-algorithm plan (at least one recursive
+    # level) whose error against the oracle meets the target; the classical
+    # products at each precision are reported beside it
+    fast = [r for r in results if r["plan"] != "classical" and " L0 " not in r["plan"]
+            and (r["rel_err_F"] is None or r["rel_err_F"] <= args.tol)]
+    best = min(fast, key=lambda r: r["ms"], default=None)
     if best is None:
         raise SystemExit("no fast-algorithm plan available for this workload")
+    classical_same = [r for r in results if " L0 " in r["plan"]]
     p = plans[best["plan"]]
     plans.clear()
     wsz = p.workspace_size(m, k, n)
@@ -406,8 +470,16 @@ def main():
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "rel_err_F": err, "rel_err_note": "e_F over the cpu_baseline's sampled rows vs the FP64 oracle",
-            "classical": {"value": ws * flops / ms_c / 1e9, "ms_per_step": ms_c, "rel_err_F": err_c},
+            "classical": {"value": ws * flops / ms_c / 1e9, "ms_per_step": ms_c, "rel_err_F": err_c,
+                          "what": "the library's classical FP64 GEMM (DFMA)"},
+            "classical_emulated": ({"value": classical_same[0]["tflops"], "ms": classical_same[0]["ms"],
+                                    "rel_err_F": classical_same[0]["rel_err_F"],
+                                    "what": "the library's classical GEMM with emulated-FP64 leaves"}
+                                   if classical_same else None),
             "speedup_vs_classical": ms_c / ms_step,
+            "speedup_vs_classical_same_precision": (classical_same[0]["ms"] / ms_step
+                                                    if classical_same and p.precision != "fp64" else ms_c / ms_step),
+            "accuracy_target": args.tol,
             "plans": results,
             "roofline": roof,
             "cpu_baseline": base_rec,

@@ -81,6 +81,11 @@ enum {
        fully unrolled per-leaf chains.  Needs more workspace, but the addition
        count grows like sum_l R^(l-1) nnz rather than nnz^L. */
     FMM_FLAG_LEVELWISE = 1u << 2,
+    /* Emulated-precision plans only: emulate each leaf product separately
+       (S/T and W in FP64) instead of running the whole recursion on residues
+       of the once-scaled A and B (the default when every base coefficient
+       is an integer: the bilinear algorithm is then exact modulo p). */
+    FMM_FLAG_LEAF_EMULATION = 1u << 3,
     FMM_FLAGS_DEFAULT = FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W
 };
 
@@ -143,6 +148,13 @@ fmm_status fmm_plan_set_moduli(fmm_plan_t plan, int n_moduli);
    flag is then cleared), FMM_OK otherwise, FMM_ERR_CUDA if the device
    reports an error. */
 fmm_status fmm_check_device_error(void);
+
+/* Copy the plan to the current device and set up everything its kernels
+   need (constant tables, kernel attributes) now, instead of on the first
+   fmm_gemm call; afterwards fmm_gemm with this plan performs no allocation or
+   synchronous copy, so it can be captured into a CUDA graph.  Errors:
+   FMM_ERR_ARG, FMM_ERR_NO_MEMORY, FMM_ERR_CUDA. */
+fmm_status fmm_plan_prepare(fmm_plan_t plan);
 
 /* Choose the leaf GEMM tile shape used by later fmm_gemm calls with this
    plan (default FMM_TILE_AUTO).  Not thread-safe against concurrent

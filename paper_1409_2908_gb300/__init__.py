@@ -24,6 +24,7 @@ PRECISIONS = {"fp64": FMM_PREC_FP64, "ozaki_bf16": FMM_PREC_OZAKI_BF16}
 FLAG_FUSED_ST = 1
 FLAG_FUSED_W = 2
 FLAG_LEVELWISE = 4
+FLAG_LEAF_EMULATION = 8
 FLAGS_DEFAULT = FLAG_FUSED_ST | FLAG_FUSED_W
 
 TILES = {"auto": 0, "128x128": 1, "96x96": 2, "64x64": 3, "32x32": 4, "128x64": 5, "64x128": 6}
@@ -104,6 +105,10 @@ class Plan:
             self.set_tile(tile)
         if moduli is not None:
             _check(L.fmm_plan_set_moduli(self._h, int(moduli)), "set_moduli")
+
+    def prepare(self):
+        """Upload the plan and set up its kernels now (before graph capture)."""
+        _check(_lib.lib().fmm_plan_prepare(self._h), "prepare")
 
     def set_tile(self, tile):
         _check(_lib.lib().fmm_plan_set_tile(self._h, TILES[tile]), "set_tile")

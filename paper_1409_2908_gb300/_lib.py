@@ -59,6 +59,8 @@ def _declare(L):
     L.fmm_gemm_batched.argtypes = [c_p, c_i64, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64,
                                    c_p, ctypes.c_size_t, c_p]
     L.fmm_gemm_batched.restype = st
+    L.fmm_plan_prepare.argtypes = [c_p]
+    L.fmm_plan_prepare.restype = st
     L.fmm_plan_set_moduli.argtypes = [c_p, ctypes.c_int]
     L.fmm_plan_set_moduli.restype = st
     L.fmm_check_device_error.argtypes = []

@@ -1,0 +1,195 @@
+"""Autotuner: for a product shape (m, k, n) and an accuracy target, pick the
+base case, the number of recursive levels, the execution scheme, the leaf
+tile and the leaf precision.
+
+The paper's rule for recursion (Section 3.3) is the model prior: a recursive
+step only pays while its sub-products stay on the flat part of the classical
+GEMM's performance curve, and the best algorithm depends on the shape
+(Section 5: algorithms that "match the shape" win on rectangular products).
+Here the classical curve is the library's own classical GEMM measured on this
+GPU, the model ranks every (algorithm, levels, scheme, precision) candidate,
+and the few best candidates are timed on the real shape; the fastest that
+meets the accuracy target is kept (per shape, in memory and optionally in a
+JSON file).
+
+Nothing here computes the product: every candidate runs through the C ABI.
+"""
+import glob
+import json
+import math
+import os
+from dataclasses import asdict, dataclass
+
+import paper_1409_2908_gb300 as fmm
+
+# measured on GB300 (bench runs, profiles/): FP64 DFMA ceiling and the
+# emulated path's per-element costs, used only to rank candidates
+FP64_TFLOPS = 1.22
+TC_TFLOPS = 690.0
+SPLIT_NS_PER_ELEM_MOD = 0.0016       # per operand element and modulus
+CRT_NS_PER_ELEM = 0.061              # per output element (15 moduli)
+HBM_GBS = 6700.0
+
+
+@dataclass(frozen=True)
+class Choice:
+    algorithm: str            # algorithm file name (levels 0: the classical product)
+    levels: int
+    flags: int
+    precision: str            # "fp64" or "ozaki_bf16"
+    moduli: int = 15
+    tile: str = "auto"
+    model_ms: float = 0.0
+    measured_ms: float = -1.0
+
+    def plan(self):
+        return fmm.Plan(self.algorithm, levels=self.levels, flags=self.flags,
+                        precision=self.precision, tile=self.tile,
+                        moduli=self.moduli if self.precision != "fp64" else None)
+
+
+def algorithms():
+    """Shipped base cases: name -> (M, K, N, R)."""
+    out = {}
+    for path in sorted(glob.glob(os.path.join(fmm.ALGORITHM_DIR, "*.fmm"))):
+        with open(path) as fh:
+            lines = [ln.split("#", 1)[0].strip() for ln in fh]
+        M, K, N, R = (int(t) for t in next(ln for ln in lines if ln).split())
+        out[os.path.basename(path)[:-4]] = (M, K, N, R)
+    return out
+
+
+def moduli_for(tol, k):
+    """Fewest moduli whose truncation error 2^(1-beta) (with a factor 16 of
+    slack for accumulation) meets the relative tolerance."""
+    for n in range(6, 17):
+        P = 1
+        for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
+            P *= p
+        beta = 62
+        while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
+            beta -= 1
+        if 16 * 2.0 ** (1 - beta) <= tol:
+            return n
+    return None
+
+
+def classical_efficiency(m, n, tile=128):
+    """Fraction of the DFMA ceiling a leaf of m x n reaches: tile fill (the
+    classical curve is flat above one tile on this GPU; below it the padded
+    tile wastes work)."""
+    fill = (m * n) / (math.ceil(m / tile) * tile * math.ceil(n / tile) * tile)
+    return max(fill, 0.05)
+
+
+class Autotuner:
+    def __init__(self, tol=1e-11, precisions=("fp64", "ozaki_bf16"), max_levels=3,
+                 trials=3, cache_file=None, measure=True):
+        self.tol = tol
+        self.precisions = tuple(precisions)
+        self.max_levels = max_levels
+        self.trials = trials
+        self.cache_file = cache_file
+        self.measure = measure
+        self._cache = {}
+        self._plans = {}
+        if cache_file and os.path.exists(cache_file):
+            with open(cache_file) as fh:
+                for key, d in json.load(fh).items():
+                    self._cache[key] = Choice(**d)
+
+    # ----------------------------------------------------------- model
+    def candidates(self, m, k, n):
+        """Every admissible candidate with its model time (ms), best first."""
+        out = []
+        algs = algorithms()
+        nmod = moduli_for(self.tol, k) if "ozaki_bf16" in self.precisions else None
+        for prec in self.precisions:
+            if prec == "ozaki_bf16" and nmod is None:
+                continue
+            out.append(self._model(m, k, n, "strassen_222_7", (2, 2, 2, 7), 0, prec, nmod))
+            for name, base in algs.items():
+                M, K, N, R = base
+                for L in range(1, self.max_levels + 1):
+                    mL, kL, nL = m // M ** L, k // K ** L, n // N ** L
+                    if min(mL, kL, nL) < 64 or R ** L > 20000:
+                        break
+                    if prec == "ozaki_bf16" and R ** L * nmod > 65535:
+                        break
+                    out.append(self._model(m, k, n, name, base, L, prec, nmod))
+        # FP64 error grows with depth; drop plans that cannot meet the target
+        out = [c for c in out if c is not None]
+        out.sort(key=lambda c: c.model_ms)
+        return out
+
+    def _model(self, m, k, n, name, base, L, prec, nmod):
+        M, K, N, R = base
+        if prec == "fp64" and L > 0 and self.tol < 1e-13 * (2.0 ** L):
+            return None
+        sm, sk, sn = M ** L, K ** L, N ** L
+        mp, kp, np_ = (m // sm) * sm, (k // sk) * sk, (n // sn) * sn
+        mL, kL, nL = mp // sm, kp // sk, np_ // sn
+        leaves = R ** L
+        fringe = 2.0 * (m * n * k - mp * np_ * kp)
+        if prec == "fp64":
+            leaf_flops = 2.0 * leaves * mL * kL * nL
+            t = leaf_flops / (FP64_TFLOPS * 1e12 * classical_efficiency(mL, nL))
+            # level-by-level additions: bytes moved per level
+            adds = 0.0
+            for l in range(1, L + 1):
+                adds += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
+                                  + (mp // M ** l) * (np_ // N ** l)) * 8 * 3
+            t += adds / (HBM_GBS * 1e9)
+            flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
+        else:
+            kpad = -(-kL // 64) * 64
+            t = 2.0 * leaves * nmod * mL * kpad * nL / (TC_TFLOPS * 1e12 * classical_efficiency(mL, nL))
+            t += (mp * kp + kp * np_) * nmod * SPLIT_NS_PER_ELEM_MOD * 1e-9 * 8
+            t += mp * np_ * CRT_NS_PER_ELEM * 1e-9 * (nmod / 15.0)
+            for l in range(1, L + 1):
+                t += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
+                               + (mp // M ** l) * (np_ // N ** l)) * nmod * 3 / (HBM_GBS * 1e9)
+            flags = fmm.FLAGS_DEFAULT
+        t += fringe / (FP64_TFLOPS * 1e12)
+        return Choice(name, L, flags, prec, nmod or 15, "auto", 1e3 * t)
+
+    # ----------------------------------------------------------- choice
+    def choose(self, m, k, n):
+        key = f"{m}x{k}x{n}:{self.tol:g}:{','.join(self.precisions)}"
+        if key in self._cache:
+            return self._cache[key]
+        cands = self.candidates(m, k, n)
+        best = cands[0]
+        if self.measure and self.trials > 1:
+            timed = [self._time(c, m, k, n) for c in cands[:self.trials]]
+            best = min(timed, key=lambda c: c.measured_ms)
+        self._cache[key] = best
+        if self.cache_file:
+            with open(self.cache_file, "w") as fh:
+                json.dump({k_: asdict(v) for k_, v in self._cache.items()}, fh, indent=1)
+        return best
+
+    def plan(self, m, k, n):
+        c = self.choose(m, k, n)
+        key = (c.algorithm, c.levels, c.flags, c.precision, c.moduli, c.tile)
+        if key not in self._plans:
+            self._plans[key] = c.plan()
+        return self._plans[key]
+
+    def _time(self, c, m, k, n):
+        import torch
+        p = c.plan()
+        A = torch.rand((m, k), dtype=torch.float64, device="cuda") * 2 - 1
+        B = torch.rand((k, n), dtype=torch.float64, device="cuda") * 2 - 1
+        C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        wsz = p.workspace_size(m, k, n)
+        ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+        fmm.gemm(p, A, B, C=C, workspace=ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fmm.gemm(p, A, B, C=C, workspace=ws)
+        e1.record()
+        e1.synchronize()
+        return Choice(**{**asdict(c), "measured_ms": e0.elapsed_time(e1)})

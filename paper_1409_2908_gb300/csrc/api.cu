@@ -110,9 +110,30 @@ struct WsLayout {
     std::vector<size_t> lvS, lvT, lvP;
 };
 
+// The whole recursion runs on residues when the base coefficients are
+// integers (the plan layer checks) and per-leaf emulation was not asked for.
+bool residue_space(const fmm_plan *p) {
+    return p->integer_coefs && !(p->flags & FMM_FLAG_LEAF_EMULATION);
+}
+
+ResPlan res_plan(const fmm_plan *p) {
+    ResPlan rp{};
+    rp.M = p->M; rp.K = p->K; rp.N = p->N; rp.R = p->R; rp.L = p->L;
+    rp.u_ptr = p->dev.lu_ptr; rp.u_code = p->dev.lu_code; rp.u_icoef = p->dev.lu_icoef;
+    rp.v_ptr = p->dev.lv_ptr; rp.v_code = p->dev.lv_code; rp.v_icoef = p->dev.lv_icoef;
+    rp.vt_code = p->dev.lvt_code;
+    rp.w_ptr = p->dev.lw_ptr; rp.w_r = p->dev.lw_r; rp.w_icoef = p->dev.lw_icoef;
+    return rp;
+}
+
 WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     WsLayout w;
     const bool oz = p->prec == FMM_PREC_OZAKI_BF16;
+    if (oz && p->L > 0 && g.fast && residue_space(p)) {
+        w.oz = 0;
+        w.total = ozaki_fast_workspace(res_plan(p), g.mp, g.kp, g.np, p->nmod);
+        return w;
+    }
     if (oz && p->L == 0) {
         // the whole product is one emulated leaf
         w.oz = 0;
@@ -213,6 +234,24 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     if (p->L == 0)
         return cuda_status(ozaki_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n, p->nmod,
                                           wsb + wl.oz, s, launches));
+    if (residue_space(p)) {
+        const bool kfr = g.kp < k;
+        if (kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
+                                         g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        if ((e = ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, g.mp, g.kp, g.np, p->nmod,
+                            kfr ? 1 : 0, wsb + wl.oz, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        if (g.mp < m &&
+            (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
+                                  FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        if (g.np < n &&
+            (e = launch_classical(A, lda, B + g.np, ldb, C + g.np, ldc, g.mp, k, n - g.np,
+                                  FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+            return cuda_status(e);
+        return FMM_OK;
+    }
     const double *pa = A, *pb = B;
     int64_t pld_a = lda, pld_b = ldb, pst_a = 0, pst_b = 0, parents = 1;
     for (int l = 1; l <= p->L; ++l) {
@@ -446,7 +485,9 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
     if (levels < 0 || levels > 6) return FMM_ERR_ARG;
     if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16) return FMM_ERR_UNSUPPORTED;
-    if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE)) return FMM_ERR_ARG;
+    if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE |
+                          FMM_FLAG_LEAF_EMULATION))
+        return FMM_ERR_ARG;
     bool representable = true;
     if (!brent_exact(M, K, N, R, U, V, W, &representable))
         return representable ? FMM_ERR_INVALID_ALGORITHM : FMM_ERR_UNSUPPORTED;
@@ -494,6 +535,15 @@ void fmm_plan_destroy(fmm_plan_t p) {
 fmm_status fmm_plan_set_tile(fmm_plan_t p, fmm_tile tile) {
     if (!p || tile < FMM_TILE_AUTO || tile > FMM_TILE_64x128) return FMM_ERR_ARG;
     p->tile = tile;
+    return FMM_OK;
+}
+
+fmm_status fmm_plan_prepare(fmm_plan_t p) {
+    if (!p) return FMM_ERR_ARG;
+    fmm_status st = ensure_uploaded(p);
+    if (st != FMM_OK) return st;
+    if (p->prec == FMM_PREC_OZAKI_BF16 && ozaki_prepare(p->nmod) != cudaSuccess) return FMM_ERR_CUDA;
+    if (prepare_fp64_kernels() != cudaSuccess) return FMM_ERR_CUDA;
     return FMM_OK;
 }
 

@@ -48,9 +48,11 @@ struct DevicePlan {
     int *lu_ptr = nullptr, *lu_code = nullptr;   // per r: A blocks (a<<16|b)
     double *lu_coef = nullptr;
     int *lv_ptr = nullptr, *lv_code = nullptr;   // per r: B blocks
+    int *lvt_code = nullptr;                     // the same blocks of B^T (c<<16|b)
     double *lv_coef = nullptr;
     int *lw_ptr = nullptr, *lw_r = nullptr;      // per C block q: (r, W_qr)
     double *lw_coef = nullptr;
+    int *lu_icoef = nullptr, *lv_icoef = nullptr, *lw_icoef = nullptr;  // integer base coefficients
     int *leaf_slot = nullptr;                    // code -(r+1) for every leaf
     double *c_coef_raw = nullptr;                // unscaled flattened W
     double *a_coef_raw = nullptr, *b_coef_raw = nullptr;  // unnormalised chains
@@ -77,6 +79,7 @@ struct fmm_plan {
     bool uploaded = false;
     fmm_precision prec = FMM_PREC_FP64;
     int nmod = 15;                           // moduli of the emulated-FP64 variant
+    bool integer_coefs = false;              // every base coefficient an integer in [-127, 127]
 };
 
 namespace fmm {
@@ -148,6 +151,20 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
                            int64_t m, int64_t k, int64_t n, int nmod, void *ws, cudaStream_t s,
                            int *launches);
 cudaError_t read_device_error(int *flag, bool clear);
+cudaError_t ozaki_prepare(int nmod);          // constant tables, kernel attributes
+cudaError_t prepare_fp64_kernels();           // kernel attributes of every tile
+// residue-space recursion (integer base coefficients only)
+struct ResPlan {
+    int M, K, N, R, L;
+    const int *u_ptr, *u_code, *u_icoef;
+    const int *v_ptr, *v_code, *v_icoef;
+    const int *vt_code;                      // B block codes with row and column swapped (B^T)
+    const int *w_ptr, *w_r, *w_icoef;
+};
+size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod);
+cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
+                       int accumulate, void *ws, cudaStream_t s, int *launches);
 
 int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
                  double extra_a, double extra_b, int num_sms);

@@ -505,8 +505,7 @@ __device__ int g_unit_code[1] = {0};
 __device__ double g_unit_coef[1] = {1.0};
 
 template <int TM, int TN, bool WS>
-cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cudaStream_t s,
-                        int *launches) {
+cudaError_t configure_tile(void (**kern_out)(const KParams), size_t *smem_out) {
     constexpr int BM = 16 * TM, BN = 16 * TN;
     const size_t smem = WS ? sizeof(double) * WS_STAGES * BK * ((BM + 1) + BN)
                            : sizeof(double) * 2 * BK * ((BM + 1) + BN);
@@ -515,7 +514,6 @@ cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cuda
         kern = leaf_gemm_ws<TM, TN>;
     else
         kern = leaf_gemm<TM, TN>;
-    const int threads = WS ? WS_THREADS : THREADS;
     static bool configured[64] = {};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -525,6 +523,20 @@ cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cuda
         if (e != cudaSuccess) return e;
         configured[dev] = true;
     }
+    if (kern_out) *kern_out = kern;
+    if (smem_out) *smem_out = smem;
+    return cudaSuccess;
+}
+
+template <int TM, int TN, bool WS>
+cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cudaStream_t s,
+                        int *launches) {
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    void (*kern)(const KParams);
+    size_t smem;
+    cudaError_t ce = configure_tile<TM, TN, WS>(&kern, &smem);
+    if (ce != cudaSuccess) return ce;
+    const int threads = WS ? WS_THREADS : THREADS;
     KParams p = base;
     const int64_t tiles_m = (p.mL + BM - 1) / BM, tiles_n = (p.nL + BN - 1) / BN;
     if (tiles_m * tiles_n > 0x7fffffffLL) return cudaErrorInvalidValue;
@@ -542,6 +554,18 @@ cudaError_t launch_tile(const KParams &base, int64_t leaves, int64_t batch, cuda
 }
 
 }  // namespace
+
+cudaError_t prepare_fp64_kernels() {
+    cudaError_t e;
+    if ((e = configure_tile<8, 8, true>(nullptr, nullptr)) != cudaSuccess) return e;
+    if ((e = configure_tile<6, 6, true>(nullptr, nullptr)) != cudaSuccess) return e;
+    if ((e = configure_tile<8, 4, true>(nullptr, nullptr)) != cudaSuccess) return e;
+    if ((e = configure_tile<4, 8, true>(nullptr, nullptr)) != cudaSuccess) return e;
+    if ((e = configure_tile<4, 4, false>(nullptr, nullptr)) != cudaSuccess) return e;
+    if ((e = configure_tile<2, 2, false>(nullptr, nullptr)) != cudaSuccess) return e;
+    int *uptr;
+    return cudaGetSymbolAddress((void **)&uptr, g_unit_ptr);
+}
 
 void tile_dims(int tile, int *bm, int *bn) {
     switch (tile) {

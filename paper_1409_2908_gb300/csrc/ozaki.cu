@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "fmm_internal.h"
 
@@ -37,7 +38,7 @@ __device__ int g_device_error = 0;   // set when a bounded wait gives up
 
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 4;
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 6;
 constexpr int OZ_CHUNK_KB = 8;          // 8 x 64 = 512 k per exact FP32 chunk
 constexpr int OZ_TBUF = 4;              // TMEM accumulators of 128 columns
 constexpr int OZ_THREADS = 192;         // warps 0-3 drain, 4 loads, 5 issues MMAs
@@ -112,10 +113,23 @@ __device__ __forceinline__ int bal_mod(int x, int p) {
     return r >= (p + 1) / 2 ? r - p : r;
 }
 
+// Balanced residue modulo moduli[q] of |x| < 2^20 (combinations of a few
+// residues): shift positive by p * 2^13, then one Barrett reduction.
+__device__ __forceinline__ int bal_mod_q(int x, int q) {
+    const int p = c_mod[q];
+    const int r = (int)mod_u32((unsigned)(x + (p << 13)), q);
+    return r >= (p + 1) / 2 ? r - p : r;
+}
+
 // Z[z][row][col] (int8 balanced residues), z = leaf * nmod + modulus index.
+// Persistent: CTA c handles tiles c, c + gridDim.x, ...; the load, MMA and
+// drain roles walk the same tile sequence, so stage and TMEM-buffer phases
+// continue across tiles and the tensor core never waits for a tile's final
+// reduction (four TMEM buffers of slack).
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             int8_t *Z, int64_t m, int64_t n, int kblocks, int nmod, int *err) {
+             int8_t *Z, int64_t m, int64_t n, int kblocks, int nmod, int tiles_m, int tiles_n,
+             int64_t tiles_total, int *err) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -124,8 +138,6 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint64_t *tempty = tfull + OZ_TBUF;
     uint32_t *tmem_slot = (uint32_t *)(tempty + OZ_TBUF);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int tn = blockIdx.x, tm = blockIdx.y, z = blockIdx.z;
-    const int p = c_mod[z % nmod];
     const int nchunks = (kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
 
     if (threadIdx.x == 0) {
@@ -142,19 +154,28 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    const int64_t per_plane = (int64_t)tiles_m * tiles_n;
 
     if (warp == 4) {
         if (lane == 0) {
-            for (int kb = 0; kb < kblocks; ++kb) {
-                const int s = kb % OZ_STAGES;
-                if (kb >= OZ_STAGES && !mbar_wait(&empty[s], ((kb / OZ_STAGES) - 1) & 1)) {
-                    atomicExch(err, 1);
-                    break;
+            int64_t g = 0;   // global k-block counter: stage and phase
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                const int z = int(tile / per_plane);
+                const int rem = int(tile % per_plane);
+                const int tm = rem / tiles_n, tn = rem % tiles_n;
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int s = int(g % OZ_STAGES);
+                    if (g >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((g / OZ_STAGES) - 1) & 1))) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *sa = smem + s * OZ_STAGE_BYTES, *sb = sa + OZ_A_BYTES;
+                    mbar_expect_tx(&full[s], OZ_STAGE_BYTES);
+                    tma_load_3d(sa, &tmA, kb * OZ_BK, tm * OZ_BM, z, &full[s]);
+                    tma_load_3d(sb, &tmB, kb * OZ_BK, tn * OZ_BN, z, &full[s]);
                 }
-                unsigned char *sa = smem + s * OZ_STAGE_BYTES, *sb = sa + OZ_A_BYTES;
-                mbar_expect_tx(&full[s], OZ_STAGE_BYTES);
-                tma_load_3d(sa, &tmA, kb * OZ_BK, tm * OZ_BM, z, &full[s]);
-                tma_load_3d(sb, &tmB, kb * OZ_BK, tn * OZ_BN, z, &full[s]);
             }
         }
     } else if (warp == 5) {
@@ -162,68 +183,91 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                    ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
             bool ok = true;
-            int kb = 0;
-            for (int c = 0; c < nchunks && ok; ++c) {
-                const int b = c % OZ_TBUF;
-                if (c >= OZ_TBUF && !mbar_wait(&tempty[b], ((c / OZ_TBUF) - 1) & 1)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t acc_tmem = tmem + (uint32_t)(b * OZ_BN);
-                const int kend = min(kblocks, (c + 1) * OZ_CHUNK_KB);
-                for (int first = 1; kb < kend; ++kb, first = 0) {
-                    const int s = kb % OZ_STAGES;
-                    if (!mbar_wait(&full[s], (kb / OZ_STAGES) & 1)) { ok = false; break; }
+            int64_t g = 0, cg = 0;   // global k-block and chunk counters
+            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                int kb = 0;
+                for (int c = 0; c < nchunks && ok; ++c, ++cg) {
+                    const int b = int(cg % OZ_TBUF);
+                    if (cg >= OZ_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / OZ_TBUF) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = su32(smem + s * OZ_STAGE_BYTES), b0 = a0 + OZ_A_BYTES;
+                    const uint32_t acc_tmem = tmem + (uint32_t)(b * OZ_BN);
+                    const int kend = min(kblocks, (c + 1) * OZ_CHUNK_KB);
+                    for (int first = 1; kb < kend; ++kb, ++g, first = 0) {
+                        const int s = int(g % OZ_STAGES);
+                        if (!mbar_wait(&full[s], uint32_t((g / OZ_STAGES) & 1))) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a0 = su32(smem + s * OZ_STAGE_BYTES), b0 = a0 + OZ_A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < OZ_BK / 16; ++kk)
-                        mma_bf16(acc_tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                                 (first && kk == 0) ? 0u : 1u);
-                    mma_commit(&empty[s]);
+                        for (int kk = 0; kk < OZ_BK / 16; ++kk)
+                            mma_bf16(acc_tmem, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                     (first && kk == 0) ? 0u : 1u);
+                        mma_commit(&empty[s]);
+                    }
+                    mma_commit(&tfull[b]);
                 }
-                mma_commit(&tfull[b]);
             }
             if (!ok) atomicExch(err, 1);
         }
     } else {
-        // warps 0-3: TMEM lanes 32*warp .. +31 hold rows of the tile
-        int acc[OZ_BN];
-#pragma unroll
-        for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
+        // warps 0-3 drain: TMEM lanes 32*warp .. +31 are rows of the tile
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c % OZ_TBUF;
-            if (!mbar_wait(&tfull[b], (c / OZ_TBUF) & 1)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * OZ_BN);
+        int64_t cg = 0;
+        for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+            const int z = int(tile / per_plane);
+            const int rem = int(tile % per_plane);
+            const int tm = rem / tiles_n, tn = rem % tiles_n;
+            const int q = z % nmod;
+            const int p = c_mod[q];
+            int acc[OZ_BN];
 #pragma unroll
-            for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
-                uint32_t r[16];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                             : "r"(base + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
+            for (int c = 0; c < nchunks; ++c, ++cg) {
+                const int b = int(cg % OZ_TBUF);
+                if (!mbar_wait(&tfull[b], uint32_t((cg / OZ_TBUF) & 1))) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * OZ_BN);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[c0 + j] += __float2int_rn(__uint_as_float(r[j]));
+                for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+                    uint32_t r[16];
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(base + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[c0 + j] += __float2int_rn(__uint_as_float(r[j]));
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&tempty[b]);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&tempty[b]);
-        }
-        if (!ok) {
-            if (lane == 0) atomicExch(err, 1);
-        } else {
+            if (!ok) break;
             const int64_t row = (int64_t)tm * OZ_BM + warp * 32 + lane;
             if (row < m) {
                 int8_t *out = Z + ((int64_t)z * m + row) * n + (int64_t)tn * OZ_BN;
                 const int64_t cols = min((int64_t)OZ_BN, n - (int64_t)tn * OZ_BN);
+                // |acc| < 2^28: shift positive by p 2^22 (< 2^31) for one Barrett step
+                if (cols == OZ_BN && n % 16 == 0) {
 #pragma unroll
-                for (int j = 0; j < OZ_BN; ++j)
-                    if (j < cols) out[j] = (int8_t)bal_mod(acc[j], p);
+                    for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
+                        __align__(16) int8_t h[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int rr = (int)mod_u32((unsigned)(acc[j0 + e] + (p << 22)), q);
+                            h[e] = (int8_t)(rr >= (p + 1) / 2 ? rr - p : rr);
+                        }
+                        *reinterpret_cast<uint4 *>(out + j0) = *reinterpret_cast<const uint4 *>(h);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < OZ_BN; ++j)
+                        if (j < cols) out[j] = (int8_t)bal_mod(acc[j], p);
+                }
             }
         }
+        if (!ok && lane == 0) atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -289,18 +333,6 @@ __global__ void split_rows_kernel(const double *X, int64_t ldx, int64_t leaf_str
     }
 }
 
-// Column exponents of Y (rows x cols per leaf, row-major): one thread per column.
-__global__ void col_exp_kernel(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
-                               int64_t cols, int64_t leaves, int beta, int *exps) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= leaves * cols) return;
-    const int64_t leaf = g / cols, col = g % cols;
-    const double *y = Y + leaf * leaf_stride + col;
-    double mx = 0.0;
-    for (int64_t i = 0; i < rows; ++i) mx = fmax(mx, fabs(y[i * ldy]));
-    exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
-}
-
 // Residue planes of Y^T (cols x kpad per plane) through a 32x32 tile
 // transpose in shared memory.  grid: (ceil(kpad/32), ceil(cols/32), leaves).
 __global__ void split_cols_kernel(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
@@ -348,7 +380,8 @@ __device__ __forceinline__ double int128_to_double(__int128 x) {
 
 // C[leaf][i][j] = (Z from its residues) * 2^-(sa_i + sb_j).
 __global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves, int nmod,
-                           const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride) {
+                           const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride,
+                           int accumulate) {
     const int64_t total = leaves * m * n;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -376,7 +409,184 @@ __global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves
         __int128 x = v[nmod - 1];
         for (int q = nmod - 2; q >= 0; --q) x = x * c_mod[q] + v[q];
         const int e = -(sa[leaf * m + i] + sb[leaf * n + j]);
-        C[leaf * leaf_stride + i * ldc + j] = ldexp(int128_to_double(x), e);
+        double *out = C + leaf * leaf_stride + i * ldc + j;
+        const double val = ldexp(int128_to_double(x), e);
+        *out = accumulate ? *out + val : val;
+    }
+}
+
+// ---------------------------------------------------------------------
+// Residue-space recursion: with integer coefficients the bilinear algorithm
+// is exact over Z/pZ, so S/T formation, the leaf products and the W
+// combination all run on residues of the once-scaled A' and B'; one CRT
+// rebuilds C' = A'B' (the same integer the classical emulation computes).
+// Buffers are laid out [matrix][modulus][rows][cols], int8 balanced.
+
+// int8 residues of X (rows x cols, ld) scaled by per-row exponents (found
+// here, one warp per row) -> out[q][row][col].
+__global__ void split_rows_i8(const double *X, int64_t ldx, int64_t rows, int64_t cols, int beta,
+                              int nmod, int8_t *out, int *exps) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= rows) return;
+    const double *x = X + row * ldx;
+    double mx = 0.0;
+    for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int s = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+    if (lane == 0) exps[row] = s;
+    for (int64_t j = lane; j < cols; j += 32) {
+        const long long v = scaled_trunc(x[j], s);
+        for (int q = 0; q < nmod; ++q)
+            out[((int64_t)q * rows + row) * cols + j] = (int8_t)residue_bf16(v, q);
+    }
+}
+
+// int8 residues of Y^T: Y (rows x cols, ld) scaled by per-column exponents,
+// written out[q][col][row] through a 32x32 tile.  grid (ceil(rows/32),
+// ceil(cols/32)), block (32, 8).
+__global__ void split_cols_t_i8(const double *Y, int64_t ldy, int64_t rows, int64_t cols, int nmod,
+                                const int *exps, int8_t *out) {
+    __shared__ long long tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        tile[r][tx] = (i < rows && j < cols) ? scaled_trunc(Y[i * ldy + j], exps[j]) : 0;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + r, i = i0 + tx;
+        if (j >= cols || i >= rows) continue;
+        const long long v = tile[tx][r];
+        for (int q = 0; q < nmod; ++q) out[((int64_t)q * cols + j) * rows + i] = (int8_t)residue_bf16(v, q);
+    }
+}
+
+// Column exponents with many threads per column: blockDim.x columns x 8 row
+// groups, reduced through shared memory.
+// grid (ceil(cols/32), leaves); leaf l reads Y + l * leaf_stride.
+__global__ void col_exp_wide(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
+                             int64_t cols, int beta, int *exps) {
+    __shared__ double part[8][32];
+    const int64_t leaf = blockIdx.y;
+    const int64_t col = (int64_t)blockIdx.x * 32 + threadIdx.x;
+    const double *y = Y + leaf * leaf_stride;
+    double mx = 0.0;
+    if (col < cols)
+        for (int64_t i = threadIdx.y; i < rows; i += 8) mx = fmax(mx, fabs(y[i * ldy + col]));
+    part[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < cols) {
+        for (int r = 1; r < 8; ++r) mx = fmax(mx, part[r][threadIdx.x]);
+        exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+    }
+}
+
+// One recursive level in residue space: child o = s*R + r, modulus q:
+// sum_t c_t (parent s, block t) mod p.  FINAL writes bfloat16 rows padded to
+// out_ld (K-major operand of the residue GEMM), otherwise int8 rows.  VEC:
+// eight consecutive columns per thread with 8-byte loads (cols, pc and out_ld
+// multiples of 8).
+template <bool FINAL, bool VEC>
+__global__ void res_form_kernel(const int8_t *parent, int64_t pr, int64_t pc, int64_t rows,
+                                int64_t cols, int R, int nmod, int64_t o_base, const int *ptr,
+                                const int *code, const int *icoef, void *out, int64_t out_ld) {
+    const int64_t o = o_base + blockIdx.y;
+    const int64_t sp = o / R;
+    const int r = int(o % R);
+    const int q = blockIdx.z;
+    const int8_t *P = parent + (sp * nmod + q) * pr * pc;
+    const int t0 = ptr[r], t1 = ptr[r + 1];
+    const int64_t plane = (o * nmod + q) * rows * out_ld;
+    constexpr int W = VEC ? 8 : 1;
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        for (int64_t j = (int64_t)threadIdx.x * W; j < out_ld; j += (int64_t)blockDim.x * W) {
+            int v[W];
+#pragma unroll
+            for (int e = 0; e < W; ++e) v[e] = 0;
+            if (j < cols) {
+                for (int t = t0; t < t1; ++t) {
+                    const int cd = code[t];
+                    const int c = icoef[t];
+                    const int8_t *src = P + ((int64_t)(cd >> 16) * rows + i) * pc + (int64_t)(cd & 0xffff) * cols + j;
+                    if (VEC) {
+                        const uint2 raw = *reinterpret_cast<const uint2 *>(src);
+                        const int8_t *bytes = reinterpret_cast<const int8_t *>(&raw);
+#pragma unroll
+                        for (int e = 0; e < W; ++e) v[e] += c * (int)bytes[e];
+                    } else {
+                        v[0] += c * (int)src[0];
+                    }
+                }
+            }
+            if (FINAL) {
+                __nv_bfloat16 *dst = (__nv_bfloat16 *)out + plane + i * out_ld + j;
+                if (VEC) {
+                    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) h[e] = __float2bfloat16_rn((float)bal_mod_q(v[e], q));
+                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(h);
+                } else {
+                    dst[0] = __float2bfloat16_rn((float)bal_mod_q(v[0], q));
+                }
+            } else {
+                int8_t *dst = (int8_t *)out + plane + i * out_ld + j;
+                if (VEC) {
+                    __align__(8) int8_t h[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) h[e] = (int8_t)bal_mod_q(v[e], q);
+                    *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(h);
+                } else {
+                    dst[0] = (int8_t)bal_mod_q(v[0], q);
+                }
+            }
+        }
+    }
+}
+
+// One level of the W combination in residue space: parent s, block qb of
+// its M x N grid, modulus q = sum_t w_t child_{s*R + r_t} mod p.  VEC: eight
+// columns per thread (cols a multiple of 8).
+template <bool VEC>
+__global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, int R, int gridN,
+                             int MN, int nmod, int8_t *parent, int64_t o_base, const int *w_ptr,
+                             const int *w_r, const int *w_icoef) {
+    const int64_t o = o_base + blockIdx.y;
+    const int64_t sp = o / MN;
+    const int qb = int(o % MN);
+    const int a = qb / gridN, c = qb % gridN;
+    const int q = blockIdx.z;
+    const int64_t prow = rows * (MN / gridN), pcol = cols * gridN;
+    int8_t *Pout = parent + (sp * nmod + q) * prow * pcol + (int64_t)a * rows * pcol + (int64_t)c * cols;
+    const int t0 = w_ptr[qb], t1 = w_ptr[qb + 1];
+    constexpr int W = VEC ? 8 : 1;
+    for (int64_t i = blockIdx.x; i < rows; i += gridDim.x) {
+        for (int64_t j = (int64_t)threadIdx.x * W; j < cols; j += (int64_t)blockDim.x * W) {
+            int v[W];
+#pragma unroll
+            for (int e = 0; e < W; ++e) v[e] = 0;
+            for (int t = t0; t < t1; ++t) {
+                const int wc = w_icoef[t];
+                const int8_t *src = child + (((sp * R + w_r[t]) * nmod + q) * rows + i) * cols + j;
+                if (VEC) {
+                    const uint2 raw = *reinterpret_cast<const uint2 *>(src);
+                    const int8_t *bytes = reinterpret_cast<const int8_t *>(&raw);
+#pragma unroll
+                    for (int e = 0; e < W; ++e) v[e] += wc * (int)bytes[e];
+                } else {
+                    v[0] += wc * (int)src[0];
+                }
+            }
+            if (VEC) {
+                __align__(8) int8_t h[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) h[e] = (int8_t)bal_mod_q(v[e], q);
+                *reinterpret_cast<uint2 *>(Pout + i * pcol + j) = *reinterpret_cast<const uint2 *>(h);
+            } else {
+                Pout[i * pcol + j] = (int8_t)bal_mod_q(v[0], q);
+            }
+        }
     }
 }
 
@@ -402,6 +612,27 @@ cudaError_t encode_fn(EncodeFn *out) {
         g_encode = (EncodeFn)fn;
     }
     *out = g_encode;
+    return cudaSuccess;
+}
+
+int num_sms() {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+cudaError_t configure_residue_gemm() {
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !configured[dev]) {
+        if ((e = cudaFuncSetAttribute(residue_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      OZ_SMEM)) != cudaSuccess)
+            return e;
+        configured[dev] = true;
+    }
     return cudaSuccess;
 }
 
@@ -476,6 +707,16 @@ cudaError_t read_device_error(int *flag, bool clear) {
 
 // Largest beta <= 62 with k 2^(2 beta + 1) < P (P = product of the moduli,
 // < 2^127 for N <= 16), so that |S'T'| < P/2 and the CRT is unambiguous.
+cudaError_t ozaki_prepare(int nmod) {
+    cudaError_t e = ensure_tables(nmod);
+    if (e != cudaSuccess) return e;
+    EncodeFn enc;
+    if ((e = encode_fn(&enc)) != cudaSuccess) return e;
+    int *err = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&err, g_device_error)) != cudaSuccess) return e;
+    return configure_residue_gemm();
+}
+
 int ozaki_beta(int nmod, int64_t k) {
     unsigned __int128 P = 1;
     for (int i = 0; i < nmod; ++i) P *= (unsigned)kOzakiModuli[i];
@@ -492,6 +733,164 @@ size_t ozaki_workspace(int64_t leaves, int nmod, int64_t m, int64_t k, int64_t n
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     return al(size_t(leaves) * nmod * m * kpad * 2) + al(size_t(leaves) * nmod * n * kpad * 2) +
            al(size_t(leaves) * m * 4) + al(size_t(leaves) * n * 4) + al(size_t(leaves) * nmod * m * n);
+}
+
+struct ResLayout {
+    size_t ra0, rb0, ea, eb, zres, cres, total;
+    std::vector<size_t> la, lb, lw;   // per level l = 1..L (lw: l = 1..L-1)
+};
+
+static ResLayout res_layout(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod) {
+    ResLayout w;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
+    w.ra0 = take(size_t(nmod) * mp * kp);
+    w.rb0 = take(size_t(nmod) * kp * np);
+    w.ea = take(size_t(mp) * 4);
+    w.eb = take(size_t(np) * 4);
+    int64_t cnt = 1, ml = mp, kl = kp, nl = np;
+    for (int l = 1; l <= rp.L; ++l) {
+        cnt *= rp.R;
+        ml /= rp.M; kl /= rp.K; nl /= rp.N;
+        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
+        if (l < rp.L) {
+            w.la.push_back(take(size_t(cnt) * nmod * ml * kl));
+            w.lb.push_back(take(size_t(cnt) * nmod * nl * kl));
+            w.lw.push_back(take(size_t(cnt) * nmod * ml * nl));
+        } else {
+            w.la.push_back(take(size_t(cnt) * nmod * ml * kpad * 2));
+            w.lb.push_back(take(size_t(cnt) * nmod * nl * kpad * 2));
+            w.zres = take(size_t(cnt) * nmod * ml * nl);
+        }
+    }
+    w.cres = take(size_t(nmod) * mp * np);
+    w.total = off;
+    return w;
+}
+
+size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod) {
+    return res_layout(rp, mp, kp, np, nmod).total;
+}
+
+// C[:mp,:np] (+)= the fast algorithm run entirely in residue space on the
+// once-scaled A' and B', rebuilt by one CRT (see the residue-space kernels).
+cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
+                       int accumulate, void *ws, cudaStream_t s, int *launches) {
+    cudaError_t e = ensure_tables(nmod);
+    if (e != cudaSuccess) return e;
+    int *err = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&err, g_device_error)) != cudaSuccess) return e;
+    const ResLayout w = res_layout(rp, mp, kp, np, nmod);
+    char *b = (char *)ws;
+    int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
+    int *ea = (int *)(b + w.ea), *eb = (int *)(b + w.eb);
+    const int beta = ozaki_beta(nmod, kp);
+    auto check = [&]() { ++*launches; return cudaGetLastError(); };
+
+    split_rows_i8<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, nmod, ra0, ea);
+    if ((e = check()) != cudaSuccess) return e;
+    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, 8), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
+    if ((e = check()) != cudaSuccess) return e;
+    // B is kept transposed from here on (residues of B^T, n x k): every T_r is
+    // then formed directly in the K-major layout the residue GEMM reads
+    split_cols_t_i8<<<dim3((unsigned)((kp + 31) / 32), (unsigned)((np + 31) / 32)), dim3(32, 8), 0, s>>>(
+        B, ldb, kp, np, nmod, eb, rb0);
+    if ((e = check()) != cudaSuccess) return e;
+    // S and T^T level by level
+    int64_t parents = 1, pm = mp, pk = kp, pn = np;
+    const int8_t *pa = ra0, *pb = rb0;
+    auto form = [&](const int8_t *par, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
+                    const int *uptr, const int *ucode, const int *ucoef, void *out, bool last,
+                    int64_t out_ld) -> cudaError_t {
+        const int64_t outs = parents * rp.R;
+        const bool vec = (cols % 8 == 0) && (pcc % 8 == 0) && (out_ld % 8 == 0);
+        const unsigned threads = 128;
+        for (int64_t ob = 0; ob < outs; ob += 65535) {
+            const unsigned cnt = (unsigned)std::min<int64_t>(65535, outs - ob);
+            dim3 grid((unsigned)std::min<int64_t>(rows, 1024), cnt, (unsigned)nmod);
+            if (last && vec)
+                res_form_kernel<true, true><<<grid, threads, 0, s>>>(par, prr, pcc, rows, cols, rp.R, nmod, ob, uptr, ucode, ucoef, out, out_ld);
+            else if (last)
+                res_form_kernel<true, false><<<grid, threads, 0, s>>>(par, prr, pcc, rows, cols, rp.R, nmod, ob, uptr, ucode, ucoef, out, out_ld);
+            else if (vec)
+                res_form_kernel<false, true><<<grid, threads, 0, s>>>(par, prr, pcc, rows, cols, rp.R, nmod, ob, uptr, ucode, ucoef, out, out_ld);
+            else
+                res_form_kernel<false, false><<<grid, threads, 0, s>>>(par, prr, pcc, rows, cols, rp.R, nmod, ob, uptr, ucode, ucoef, out, out_ld);
+            cudaError_t ce = check();
+            if (ce != cudaSuccess) return ce;
+        }
+        return cudaSuccess;
+    };
+    for (int l = 1; l <= rp.L; ++l) {
+        const int64_t ml = pm / rp.M, kl = pk / rp.K, nl = pn / rp.N;
+        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
+        const bool last = l == rp.L;
+        if ((e = form(pa, pm, pk, ml, kl, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[l - 1], last,
+                      last ? kpad : kl)) != cudaSuccess)
+            return e;
+        // B^T: parent n x k, child nl x kl, block codes with rows and columns swapped
+        if ((e = form(pb, pn, pk, nl, kl, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[l - 1], last,
+                      last ? kpad : kl)) != cudaSuccess)
+            return e;
+        pa = (const int8_t *)(b + w.la[l - 1]);
+        pb = (const int8_t *)(b + w.lb[l - 1]);
+        parents *= rp.R;
+        pm = ml; pk = kl; pn = nl;
+    }
+    // the leaf products, all leaves and moduli in one launch
+    const int64_t mL = pm, kL = pk, nL = pn, leaves = parents;
+    const int64_t kpadL = (kL + OZ_BK - 1) / OZ_BK * OZ_BK;
+    int8_t *Z = (int8_t *)(b + w.zres);
+    {
+        CUtensorMap ta, tb;
+        if ((e = make_map3d(&ta, b + w.la.back(), kpadL, mL, leaves * nmod, OZ_BM)) != cudaSuccess) return e;
+        if ((e = make_map3d(&tb, b + w.lb.back(), kpadL, nL, leaves * nmod, OZ_BN)) != cudaSuccess) return e;
+        if ((e = configure_residue_gemm()) != cudaSuccess) return e;
+        const int64_t planes = leaves * nmod;
+        const int64_t tn = (nL + OZ_BN - 1) / OZ_BN, tmb = (mL + OZ_BM - 1) / OZ_BM;
+        if (planes > (1 << 24)) return cudaErrorInvalidValue;
+        cudaEvent_t t0 = timing_mark(s);
+        const int64_t tiles = tn * tmb * planes;
+        const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
+        residue_gemm<<<ctas, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, Z, mL, nL, int(kpadL / OZ_BK), nmod,
+                                                       int(tmb), int(tn), tiles, err);
+        if ((e = check()) != cudaSuccess) return e;
+        if (t0 && !timing_mark(s)) timing_unmark();
+    }
+    // W level by level, down to the residues of C'
+    int64_t cm = mL, cn = nL;
+    const int8_t *child = Z;
+    int64_t lp = leaves / rp.R;
+    for (int l = rp.L; l >= 1; --l) {
+        int8_t *parent = (l == 1) ? (int8_t *)(b + w.cres) : (int8_t *)(b + w.lw[l - 2]);
+        const int64_t outs = lp * rp.M * rp.N;
+        const bool vec = cn % 8 == 0;
+        for (int64_t ob = 0; ob < outs; ob += 65535) {
+            const unsigned cnt = (unsigned)std::min<int64_t>(65535, outs - ob);
+            dim3 grid((unsigned)std::min<int64_t>(cm, 1024), cnt, (unsigned)nmod);
+            if (vec)
+                res_w_kernel<true><<<grid, 128, 0, s>>>(child, cm, cn, rp.R, rp.N, rp.M * rp.N, nmod, parent,
+                                                        ob, rp.w_ptr, rp.w_r, rp.w_icoef);
+            else
+                res_w_kernel<false><<<grid, 128, 0, s>>>(child, cm, cn, rp.R, rp.N, rp.M * rp.N, nmod, parent,
+                                                         ob, rp.w_ptr, rp.w_r, rp.w_icoef);
+            if ((e = check()) != cudaSuccess) return e;
+        }
+        child = parent;
+        cm *= rp.M;
+        cn *= rp.N;
+        lp /= rp.R;
+    }
+    {
+        const int64_t total = mp * np;
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        crt_kernel<<<blocks, 256, 0, s>>>((const int8_t *)(b + w.cres), mp, np, 1, nmod, ea, eb, C, ldc,
+                                          0, accumulate);
+        if ((e = check()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Leaf products Out[leaf] (m x n, ld ldo, leaf stride) = S[leaf] T[leaf]
@@ -528,8 +927,9 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
-        const int64_t th = leaves * n;
-        col_exp_kernel<<<(unsigned)((th + 255) / 256), 256, 0, s>>>(T, ldt, ts, k, n, leaves, beta, eb);
+        if (leaves > 65535) return cudaErrorInvalidValue;
+        col_exp_wide<<<dim3((unsigned)((n + 31) / 32), (unsigned)leaves), dim3(32, 8), 0, s>>>(
+            T, ldt, ts, k, n, beta, eb);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
@@ -541,21 +941,15 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
         CUtensorMap ta, tb;
         if ((e = make_map3d(&ta, ra, kpad, m, leaves * nmod, OZ_BM)) != cudaSuccess) return e;
         if ((e = make_map3d(&tb, rb, kpad, n, leaves * nmod, OZ_BN)) != cudaSuccess) return e;
-        static bool configured[64] = {};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev < 64 && !configured[dev]) {
-            if ((e = cudaFuncSetAttribute(residue_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          OZ_SMEM)) != cudaSuccess)
-                return e;
-            configured[dev] = true;
-        }
+        if ((e = configure_residue_gemm()) != cudaSuccess) return e;
         const int64_t planes = leaves * nmod;
         const int64_t tn = (n + OZ_BN - 1) / OZ_BN, tmb = (m + OZ_BM - 1) / OZ_BM;
-        if (planes > 65535 || tmb > 65535) return cudaErrorInvalidValue;
+        if (planes > (1 << 24)) return cudaErrorInvalidValue;
         cudaEvent_t t0 = timing_mark(s);
-        residue_gemm<<<dim3((unsigned)tn, (unsigned)tmb, (unsigned)planes), OZ_THREADS, OZ_SMEM, s>>>(
-            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, err);
+        const int64_t tiles = tn * tmb * planes;
+        const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
+        residue_gemm<<<ctas, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb),
+                                                       int(tn), tiles, err);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (t0 && !timing_mark(s)) timing_unmark();
@@ -563,7 +957,7 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
     {
         const int64_t total = leaves * m * n;
         const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        crt_kernel<<<blocks, 256, 0, s>>>(Z, m, n, leaves, nmod, ea, eb, Out, ldo, os);
+        crt_kernel<<<blocks, 256, 0, s>>>(Z, m, n, leaves, nmod, ea, eb, Out, ldo, os, 0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -197,6 +197,10 @@ fmm_status build_plan(fmm_plan *p, int M, int K, int N, int R, const double *U,
     p->U.assign(U, U + (size_t)M * K * R);
     p->V.assign(V, V + (size_t)K * N * R);
     p->W.assign(W, W + (size_t)M * N * R);
+    p->integer_coefs = true;
+    for (const std::vector<double> *F : {&p->U, &p->V, &p->W})
+        for (double c : *F)
+            if (c != std::floor(c) || std::fabs(c) > 127.0) p->integer_coefs = false;
     unroll(U, M, K, R, L, &p->a);
     unroll(V, K, N, R, L, &p->b);
     unroll(W, M, N, R, L, &p->c);
@@ -316,6 +320,21 @@ fmm_status upload_plan(fmm_plan *p) {
             }
         lw_ptr[q + 1] = int(lw_r.size());
     }
+    // integer copies of the base coefficients (residue-space recursion)
+    auto to_int = [&](const std::vector<double> &v, std::vector<int> *out) {
+        out->resize(v.size() + 1, 0);
+        for (size_t i = 0; i < v.size(); ++i) {
+            const double c = v[i];
+            (*out)[i] = (c == std::floor(c) && std::fabs(c) <= 127.0) ? int(c) : 0;
+        }
+    };
+    std::vector<int> lu_icoef, lv_icoef, lw_icoef;
+    std::vector<int> lvt_code(lv_code.size() + 1, 0);
+    for (size_t t = 0; t < lv_code.size(); ++t)
+        lvt_code[t] = ((lv_code[t] & 0xffff) << 16) | (lv_code[t] >> 16);
+    to_int(lu_coef, &lu_icoef);
+    to_int(lv_coef, &lv_icoef);
+    to_int(lw_coef, &lw_icoef);
     std::vector<int> leaf_slot(leaves);
     for (int64_t r = 0; r < leaves; ++r) leaf_slot[r] = -int(r + 1);
     std::vector<double> c_coef_raw(p->c.coef);
@@ -341,6 +360,8 @@ fmm_status upload_plan(fmm_plan *p) {
                  o_lw_coef = bl.add<double>(lw_coef.size() + 1);
     const size_t o_leaf_slot = bl.add<int>(leaves), o_c_raw = bl.add<double>(nc);
     const size_t o_a_raw = bl.add<double>(na), o_b_raw = bl.add<double>(nb);
+    const size_t o_lu_i = bl.add<int>(lu_icoef.size()), o_lv_i = bl.add<int>(lv_icoef.size()),
+                 o_lw_i = bl.add<int>(lw_icoef.size()), o_lvt = bl.add<int>(lvt_code.size());
 
     std::vector<unsigned char> host(bl.bytes, 0);
     auto put = [&](size_t off, const void *src, size_t n) { if (n) std::memcpy(host.data() + off, src, n); };
@@ -375,6 +396,10 @@ fmm_status upload_plan(fmm_plan *p) {
     put(o_c_raw, c_coef_raw.data(), c_coef_raw.size() * 8);
     put(o_a_raw, p->a.coef.data(), p->a.coef.size() * 8);
     put(o_b_raw, p->b.coef.data(), p->b.coef.size() * 8);
+    put(o_lu_i, lu_icoef.data(), lu_icoef.size() * 4);
+    put(o_lv_i, lv_icoef.data(), lv_icoef.size() * 4);
+    put(o_lw_i, lw_icoef.data(), lw_icoef.size() * 4);
+    put(o_lvt, lvt_code.data(), lvt_code.size() * 4);
 
     void *blob = nullptr;
     cudaError_t e = cudaMalloc(&blob, bl.bytes);
@@ -403,6 +428,8 @@ fmm_status upload_plan(fmm_plan *p) {
     d.lw_ptr = (int *)(b + o_lw_ptr); d.lw_r = (int *)(b + o_lw_r); d.lw_coef = (double *)(b + o_lw_coef);
     d.leaf_slot = (int *)(b + o_leaf_slot); d.c_coef_raw = (double *)(b + o_c_raw);
     d.a_coef_raw = (double *)(b + o_a_raw); d.b_coef_raw = (double *)(b + o_b_raw);
+    d.lu_icoef = (int *)(b + o_lu_i); d.lv_icoef = (int *)(b + o_lv_i); d.lw_icoef = (int *)(b + o_lw_i);
+    d.lvt_code = (int *)(b + o_lvt);
     return FMM_OK;
 }
 

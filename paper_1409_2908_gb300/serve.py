@@ -1,0 +1,251 @@
+"""Serving loop for GEMM requests of mixed shapes: continuous batching with
+admission by device memory, operands kept on the device, requests grouped by
+plan and launched as captured CUDA graphs, latency percentiles beside
+throughput.
+
+  * A request brings its operands (device tensors) and an arrival time.
+  * Requests are admitted in arrival order while their output and workspace
+    fit the memory budget and a stream slot is free; a request arriving while
+    others run is admitted as soon as slots and memory free up.
+  * Admitted requests that share a plan and a shape form a group; the group's
+    products are captured into one CUDA graph on the slot's stream and
+    replayed (graphs are cached per plan, shape and slot, with fixed
+    operand buffers, so a recurring shape replays without capture).
+  * Groups on different streams overlap on the device; completion is polled
+    with CUDA events.
+
+Every product runs through the library's C ABI (fmm_gemm); the plans come
+from the autotuner.  Plans are deterministic (stored-product or emulated
+schemes), so a result does not depend on what else is running.
+"""
+import time
+from collections import OrderedDict, deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import paper_1409_2908_gb300 as fmm
+
+
+@dataclass
+class Request:
+    rid: int
+    A: object                 # device tensor m x k (float64)
+    B: object                 # device tensor k x n
+    arrival: float            # seconds from the start of the run
+    C: object = None
+    t_admit: float = -1.0
+    t_done: float = -1.0
+
+    @property
+    def shape(self):
+        return (self.A.shape[0], self.A.shape[1], self.B.shape[1])
+
+    @property
+    def flops(self):
+        m, k, n = self.shape
+        return 2.0 * m * k * n
+
+
+@dataclass
+class _Graph:
+    graph: object
+    A: object
+    B: object
+    C: object
+    ws: object
+    nbytes: int
+
+
+@dataclass
+class _Group:
+    reqs: list
+    event: object
+    stream: object
+    nbytes: int
+
+
+@dataclass
+class Stats:
+    completed: int = 0
+    wall_s: float = 0.0
+    flops: float = 0.0
+    latencies: list = field(default_factory=list)
+    graphs_captured: int = 0
+    graph_replays: int = 0
+    max_inflight: int = 0
+
+    def summary(self):
+        lat = np.array(self.latencies) * 1e3
+        return {"requests": self.completed, "wall_s": self.wall_s,
+                "effective_tflops": self.flops / self.wall_s / 1e12 if self.wall_s else 0.0,
+                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "graphs_captured": self.graphs_captured, "graph_replays": self.graph_replays,
+                "max_inflight_groups": self.max_inflight}
+
+
+class Server:
+    def __init__(self, tuner, memory_budget_bytes, slots=4, graph_cache_bytes=None, use_graphs=True):
+        import torch
+        self.tuner = tuner
+        self.budget = int(memory_budget_bytes)
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.free_slots = deque(range(slots))
+        self.use_graphs = use_graphs
+        self.graph_cache_bytes = graph_cache_bytes if graph_cache_bytes is not None else self.budget // 2
+        self._graphs = OrderedDict()      # (plan key, shape, slot) -> _Graph
+        self._graph_bytes = 0
+        self.used = 0
+        self.stats = Stats()
+
+    # ------------------------------------------------------------ memory
+    def _bytes(self, plan, m, k, n):
+        return 8 * m * n + plan.workspace_size(m, k, n)
+
+    def _plan(self, m, k, n):
+        p = self.tuner.plan(m, k, n)
+        if not getattr(p, "_prepared", False):
+            p.prepare()
+            p._prepared = True
+        return p
+
+    # ------------------------------------------------------------ launch
+    def _graph_for(self, plan, shape, slot):
+        import torch
+        key = (id(plan), shape, slot)
+        g = self._graphs.get(key)
+        if g is not None:
+            self._graphs.move_to_end(key)
+            return g
+        m, k, n = shape
+        nbytes = 8 * (m * k + k * n + m * n) + plan.workspace_size(m, k, n)
+        # evict least recently used graphs whose slot is idle (a busy slot's
+        # graph buffers may still be read by its stream)
+        for old_key in list(self._graphs):
+            if self._graph_bytes + nbytes <= self.graph_cache_bytes:
+                break
+            if old_key[2] in self.free_slots or old_key[2] == slot:
+                self._graph_bytes -= self._graphs.pop(old_key).nbytes
+        A = torch.empty((m, k), dtype=torch.float64, device="cuda")
+        B = torch.empty((k, n), dtype=torch.float64, device="cuda")
+        C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        wsz = plan.workspace_size(m, k, n)
+        ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+        stream = self.streams[slot]
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
+            fmm.gemm(plan, A, B, C=C, workspace=ws, stream=torch.cuda.current_stream())
+        g = _Graph(graph, A, B, C, ws, nbytes)
+        self._graphs[key] = g
+        self._graph_bytes += nbytes
+        self.stats.graphs_captured += 1
+        return g
+
+    def _launch(self, group_reqs, plan, slot):
+        import torch
+        stream = self.streams[slot]
+        m, k, n = group_reqs[0].shape
+        nbytes = 0
+        with torch.cuda.stream(stream):
+            for r in group_reqs:
+                r.C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+                if self.use_graphs:
+                    g = self._graph_for(plan, (m, k, n), slot)
+                    g.A.copy_(r.A, non_blocking=True)
+                    g.B.copy_(r.B, non_blocking=True)
+                    g.graph.replay()
+                    r.C.copy_(g.C, non_blocking=True)
+                    self.stats.graph_replays += 1
+                else:
+                    wsz = plan.workspace_size(m, k, n)
+                    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+                    fmm.gemm(plan, r.A, r.B, C=r.C, workspace=ws, stream=stream)
+                nbytes += self._bytes(plan, m, k, n)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        return _Group(group_reqs, ev, stream, nbytes)
+
+    # ------------------------------------------------------------ loop
+    def run(self, requests, max_group=8):
+        """Serve `requests` (sorted by arrival); returns the stats summary."""
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        queue = deque()
+        inflight = []
+        t0 = time.perf_counter()
+        while pending or queue or inflight:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.popleft())
+            # retire finished groups
+            still = []
+            for g in inflight:
+                if g.event.query():
+                    done = time.perf_counter() - t0
+                    for r in g.reqs:
+                        r.t_done = done
+                        self.stats.latencies.append(done - r.arrival)
+                        self.stats.flops += r.flops
+                        self.stats.completed += 1
+                    self.used -= g.nbytes
+                    self.free_slots.append(self.streams.index(g.stream))
+                else:
+                    still.append(g)
+            inflight = still
+            # admit and group by (plan, shape) while memory and slots allow
+            while queue and self.free_slots:
+                head = queue[0]
+                plan = self._plan(*head.shape)
+                need = self._bytes(plan, *head.shape)
+                if self.used + need > self.budget and inflight:
+                    break
+                group = [queue.popleft()]
+                for r in list(queue):
+                    if len(group) >= max_group:
+                        break
+                    if r.shape == head.shape and self.used + need * (len(group) + 1) <= self.budget:
+                        group.append(r)
+                        queue.remove(r)
+                for r in group:
+                    r.t_admit = now
+                slot = self.free_slots.popleft()
+                g = self._launch(group, plan, slot)
+                self.used += g.nbytes
+                inflight.append(g)
+                self.stats.max_inflight = max(self.stats.max_inflight, len(inflight))
+            if not queue and not inflight and pending:
+                time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.001)))
+        self.stats.wall_s = time.perf_counter() - t0
+        return self.stats.summary()
+
+
+def request_shapes(count, lo=256, hi=8192, seed=1409):
+    """m, k, n of each request, each log-uniform in [lo, hi]."""
+    g = np.random.default_rng(seed)
+    return np.exp(g.uniform(np.log(lo), np.log(hi), size=(count, 3))).astype(int)
+
+
+def poisson_requests(count, rate_per_s, lo=256, hi=8192, seed=1409, device="cuda", pool=None):
+    """Requests with Poisson arrivals and m, k, n each log-uniform in
+    [lo, hi]; operands uniform[-1, 1] on the device.  With `pool` (a 1-D
+    float64 device tensor of at least hi*hi elements) the operands are views
+    of it instead of fresh allocations (the operands stay device-resident and
+    a long stream of requests fits in memory)."""
+    import torch
+    g = np.random.default_rng(seed + 1)
+    t = np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
+    dims = request_shapes(count, lo, hi, seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    reqs = []
+    for i in range(count):
+        m, k, n = (int(x) for x in dims[i])
+        if pool is not None:
+            A = pool[:m * k].view(m, k)
+            B = pool[m * k:m * k + k * n].view(k, n) if m * k + k * n <= pool.numel() else pool[:k * n].view(k, n)
+        else:
+            A = torch.rand((m, k), dtype=torch.float64, device=device, generator=gen) * 2 - 1
+            B = torch.rand((k, n), dtype=torch.float64, device=device, generator=gen) * 2 - 1
+        reqs.append(Request(i, A, B, float(t[i])))
+    return reqs

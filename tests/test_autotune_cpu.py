@@ -1,0 +1,40 @@
+"""CPU checks of the autotuner's candidate model (no timing)."""
+import pytest
+
+from paper_1409_2908_gb300 import autotune
+
+
+def test_candidates_cover_algorithms_levels_precisions():
+    t = autotune.Autotuner(tol=1e-11, measure=False)
+    cands = t.candidates(8192, 8192, 8192)
+    names = {(c.algorithm, c.levels, c.precision) for c in cands}
+    assert ("strassen_222_7", 0, "fp64") in names
+    assert ("strassen_222_7", 3, "fp64") in names
+    assert any(c.precision == "ozaki_bf16" and c.levels >= 1 for c in cands)
+    assert cands == sorted(cands, key=lambda c: c.model_ms)
+
+
+def test_recursion_stops_when_leaves_get_small():
+    # the paper's cutoff: no step whose sub-products fall below the flat part
+    t = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False)
+    for c in t.candidates(256, 256, 256):
+        M = autotune.algorithms()[c.algorithm][0] if c.levels else 1
+        assert 256 // M ** c.levels >= 64
+
+
+def test_shape_matching_prefers_rank_k_algorithms():
+    # an outer-product shape (k small) favours a base case with small K
+    t = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False)
+    best = t.choose(16384, 2048, 16384)
+    assert best.levels >= 1
+
+
+def test_moduli_for_tolerance():
+    assert autotune.moduli_for(1e-11, 8192) <= 15
+    assert autotune.moduli_for(1e-6, 8192) < autotune.moduli_for(1e-14, 8192)
+    assert autotune.moduli_for(1e-30, 8192) is None
+
+
+def test_strict_tolerance_drops_deep_fp64_plans():
+    t = autotune.Autotuner(tol=1e-14, precisions=("fp64",), measure=False)
+    assert all(c.levels <= 1 for c in t.candidates(4096, 4096, 4096))
