@@ -45,6 +45,9 @@ WORKLOADS = {
     # profiling case: inputs above L2 (128 MiB each) but small enough for a full ncu capture
     "square4096": dict(m=4096, k=4096, n=4096, desc="fp64 square 4096x4096x4096, uniform[-1,1]",
                        cands=[("strassen_222_7", 1), ("strassen_222_7", 2)]),
+    # precision variants (emulated FP64 with several moduli counts, TF32)
+    "precision16384": dict(m=16384, k=16384, n=16384, desc="square 16384x16384x16384, precision variants",
+                           cands=[("strassen_222_7", 1), ("strassen_222_7", 2)]),
     "strassen512": dict(m=512, k=512, n=512, desc="fp64 square 512x512x512, uniform[-1,1]",
                         cands=[("strassen_222_7", 1)]),
 }
@@ -276,7 +279,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
     ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS) + ["serving"])
@@ -287,6 +290,9 @@ def main():
     ap.add_argument("--fused-only", action="store_true", help="only the fused scheme as candidates")
     ap.add_argument("--moduli", type=int, default=15, help="moduli of the emulated-FP64 variant")
     ap.add_argument("--tol", type=float, default=1e-11, help="accuracy target (e_F vs the oracle)")
+    ap.add_argument("--moduli-list", default=None, help="comma list of moduli counts to try (emulated FP64)")
+    ap.add_argument("--data", default="uniform", choices=["uniform", "loguniform"])
+    ap.add_argument("--no-classical", action="store_true", help="skip the FP64 classical comparator")
     ap.add_argument("--all-schemes", action="store_true", help="try every FP64 execution scheme")
     ap.add_argument("--precisions", default="fp64,ozaki_bf16",
                     help="comma list of leaf precisions to try: fp64, ozaki_bf16")
@@ -311,7 +317,7 @@ def main():
     wl = WORKLOADS[args.workload]
     m, k, n = wl["m"], wl["k"], wl["n"]
     flops = 2.0 * m * k * n
-    A, B = synth.operands(m, k, n, 1410)
+    A, B = synth.operands(m, k, n, 1410, kind=args.data)
     Ad = torch.from_numpy(A).cuda()
     Bd = torch.from_numpy(B).cuda()
     Cd = torch.empty((m, n), dtype=torch.float64, device="cuda")
@@ -339,7 +345,7 @@ def main():
             cands += [(a, L, sc, prec) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
                       for sc in (fp64_schemes if not args.fused_only else ["fused"])]
         else:
-            # emulated FP64: the classical product (0 levels) and the fast plans, level by level
+            # tensor-core leaves: the classical product (0 levels) and the fast plans
             cands += [("strassen_222_7", 0, "lw", prec)]
             cands += [(a, L, "lw", prec) for a, L in wl["cands"]
                       if os.path.exists(fmm.algorithm_path(a)) and L <= 2]
@@ -349,9 +355,15 @@ def main():
                   parts[3] if len(parts) > 3 else "fp64")]
     plans = {}
     results = []
+    mod_list = [int(x) for x in args.moduli_list.split(",")] if args.moduli_list else [args.moduli]
+    expanded = []
     for a, L, sc, prec in cands:
-        p = fmm.Plan(a, levels=L, flags=schemes[sc], precision=prec,
-                     moduli=args.moduli if prec != "fp64" else None)
+        if prec == "ozaki_bf16":
+            expanded += [(a, L, sc, prec, nm) for nm in mod_list]
+        else:
+            expanded.append((a, L, sc, prec, None))
+    for a, L, sc, prec, nmod in expanded:
+        p = fmm.Plan(a, levels=L, flags=schemes[sc], precision=prec, moduli=nmod)
         inf = p.info()
         chain = (inf["nnz_a_terms"] + inf["nnz_b_terms"]) / (2.0 * inf["leaves"])
         if prec == "fp64" and sc in ("fused", "wo_st") and chain > 8 and len(cands) > 1:
@@ -364,17 +376,21 @@ def main():
         torch.cuda.synchronize()
         ms = time_steps(torch, f, 1, stream)
         err = rel_err_rows(Cd)
-        label = f"{a} L{L} {sc}" + ("" if prec == "fp64" else f" {prec}")
+        label = f"{a} L{L} {sc}" + ("" if prec == "fp64" else f" {prec}") + (f" x{nmod}" if nmod else "")
+        p.moduli = nmod
         plans[label] = p
         results.append({"plan": label, "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err,
                         "workspace_bytes": wsz})
         del f, wsb
     fc = (lambda: fmm.classical_gemm(Ad, Bd, C=Cd, stream=stream))
-    fc()
-    torch.cuda.synchronize()
-    ms_c1 = time_steps(torch, fc, 1, stream)
-    err_c = rel_err_rows(Cd)
-    results.append({"plan": "classical", "tflops": flops / ms_c1 / 1e9, "ms": ms_c1, "rel_err_F": err_c})
+    if not args.no_classical:
+        fc()
+        torch.cuda.synchronize()
+        ms_c1 = time_steps(torch, fc, 1, stream)
+        err_c = rel_err_rows(Cd)
+        results.append({"plan": "classical", "tflops": flops / ms_c1 / 1e9, "ms": ms_c1, "rel_err_F": err_c})
+    else:
+        err_c = None
     # the headline is the fastest FAST-algorithm plan (at least one recursive
     # level) whose error against the oracle meets the target; the classical
     # products at each precision are reported beside it
@@ -383,8 +399,9 @@ def main():
     best = min(fast, key=lambda r: r["ms"], default=None)
     if best is None:
         raise SystemExit("no fast-algorithm plan available for this workload")
-    classical_same = [r for r in results if " L0 " in r["plan"]]
     p = plans[best["plan"]]
+    tag = best["plan"].split(" ", 3)[-1] if p.precision != "fp64" else None   # "lw <prec> [xN]"
+    classical_same = [r for r in results if " L0 " in r["plan"] and tag and r["plan"].endswith(tag)]
     plans.clear()
     wsz = p.workspace_size(m, k, n)
     wsb = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
@@ -408,10 +425,12 @@ def main():
     err = rel_err_rows(Cd)
 
     # classical comparator, same steps
-    for _ in range(args.warmup):
-        fc()
-    sync_all(torch, ws)
-    ms_c = max_over_ranks(torch, ws, time_steps(torch, fc, args.steps, stream)) / args.steps
+    ms_c = None
+    if not args.no_classical:
+        for _ in range(args.warmup):
+            fc()
+        sync_all(torch, ws)
+        ms_c = max_over_ranks(torch, ws, time_steps(torch, fc, args.steps, stream)) / args.steps
 
     # roofline of the dominant kernel
     mL = (m // info["M"] ** info["levels"])
@@ -427,8 +446,19 @@ def main():
                 "peak_source": "FP64 DFMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clocks)",
                 "algorithmic_flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg,
                 "leaf_share_of_step": leaf_avg / ms_step}
+    elif p.precision == "tf32":
+        kpad = -(-kL // 32) * 32
+        leaf_flops = 2.0 * info["leaves"] * mL * kpad * nL
+        achieved = leaf_flops / leaf_avg / 1e9
+        peak, src = measured_bf16_peak()
+        peak, src = peak / 2.0, src + " x 1/2 (tf32 = half the bf16 rate, recipe nominal ratio)"
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "tf32_gemm (tcgen05 kind::tf32, all leaves)",
+                "peak_source": src, "algorithmic_flops_per_launch": leaf_flops,
+                "leaf_ms_avg": leaf_avg, "leaf_share_of_step": leaf_avg / ms_step}
     else:
-        nmod = args.moduli
+        nmod = p.moduli or args.moduli
         kpad = -(-kL // 64) * 64
         leaf_flops = 2.0 * info["leaves"] * nmod * mL * kpad * nL
         achieved = leaf_flops / leaf_avg / 1e9
@@ -463,22 +493,23 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if p.precision == "fp64" else f"bf16 residues x {args.moduli} (CRT-emulated f64)",
+            "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate)"}.get(
+                p.precision, f"bf16 residues x {p.moduli or args.moduli} (CRT-emulated f64)"),
             "data": "synthetic uniform[-1,1] (PCG64 seed 1410)",
             "config": {"workload": wl["desc"], "m": m, "k": k, "n": n, "plan": best["plan"],
                        "scheme": scheme_desc(p.flags, fmm), "leaf_tile": "auto",
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "rel_err_F": err, "rel_err_note": "e_F over the cpu_baseline's sampled rows vs the FP64 oracle",
-            "classical": {"value": ws * flops / ms_c / 1e9, "ms_per_step": ms_c, "rel_err_F": err_c,
-                          "what": "the library's classical FP64 GEMM (DFMA)"},
+            "classical": ({"value": ws * flops / ms_c / 1e9, "ms_per_step": ms_c, "rel_err_F": err_c,
+                           "what": "the library's classical FP64 GEMM (DFMA)"} if ms_c else None),
             "classical_emulated": ({"value": classical_same[0]["tflops"], "ms": classical_same[0]["ms"],
                                     "rel_err_F": classical_same[0]["rel_err_F"],
                                     "what": "the library's classical GEMM with emulated-FP64 leaves"}
                                    if classical_same else None),
-            "speedup_vs_classical": ms_c / ms_step,
+            "speedup_vs_classical": (ms_c / ms_step) if ms_c else None,
             "speedup_vs_classical_same_precision": (classical_same[0]["ms"] / ms_step
-                                                    if classical_same and p.precision != "fp64" else ms_c / ms_step),
+                                                    if classical_same else ((ms_c / ms_step) if ms_c else None)),
             "accuracy_target": args.tol,
             "plans": results,
             "roofline": roof,

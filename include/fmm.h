@@ -60,7 +60,12 @@ typedef enum {
        combination and the fringe stay FP64.  Error: truncation of the
        scaled operands to beta bits, beta = floor((log2 prod p - 1 -
        log2 k_L)/2) (about 51 bits for N = 15, k_L = 16384). */
-    FMM_PREC_OZAKI_BF16 = 3
+    FMM_PREC_OZAKI_BF16 = 3,
+    /* Leaf products on the tensor cores in TF32 (operands rounded to a
+       10-bit significand, FP32 accumulation), widened to FP64 for the W
+       combination; S/T formation and the fringe stay FP64.  Relative error
+       of order 2^-11 per leaf operand. */
+    FMM_PREC_TF32 = 2
 } fmm_precision;
 
 /* Execution-scheme flags (fmm_plan_create / fmm_plan_load `flags`). */

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfmm.so")
-SOURCES = ["plan.cpp", "fp64_kernels.cu", "api.cu", "noalloc.cu", "ozaki.cu"]
+SOURCES = ["plan.cpp", "fp64_kernels.cu", "api.cu", "noalloc.cu", "ozaki.cu", "tf32.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -128,8 +128,14 @@ ResPlan res_plan(const fmm_plan *p) {
 
 WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     WsLayout w;
-    const bool oz = p->prec == FMM_PREC_OZAKI_BF16;
-    if (oz && p->L > 0 && g.fast && residue_space(p)) {
+    const bool tf = p->prec == FMM_PREC_TF32;
+    const bool oz = p->prec == FMM_PREC_OZAKI_BF16 || tf;
+    if (tf && p->L == 0) {
+        w.oz = 0;
+        w.total = tf32_workspace(1, g.mp, g.kp, g.np);
+        return w;
+    }
+    if (!tf && oz && p->L > 0 && g.fast && residue_space(p)) {
         w.oz = 0;
         w.total = ozaki_fast_workspace(res_plan(p), g.mp, g.kp, g.np, p->nmod);
         return w;
@@ -180,7 +186,8 @@ WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     }
     if (oz) {
         w.oz = off;
-        off = align256(off + ozaki_workspace(p->leaves, p->nmod, g.mL, g.kL, g.nL));
+        off = align256(off + (tf ? tf32_workspace(p->leaves, g.mL, g.kL, g.nL)
+                                 : ozaki_workspace(p->leaves, p->nmod, g.mL, g.kL, g.nL)));
     }
     w.total = off;
     return w;
@@ -230,11 +237,19 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
                           int64_t m, int64_t k, int64_t n, char *wsb, cudaStream_t s,
                           int *launches) {
     cudaError_t e;
-    // (the timing pair, when enabled, brackets the residue GEMM inside)
+    // (the timing pair, when enabled, brackets the tensor-core GEMM inside)
+    const bool tf = p->prec == FMM_PREC_TF32;
+    auto leaf_products = [&](const double *S_, int64_t lds, int64_t ss, const double *T_, int64_t ldt,
+                             int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
+                             int64_t mm, int64_t kk, int64_t nn) {
+        return tf ? tf32_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, 0,
+                                  wsb + wl.oz, s, launches)
+                  : ozaki_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, p->nmod,
+                                   wsb + wl.oz, s, launches);
+    };
     if (p->L == 0)
-        return cuda_status(ozaki_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n, p->nmod,
-                                          wsb + wl.oz, s, launches));
-    if (residue_space(p)) {
+        return cuda_status(leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n));
+    if (!tf && residue_space(p)) {
         const bool kfr = g.kp < k;
         if (kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
                                          g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
@@ -269,9 +284,8 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
         parents *= p->R;
     }
     double *prod = (double *)(wsb + wl.lvP.back());
-    if ((e = ozaki_products(pa, g.kL, g.mL * g.kL, pb, g.nL, g.kL * g.nL, prod, g.nL,
-                            g.mL * g.nL, p->leaves, g.mL, g.kL, g.nL, p->nmod, wsb + wl.oz, s,
-                            launches)) != cudaSuccess)
+    if ((e = leaf_products(pa, g.kL, g.mL * g.kL, pb, g.nL, g.kL * g.nL, prod, g.nL, g.mL * g.nL,
+                           p->leaves, g.mL, g.kL, g.nL)) != cudaSuccess)
         return cuda_status(e);
     const bool kfringe = g.kp < k;
     if (kfringe &&
@@ -307,7 +321,7 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
                     size_t ws_bytes, cudaStream_t s, int *launches) {
     const Geometry g = geometry(p, m, k, n);
-    if (p->prec == FMM_PREC_OZAKI_BF16 && (p->L == 0 || g.fast)) {
+    if ((p->prec == FMM_PREC_OZAKI_BF16 || p->prec == FMM_PREC_TF32) && (p->L == 0 || g.fast)) {
         // int32 drain sums stay below 2^31 for k_L <= 65536 (2^23 per 512-chunk)
         if (g.kL > 65536) return FMM_ERR_UNSUPPORTED;
         const WsLayout wl = ws_layout(p, g);
@@ -484,7 +498,8 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (M < 1 || K < 1 || N < 1 || R < 1 || R > 4096) return FMM_ERR_ARG;
     if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
     if (levels < 0 || levels > 6) return FMM_ERR_ARG;
-    if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16) return FMM_ERR_UNSUPPORTED;
+    if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16 && prec != FMM_PREC_TF32)
+        return FMM_ERR_UNSUPPORTED;
     if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE |
                           FMM_FLAG_LEAF_EMULATION))
         return FMM_ERR_ARG;
@@ -543,6 +558,7 @@ fmm_status fmm_plan_prepare(fmm_plan_t p) {
     fmm_status st = ensure_uploaded(p);
     if (st != FMM_OK) return st;
     if (p->prec == FMM_PREC_OZAKI_BF16 && ozaki_prepare(p->nmod) != cudaSuccess) return FMM_ERR_CUDA;
+    if (p->prec == FMM_PREC_TF32 && tf32_prepare() != cudaSuccess) return FMM_ERR_CUDA;
     if (prepare_fp64_kernels() != cudaSuccess) return FMM_ERR_CUDA;
     return FMM_OK;
 }
@@ -554,9 +570,10 @@ fmm_status fmm_plan_set_moduli(fmm_plan_t p, int n_moduli) {
 }
 
 fmm_status fmm_check_device_error(void) {
-    int flag = 0;
+    int flag = 0, flag2 = 0;
     if (read_device_error(&flag, true) != cudaSuccess) return FMM_ERR_CUDA;
-    return flag ? FMM_ERR_TIMEOUT : FMM_OK;
+    if (read_tf32_error(&flag2, true) != cudaSuccess) return FMM_ERR_CUDA;
+    return (flag || flag2) ? FMM_ERR_TIMEOUT : FMM_OK;
 }
 
 fmm_status fmm_plan_info(fmm_plan_t p, fmm_plan_info_t *info) {

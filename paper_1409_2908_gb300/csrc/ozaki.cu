@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "fmm_internal.h"
+#include "tcgen05.cuh"
 
 namespace fmm {
 
@@ -45,7 +46,6 @@ constexpr int OZ_THREADS = 192;         // warps 0-3 drain, 4 loads, 5 issues MM
 constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2, OZ_B_BYTES = OZ_BN * OZ_BK * 2;
 constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
-constexpr long long OZ_WAIT_LIMIT = 1ll << 26;
 constexpr int OZ_MAX_MOD = 20;
 
 __constant__ int c_mod[OZ_MAX_MOD];                       // moduli
@@ -62,49 +62,7 @@ __device__ __forceinline__ unsigned mod_u32(unsigned x, int q) {
     return r >= p ? r - p : r;
 }
 
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t cnt) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(cnt) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
-    const uint32_t a = su32(b);
-    for (long long i = 0; i < OZ_WAIT_LIMIT; ++i) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z, uint64_t *bar) {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                 ::"r"(su32(dst)), "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(su32(bar)) : "memory");
-}
-// Shared-memory matrix descriptor: K-major tile of 128-byte rows, 128-byte
-// swizzle, 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar)) : "memory");
-}
+using namespace tc;
 
 // Balanced residue of x (|x| < 2^31) modulo p.
 __device__ __forceinline__ int bal_mod(int x, int p) {
@@ -378,39 +336,84 @@ __device__ __forceinline__ double int128_to_double(__int128 x) {
     return neg ? -d : d;
 }
 
-// C[leaf][i][j] = (Z from its residues) * 2^-(sa_i + sb_j).
-__global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves, int nmod,
-                           const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride,
-                           int accumulate) {
-    const int64_t total = leaves * m * n;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t leaf = g / (m * n), rem = g % (m * n), i = rem / n, j = rem % n;
-        // mixed-radix digits v_q of Z (balanced): Z = sum_q v_q prod_{l<q} p_l
-        int v[OZ_MAX_MOD];
+// Exact scaling of an FP64 value by 2^e (x an integer-valued double, so no
+// rounding unless the result leaves the normal range; then ldexp).
+__device__ __forceinline__ double scale_pow2(double x, int e) {
+    if (e > -1022 && e < 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(x, e);
+}
+
+// Z from its N residues (Garner's mixed-radix digits, exact 128-bit Horner,
+// one correct rounding) times 2^-(sa_i + sb_j); V consecutive columns per
+// thread (one 4-byte load per modulus when V == 4).
+template <int V>
+__device__ __forceinline__ void crt_values(const int8_t *Z, int64_t plane0, int64_t plane, int nmod,
+                                           double *vals) {
+    int v[V][OZ_MAX_MOD];
 #pragma unroll
-        for (int q = 0; q < OZ_MAX_MOD; ++q) {
-            if (q >= nmod) break;
-            const int p = c_mod[q];
-            const int z = Z[((leaf * nmod + q) * m + i) * n + j];
-            int sum = z;
+    for (int q = 0; q < OZ_MAX_MOD; ++q) {
+        if (q >= nmod) break;
+        int z[V];
+        if (V == 4) {
+            const int raw = *reinterpret_cast<const int *>(Z + plane0 + (int64_t)q * plane);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) z[e] = (int)(int8_t)(raw >> (8 * e));
+        } else {
+            z[0] = Z[plane0 + (int64_t)q * plane];
+        }
+        const int p = c_mod[q];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            int sum = z[e];
 #pragma unroll
             for (int l = 0; l < OZ_MAX_MOD; ++l) {
                 if (l >= q) break;
-                sum -= v[l] * c_wmod[l][q];
+                sum -= v[e][l] * c_wmod[l][q];
             }
-            // sum lies in (-2^20, 2^20): shift it positive, reduce, scale by the inverse
             const unsigned t = mod_u32((unsigned)(sum + (p << 13)), q);
             const int d = (int)mod_u32(t * (unsigned)c_winv[q], q);
-            v[q] = d >= (p + 1) / 2 ? d - p : d;
+            v[e][q] = d >= (p + 1) / 2 ? d - p : d;
         }
-        // Z = sum_q v_q prod_{l<q} p_l by Horner's rule in exact 128-bit
-        // integers (|Z| < P/2 < 2^127 for N <= 16), then one correct rounding
-        __int128 x = v[nmod - 1];
-        for (int q = nmod - 2; q >= 0; --q) x = x * c_mod[q] + v[q];
-        const int e = -(sa[leaf * m + i] + sb[leaf * n + j]);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        __int128 x = v[e][nmod - 1];
+        for (int q = nmod - 2; q >= 0; --q) x = x * c_mod[q] + v[e][q];
+        vals[e] = int128_to_double(x);
+    }
+}
+
+// C[leaf][i][j] (+)= (Z from its residues) * 2^-(sa_i + sb_j).
+__global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves, int nmod,
+                           const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride,
+                           int accumulate) {
+    const int64_t plane = m * n;
+    if (n % 4 == 0) {
+        const int64_t total = leaves * plane / 4;
+        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+             g += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t e0 = g * 4;
+            const int64_t leaf = e0 / plane, rem = e0 % plane, i = rem / n, j = rem % n;
+            double vals[4];
+            crt_values<4>(Z, leaf * nmod * plane + rem, plane, nmod, vals);
+            double *out = C + leaf * leaf_stride + i * ldc + j;
+            const int ei = sa[leaf * m + i];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const double val = scale_pow2(vals[e], -(ei + sb[leaf * n + j + e]));
+                out[e] = accumulate ? out[e] + val : val;
+            }
+        }
+        return;
+    }
+    const int64_t total = leaves * plane;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t leaf = g / plane, rem = g % plane, i = rem / n, j = rem % n;
+        double val;
+        crt_values<1>(Z, leaf * nmod * plane + rem, plane, nmod, &val);
+        val = scale_pow2(val, -(sa[leaf * m + i] + sb[leaf * n + j]));
         double *out = C + leaf * leaf_stride + i * ldc + j;
-        const double val = ldexp(int128_to_double(x), e);
         *out = accumulate ? *out + val : val;
     }
 }

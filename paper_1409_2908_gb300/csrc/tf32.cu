@@ -1,0 +1,308 @@
+// TF32 leaf products on the tensor cores (precision variant FMM_PREC_TF32):
+// the FP64 leaf operands S_r, T_r are rounded to TF32 (10-bit significand,
+// round to nearest) in FP32 K-major layout, multiplied by tcgen05
+// (kind::tf32, FP32 accumulation in TMEM over the whole k), and the FP32
+// products are widened back to FP64 for the W combination.  Expected
+// relative error ~ 2^-11 per operand; stated per result by the benchmark.
+//
+// Same pipeline as the emulated-FP64 residue GEMM: persistent CTAs, TMA
+// (128-byte swizzle) into a 6-stage mbarrier ring, one load thread, one MMA
+// thread, four drain warps; two TMEM accumulators let a tile's drain overlap
+// the next tile's MMAs.  Every wait is bounded.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "fmm_internal.h"
+#include "tcgen05.cuh"
+
+namespace fmm {
+
+__device__ int g_tf32_error = 0;   // set when a bounded wait gives up
+
+namespace {
+
+using namespace tc;
+
+constexpr int TB_M = 128, TB_N = 128, TB_K = 32, TB_STAGES = 6;   // TB_K fp32 = 128 bytes
+constexpr int TB_A = TB_M * TB_K * 4, TB_B = TB_N * TB_K * 4, TB_STAGE = TB_A + TB_B;
+constexpr int TB_TBUF = 2;
+constexpr int TB_THREADS = 192;
+constexpr int TB_SMEM = TB_STAGES * TB_STAGE + 1024 + 256;
+
+__global__ void __launch_bounds__(TB_THREADS, 1)
+tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          double *Out, int64_t m, int64_t n, int kblocks, int tiles_m, int tiles_n,
+          int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + TB_STAGES * TB_STAGE);
+    uint64_t *empty = full + TB_STAGES;
+    uint64_t *tfull = empty + TB_STAGES;
+    uint64_t *tempty = tfull + TB_TBUF;
+    uint32_t *tmem_slot = (uint32_t *)(tempty + TB_TBUF);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int64_t per_plane = (int64_t)tiles_m * tiles_n;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TB_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < TB_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 128); }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(su32(tmem_slot)), "r"(TB_TBUF * TB_N) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            int64_t g = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                const int z = int(tile / per_plane);
+                const int rem = int(tile % per_plane);
+                const int tm = rem / tiles_n, tn = rem % tiles_n;
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int s = int(g % TB_STAGES);
+                    if (g >= TB_STAGES && !mbar_wait(&empty[s], uint32_t(((g / TB_STAGES) - 1) & 1))) {
+                        atomicExch(err, 1);
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *sa = smem + s * TB_STAGE, *sb = sa + TB_A;
+                    mbar_expect_tx(&full[s], TB_STAGE);
+                    tma_load_3d(sa, &tmA, kb * TB_K, tm * TB_M, z, &full[s]);
+                    tma_load_3d(sb, &tmB, kb * TB_K, tn * TB_N, z, &full[s]);
+                }
+            }
+        }
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // FP32 accumulator, TF32 A and B, both K-major
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
+                                   ((uint32_t)(TB_N >> 3) << 17) | ((uint32_t)(TB_M >> 4) << 24);
+            bool ok = true;
+            int64_t g = 0, it = 0;
+            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
+                const int b = int(it % TB_TBUF);
+                if (it >= TB_TBUF && !mbar_wait(&tempty[b], uint32_t(((it / TB_TBUF) - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(b * TB_N);
+                for (int kb = 0; kb < kblocks; ++kb, ++g) {
+                    const int s = int(g % TB_STAGES);
+                    if (!mbar_wait(&full[s], uint32_t((g / TB_STAGES) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = su32(smem + s * TB_STAGE), b0 = a0 + TB_A;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)   // K = 8 tf32 (32 bytes) per MMA
+                        mma_tf32(acc, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                 (kb == 0 && kk == 0) ? 0u : 1u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[b]);
+            }
+            if (!ok) atomicExch(err, 1);
+        }
+    } else {
+        bool ok = true;
+        int64_t it = 0;
+        for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
+            const int z = int(tile / per_plane);
+            const int rem = int(tile % per_plane);
+            const int tm = rem / tiles_n, tn = rem % tiles_n;
+            const int b = int(it % TB_TBUF);
+            if (!mbar_wait(&tfull[b], uint32_t((it / TB_TBUF) & 1))) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TB_N);
+            const int64_t row = (int64_t)tm * TB_M + warp * 32 + lane;
+            const int64_t cols = min((int64_t)TB_N, n - (int64_t)tn * TB_N);
+            double *out = Out + (int64_t)z * out_stride + row * ldo + (int64_t)tn * TB_N;
+#pragma unroll
+            for (int c0 = 0; c0 < TB_N; c0 += 16) {
+                uint32_t r[16];
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                             : "r"(base + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < m) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if (c0 + j < cols) {
+                            const double v = (double)__uint_as_float(r[j]);
+                            out[c0 + j] = accumulate ? out[c0 + j] + v : v;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&tempty[b]);
+        }
+        if (!ok && lane == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TB_TBUF * TB_N) : "memory");
+}
+
+__device__ __forceinline__ float to_tf32(double x) {
+    float f = (float)x;
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    return __uint_as_float(r);
+}
+
+// X (rows x cols per plane, ld, plane stride) -> TF32 in FP32, rows padded to kpad.
+__global__ void tf32_rows(const double *X, int64_t ldx, int64_t xs, int64_t rows, int64_t cols,
+                          int64_t kpad, int64_t planes, float *out) {
+    const int64_t total = planes * rows * kpad;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t pl = g / (rows * kpad), rem = g % (rows * kpad), i = rem / kpad, j = rem % kpad;
+        out[g] = j < cols ? to_tf32(X[pl * xs + i * ldx + j]) : 0.0f;
+    }
+}
+
+// Y (rows x cols per plane) -> TF32 of Y^T (cols x kpad), through 32x32 tiles.
+__global__ void tf32_cols_t(const double *Y, int64_t ldy, int64_t ys, int64_t rows, int64_t cols,
+                            int64_t kpad, float *out) {
+    __shared__ float tile[32][33];
+    const int64_t pl = blockIdx.z;
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        tile[r][tx] = (i < rows && j < cols) ? to_tf32(Y[pl * ys + i * ldy + j]) : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t j = j0 + r, i = i0 + tx;
+        if (j < cols && i < kpad) out[(pl * cols + j) * kpad + i] = tile[tx][r];
+    }
+}
+
+typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                             const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                             CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                             CUtensorMapFloatOOBfill);
+
+std::mutex g_tf_mu;
+EncodeFn g_tf_encode = nullptr;
+
+cudaError_t map3d_f32(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int64_t planes) {
+    {
+        std::lock_guard<std::mutex> g(g_tf_mu);
+        if (!g_tf_encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+            if (e != cudaSuccess) return e;
+            if (!fn || q != cudaDriverEntryPointSuccess) return cudaErrorNotSupported;
+            g_tf_encode = (EncodeFn)fn;
+        }
+    }
+    cuuint64_t gdim[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
+    cuuint64_t gstr[2] = {(cuuint64_t)kpad * 4, (cuuint64_t)(kpad * rows * 4)};
+    cuuint32_t box[3] = {(cuuint32_t)TB_K, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = g_tf_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ptr, gdim, gstr, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int sm_count() {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace
+
+size_t tf32_workspace(int64_t leaves, int64_t m, int64_t k, int64_t n) {
+    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return al(size_t(leaves) * m * kpad * 4) + al(size_t(leaves) * n * kpad * 4);
+}
+
+cudaError_t tf32_prepare() {
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 64 && !configured[dev]) {
+        if ((e = cudaFuncSetAttribute(tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM)) !=
+            cudaSuccess)
+            return e;
+        configured[dev] = true;
+    }
+    int *err = nullptr;
+    return cudaGetSymbolAddress((void **)&err, g_tf32_error);
+}
+
+cudaError_t read_tf32_error(int *flag, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(flag, g_tf32_error, sizeof(int));
+    if (e != cudaSuccess) return e;
+    if (clear && *flag) {
+        const int zero = 0;
+        e = cudaMemcpyToSymbol(g_tf32_error, &zero, sizeof(int));
+    }
+    return e;
+}
+
+// Out[leaf] (m x n, ldo, leaf stride os) (+)= tf32(S[leaf]) tf32(T[leaf]).
+cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
+                          int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
+                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches) {
+    cudaError_t e = tf32_prepare();
+    if (e != cudaSuccess) return e;
+    int *err = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&err, g_tf32_error)) != cudaSuccess) return e;
+    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K;
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+    float *fa = (float *)ws;
+    float *fb = (float *)((char *)ws + al(size_t(leaves) * m * kpad * 4));
+    {
+        const int64_t total = leaves * m * kpad;
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+        tf32_rows<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, fa);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        if (leaves > 65535) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
+        tf32_cols_t<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, fb);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    CUtensorMap ta, tb;
+    if ((e = map3d_f32(&ta, fa, kpad, m, leaves)) != cudaSuccess) return e;
+    if ((e = map3d_f32(&tb, fb, kpad, n, leaves)) != cudaSuccess) return e;
+    const int64_t tm = (m + TB_M - 1) / TB_M, tn = (n + TB_N - 1) / TB_N;
+    const int64_t tiles = tm * tn * leaves;
+    const unsigned ctas = (unsigned)std::min<int64_t>(tiles, sm_count());
+    cudaEvent_t t0 = timing_mark(s);
+    tf32_gemm<<<ctas, TB_THREADS, TB_SMEM, s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm), int(tn),
+                                                tiles, ldo, os, accumulate, err);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (t0 && !timing_mark(s)) timing_unmark();
+    return cudaSuccess;
+}
+
+}  // namespace fmm
