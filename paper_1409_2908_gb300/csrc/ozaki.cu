@@ -39,13 +39,9 @@ __device__ int g_device_error = 0;   // set when a bounded wait gives up
 
 namespace {
 
-constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64, OZ_STAGES = 6;
+constexpr int OZ_BM = 128, OZ_BK = 64;
 constexpr int OZ_CHUNK_KB = 8;          // 8 x 64 = 512 k per exact FP32 chunk
-constexpr int OZ_TBUF = 4;              // TMEM accumulators of 128 columns
-constexpr int OZ_THREADS = 192;         // warps 0-3 drain, 4 loads, 5 issues MMAs
-constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2, OZ_B_BYTES = OZ_BN * OZ_BK * 2;
-constexpr int OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE_BYTES + 1024 + 256;
+constexpr int OZ_A_BYTES = OZ_BM * OZ_BK * 2;
 constexpr int OZ_MAX_MOD = 20;
 
 __constant__ int c_mod[OZ_MAX_MOD];                       // moduli
@@ -84,10 +80,29 @@ __device__ __forceinline__ int bal_mod_q(int x, int q) {
 // drain roles walk the same tile sequence, so stage and TMEM-buffer phases
 // continue across tiles and the tensor core never waits for a tile's final
 // reduction (four TMEM buffers of slack).
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+template <int BN>
+struct OzCfg;
+template <>
+struct OzCfg<128> {   // 4 drain warps, 4 TMEM accumulators, 6 stages of 32 KB
+    static constexpr int TBUF = 4, DRAIN_WARPS = 4, STAGES = 6;
+};
+template <>
+struct OzCfg<256> {   // 8 drain warps (two column halves), 2 accumulators, 4 stages of 48 KB
+    static constexpr int TBUF = 2, DRAIN_WARPS = 8, STAGES = 4;
+};
+template <int BN>
+constexpr int oz_threads() { return (OzCfg<BN>::DRAIN_WARPS + 2) * 32; }
+template <int BN>
+constexpr int oz_smem() { return OzCfg<BN>::STAGES * (OZ_A_BYTES + BN * OZ_BK * 2) + 1024 + 256; }
+
+template <int BN>
+__global__ void __launch_bounds__(oz_threads<BN>(), 1)
 residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              int8_t *Z, int64_t m, int64_t n, int kblocks, int nmod, int tiles_m, int tiles_n,
              int64_t tiles_total, int *err) {
+    constexpr int OZ_TBUF = OzCfg<BN>::TBUF, OZ_STAGES = OzCfg<BN>::STAGES;
+    constexpr int DW = OzCfg<BN>::DRAIN_WARPS;
+    constexpr int OZ_BN = BN, OZ_B_BYTES = BN * OZ_BK * 2, OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = (uint64_t *)(smem + OZ_STAGES * OZ_STAGE_BYTES);
@@ -100,7 +115,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < OZ_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 128); }
+        for (int b = 0; b < OZ_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], DW * 32); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -114,7 +129,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     const uint32_t tmem = *tmem_slot;
     const int64_t per_plane = (int64_t)tiles_m * tiles_n;
 
-    if (warp == 4) {
+    if (warp == DW) {
         if (lane == 0) {
             int64_t g = 0;   // global k-block counter: stage and phase
             bool ok = true;
@@ -136,7 +151,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == DW + 1) {
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                    ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
@@ -170,7 +185,9 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             if (!ok) atomicExch(err, 1);
         }
     } else {
-        // warps 0-3 drain: TMEM lanes 32*warp .. +31 are rows of the tile
+        // drain warps: warp w reads TMEM lanes 32*(w%4)..+31 (rows of the tile)
+        // and the 128-column half w/4 of the accumulator
+        const int lg = warp % 4, ch = warp / 4;
         bool ok = true;
         int64_t cg = 0;
         for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
@@ -179,16 +196,16 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const int tm = rem / tiles_n, tn = rem % tiles_n;
             const int q = z % nmod;
             const int p = c_mod[q];
-            int acc[OZ_BN];
+            int acc[128];
 #pragma unroll
-            for (int j = 0; j < OZ_BN; ++j) acc[j] = 0;
+            for (int j = 0; j < 128; ++j) acc[j] = 0;
             for (int c = 0; c < nchunks; ++c, ++cg) {
                 const int b = int(cg % OZ_TBUF);
                 if (!mbar_wait(&tfull[b], uint32_t((cg / OZ_TBUF) & 1))) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * OZ_BN);
+                const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * OZ_BN + ch * 128);
 #pragma unroll
-                for (int c0 = 0; c0 < OZ_BN; c0 += 16) {
+                for (int c0 = 0; c0 < 128; c0 += 16) {
                     uint32_t r[16];
                     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
@@ -202,14 +219,15 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 mbar_arrive(&tempty[b]);
             }
             if (!ok) break;
-            const int64_t row = (int64_t)tm * OZ_BM + warp * 32 + lane;
+            const int64_t row = (int64_t)tm * OZ_BM + lg * 32 + lane;
             if (row < m) {
-                int8_t *out = Z + ((int64_t)z * m + row) * n + (int64_t)tn * OZ_BN;
-                const int64_t cols = min((int64_t)OZ_BN, n - (int64_t)tn * OZ_BN);
+                const int64_t col0 = (int64_t)tn * OZ_BN + ch * 128;
+                int8_t *out = Z + ((int64_t)z * m + row) * n + col0;
+                const int64_t cols = min((int64_t)128, n - col0);
                 // |acc| < 2^28: shift positive by p 2^22 (< 2^31) for one Barrett step
-                if (cols == OZ_BN && n % 16 == 0) {
+                if (cols == 128 && n % 16 == 0) {
 #pragma unroll
-                    for (int j0 = 0; j0 < OZ_BN; j0 += 16) {
+                    for (int j0 = 0; j0 < 128; j0 += 16) {
                         __align__(16) int8_t h[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
@@ -220,7 +238,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < OZ_BN; ++j)
+                    for (int j = 0; j < 128; ++j)
                         if (j < cols) out[j] = (int8_t)bal_mod(acc[j], p);
                 }
             }
@@ -625,19 +643,26 @@ int num_sms() {
     return sms;
 }
 
-cudaError_t configure_residue_gemm() {
+template <int BN>
+cudaError_t configure_residue_gemm_bn() {
     static bool configured[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 64 && !configured[dev]) {
-        if ((e = cudaFuncSetAttribute(residue_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      OZ_SMEM)) != cudaSuccess)
+        if ((e = cudaFuncSetAttribute(residue_gemm<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      oz_smem<BN>())) != cudaSuccess)
             return e;
         configured[dev] = true;
     }
     return cudaSuccess;
 }
+
+cudaError_t configure_residue_gemm() {
+    cudaError_t e = configure_residue_gemm_bn<128>();
+    return e != cudaSuccess ? e : configure_residue_gemm_bn<256>();
+}
+
 
 long long mod_pow_inv(long long a, long long p) {
     // inverse of a modulo p (a, p coprime) by the extended Euclidean algorithm
@@ -693,6 +718,34 @@ cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, in
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// One persistent launch over all tiles of all planes; N = 256 tiles when the
+// planes are at least 256 wide.
+cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64_t m, int64_t n,
+                                int64_t kpad, int64_t planes, int nmod, int *err, cudaStream_t s,
+                                int *launches) {
+    cudaError_t e;
+    if ((e = configure_residue_gemm()) != cudaSuccess) return e;
+    const bool wide = n >= 256;
+    const int bn = wide ? 256 : 128;
+    CUtensorMap ta, tb;
+    if ((e = make_map3d(&ta, (void *)ra, kpad, m, planes, OZ_BM)) != cudaSuccess) return e;
+    if ((e = make_map3d(&tb, (void *)rb, kpad, n, planes, bn)) != cudaSuccess) return e;
+    const int64_t tn = (n + bn - 1) / bn, tmb = (m + OZ_BM - 1) / OZ_BM;
+    const int64_t tiles = tn * tmb * planes;
+    const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
+    cudaEvent_t t0 = timing_mark(s);
+    if (wide)
+        residue_gemm<256><<<ctas, oz_threads<256>(), oz_smem<256>(), s>>>(
+            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+    else
+        residue_gemm<128><<<ctas, oz_threads<128>(), oz_smem<128>(), s>>>(
+            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (t0 && !timing_mark(s)) timing_unmark();
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -846,22 +899,9 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int64_t mL = pm, kL = pk, nL = pn, leaves = parents;
     const int64_t kpadL = (kL + OZ_BK - 1) / OZ_BK * OZ_BK;
     int8_t *Z = (int8_t *)(b + w.zres);
-    {
-        CUtensorMap ta, tb;
-        if ((e = make_map3d(&ta, b + w.la.back(), kpadL, mL, leaves * nmod, OZ_BM)) != cudaSuccess) return e;
-        if ((e = make_map3d(&tb, b + w.lb.back(), kpadL, nL, leaves * nmod, OZ_BN)) != cudaSuccess) return e;
-        if ((e = configure_residue_gemm()) != cudaSuccess) return e;
-        const int64_t planes = leaves * nmod;
-        const int64_t tn = (nL + OZ_BN - 1) / OZ_BN, tmb = (mL + OZ_BM - 1) / OZ_BM;
-        if (planes > (1 << 24)) return cudaErrorInvalidValue;
-        cudaEvent_t t0 = timing_mark(s);
-        const int64_t tiles = tn * tmb * planes;
-        const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
-        residue_gemm<<<ctas, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, Z, mL, nL, int(kpadL / OZ_BK), nmod,
-                                                       int(tmb), int(tn), tiles, err);
-        if ((e = check()) != cudaSuccess) return e;
-        if (t0 && !timing_mark(s)) timing_unmark();
-    }
+    if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, leaves * nmod, nmod,
+                                 err, s, launches)) != cudaSuccess)
+        return e;
     // W level by level, down to the residues of C'
     int64_t cm = mL, cn = nL;
     const int8_t *child = Z;
@@ -940,23 +980,9 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    {
-        CUtensorMap ta, tb;
-        if ((e = make_map3d(&ta, ra, kpad, m, leaves * nmod, OZ_BM)) != cudaSuccess) return e;
-        if ((e = make_map3d(&tb, rb, kpad, n, leaves * nmod, OZ_BN)) != cudaSuccess) return e;
-        if ((e = configure_residue_gemm()) != cudaSuccess) return e;
-        const int64_t planes = leaves * nmod;
-        const int64_t tn = (n + OZ_BN - 1) / OZ_BN, tmb = (m + OZ_BM - 1) / OZ_BM;
-        if (planes > (1 << 24)) return cudaErrorInvalidValue;
-        cudaEvent_t t0 = timing_mark(s);
-        const int64_t tiles = tn * tmb * planes;
-        const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
-        residue_gemm<<<ctas, OZ_THREADS, OZ_SMEM, s>>>(ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb),
-                                                       int(tn), tiles, err);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (t0 && !timing_mark(s)) timing_unmark();
-    }
+    if ((e = launch_residue_gemm(ra, rb, Z, m, n, kpad, leaves * nmod, nmod, err, s, launches)) !=
+        cudaSuccess)
+        return e;
     {
         const int64_t total = leaves * m * n;
         const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);

@@ -7,10 +7,11 @@ throughput.
   * Requests are admitted in arrival order while their output and workspace
     fit the memory budget and a stream slot is free; a request arriving while
     others run is admitted as soon as slots and memory free up.
-  * Admitted requests that share a plan and a shape form a group; the group's
-    products are captured into one CUDA graph on the slot's stream and
-    replayed (graphs are cached per plan, shape and slot, with fixed
-    operand buffers, so a recurring shape replays without capture).
+  * Admitted requests that share a plan and a shape form a group.  A shape
+    that recurs is replayed from a CUDA graph captured once per plan, shape
+    and slot (fixed operand buffers; capture runs on the slot's stream
+    without a device-wide synchronisation); a shape's first occurrence runs
+    directly.
   * Groups on different streams overlap on the device; completion is polled
     with CUDA events.
 
@@ -96,6 +97,7 @@ class Server:
         self.graph_cache_bytes = graph_cache_bytes if graph_cache_bytes is not None else self.budget // 2
         self._graphs = OrderedDict()      # (plan key, shape, slot) -> _Graph
         self._graph_bytes = 0
+        self._seen = {}
         self.used = 0
         self.stats = Stats()
 
@@ -134,9 +136,15 @@ class Server:
         ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
         stream = self.streams[slot]
         graph = torch.cuda.CUDAGraph()
-        torch.cuda.synchronize()
-        with torch.cuda.graph(graph, stream=stream, capture_error_mode="relaxed"):
-            fmm.gemm(plan, A, B, C=C, workspace=ws, stream=torch.cuda.current_stream())
+        # capture on the slot's own stream: no device-wide synchronisation, so
+        # groups running on the other streams keep going
+        stream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(stream):
+            graph.capture_begin(capture_error_mode="relaxed")
+            try:
+                fmm.gemm(plan, A, B, C=C, workspace=ws, stream=stream)
+            finally:
+                graph.capture_end()
         g = _Graph(graph, A, B, C, ws, nbytes)
         self._graphs[key] = g
         self._graph_bytes += nbytes
@@ -151,7 +159,11 @@ class Server:
         with torch.cuda.stream(stream):
             for r in group_reqs:
                 r.C = torch.empty((m, n), dtype=torch.float64, device="cuda")
-                if self.use_graphs:
+                shape_key = (id(plan), (m, k, n))
+                self._seen[shape_key] = self._seen.get(shape_key, 0) + 1
+                # a shape seen before is replayed from a captured graph; the
+                # first occurrence runs directly (capturing a one-off shape buys nothing)
+                if self.use_graphs and self._seen[shape_key] > 1:
                     g = self._graph_for(plan, (m, k, n), slot)
                     g.A.copy_(r.A, non_blocking=True)
                     g.B.copy_(r.B, non_blocking=True)
