@@ -11,7 +11,14 @@ lifted from GF(2) to the 2-adic integers (Hensel lifting: one linear solve
 over GF(2) per bit) and each coefficient is read back as a small rational by
 rational reconstruction; the result is checked exactly against Eq. (2).
 
+For larger cases (<4,2,4;26>) the walk runs in C (flipwalk.c, compiled with
+gcc on first use): it adds plus transitions that split two terms into three,
+so isolated rank-R schemes can be left, and emits the sparsest rank-R scheme
+of each window; every emitted scheme is lifted and the sparsest one with
+dyadic coefficients is written.
+
 Usage: python -m paper_1409_2908_gb300.algorithms.flip2 M K N R [--workers W] [--out FILE]
+       python -m paper_1409_2908_gb300.algorithms.flip2 M K N R --c-walker [--seconds S]
 """
 import argparse
 import multiprocessing as mp
@@ -221,6 +228,48 @@ def attempt(args):
     return seed, None, f"mod-2 rank {len(terms)} after {info} steps, lift failed"
 
 
+def _c_walker_bin():
+    import subprocess
+    import tempfile
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "flipwalk.c")
+    out = os.path.join(tempfile.gettempdir(), f"flipwalk_{os.getpid()}")
+    subprocess.run(["gcc", "-O2", "-o", out, src], check=True)
+    return out
+
+
+def c_walk(M, K, N, R, seeds, seconds, windows=100000, gap=50):
+    """Run the C walker on several seeds in parallel for `seconds` and lift
+    every emitted scheme; returns the sparsest exact dyadic (U, V, W)."""
+    import subprocess
+    from .search import nnz
+    exe = _c_walker_bin()
+    procs = [subprocess.Popen(["timeout", str(seconds), exe, str(M), str(K), str(N), str(R), str(s),
+                               str(10 ** 12), "200000", str(windows), str(gap)],
+                              stdout=subprocess.PIPE, text=True) for s in seeds]
+    lines = []
+    for p in procs:
+        lines += p.communicate()[0].splitlines()
+    os.unlink(exe)
+
+    def weight(line):
+        return sum(bin(int(x, 16)).count("1") for x in line.replace(";", " ").split())
+
+    best = None
+    for line in sorted(set(lines), key=weight)[:60]:
+        terms = [[int(x, 16) for x in t.split()] for t in line.split(";")]
+        for bits in (8, 40):
+            ex = lift(M, K, N, [list(t) for t in terms], bits=bits)
+            if ex is not None:
+                break
+        if ex is None:
+            continue
+        dyadic = all((v.denominator & (v.denominator - 1)) == 0 for F in ex for row in F for v in row)
+        tot = sum(nnz(F) for F in ex)
+        if dyadic and (best is None or tot < best[0]):
+            best = (tot, ex)
+    return best
+
+
 def main():
     from .search import write_fmm, nnz
     ap = argparse.ArgumentParser()
@@ -231,7 +280,19 @@ def main():
     ap.add_argument("--steps", type=int, default=3_000_000)
     ap.add_argument("--plateau", type=int, default=200_000)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--c-walker", action="store_true", help="walk in C with plus transitions")
+    ap.add_argument("--seconds", type=int, default=300)
     a = ap.parse_args()
+    if a.c_walker:
+        best = c_walk(a.M, a.K, a.N, a.R, range(1, a.workers + 1), a.seconds)
+        if best is None:
+            return 1
+        tot, (Uf, Vf, Wf) = best
+        out = a.out or f"fmm_{a.M}{a.K}{a.N}_{a.R}.fmm"
+        write_fmm(out, a.M, a.K, a.N, a.R, Uf, Vf, Wf,
+                  f"found by a GF(2) flip-graph walk with plus transitions and Hensel lifting, nnz {tot}")
+        print("wrote", out, "nnz", tot)
+        return 0
     for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[var] = "1"
     t0 = time.time()
