@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -113,7 +114,14 @@ struct WsLayout {
 // The whole recursion runs on residues when the base coefficients are
 // integers (the plan layer checks) and per-leaf emulation was not asked for.
 bool residue_space(const fmm_plan *p) {
-    return p->integer_coefs && !(p->flags & FMM_FLAG_LEAF_EMULATION);
+    if (!p->integer_coefs || (p->flags & FMM_FLAG_LEAF_EMULATION)) return false;
+    // the residue kernels stage one level's term lists in shared memory
+    auto nnz = [](const std::vector<double> &F) {
+        size_t c = 0;
+        for (double x : F) c += x != 0.0;
+        return c;
+    };
+    return p->R <= 64 && p->M * p->N <= 64 && nnz(p->U) <= 512 && nnz(p->V) <= 512 && nnz(p->W) <= 512;
 }
 
 ResPlan res_plan(const fmm_plan *p) {
@@ -123,6 +131,12 @@ ResPlan res_plan(const fmm_plan *p) {
     rp.v_ptr = p->dev.lv_ptr; rp.v_code = p->dev.lv_code; rp.v_icoef = p->dev.lv_icoef;
     rp.vt_code = p->dev.lvt_code;
     rp.w_ptr = p->dev.lw_ptr; rp.w_r = p->dev.lw_r; rp.w_icoef = p->dev.lw_icoef;
+    rp.w_absmax = 0;
+    for (int q = 0; q < p->M * p->N; ++q) {
+        double sum = 0;
+        for (int r = 0; r < p->R; ++r) sum += std::fabs(p->W[size_t(q) * p->R + r]);
+        rp.w_absmax = std::max(rp.w_absmax, int(sum));
+    }
     return rp;
 }
 
@@ -141,9 +155,9 @@ WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
         return w;
     }
     if (oz && p->L == 0) {
-        // the whole product is one emulated leaf
+        // the whole product is one emulated product (the residue path with no level)
         w.oz = 0;
-        w.total = ozaki_workspace(1, p->nmod, g.mp, g.kp, g.np);
+        w.total = ozaki_fast_workspace(res_plan(p), g.mp, g.kp, g.np, p->nmod);
         return w;
     }
     if (!g.fast) return w;
@@ -248,7 +262,9 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
                                    wsb + wl.oz, s, launches);
     };
     if (p->L == 0)
-        return cuda_status(leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n));
+        return cuda_status(tf ? leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n)
+                              : ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, m, k, n, p->nmod, 0, wsb, s,
+                                           launches));
     if (!tf && residue_space(p)) {
         const bool kfr = g.kp < k;
         if (kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,

@@ -17,6 +17,8 @@
 // layouts are chosen to keep fragment reads broadcast or conflict-free.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "fmm_internal.h"
@@ -699,9 +701,105 @@ cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int 
     return cudaSuccess;
 }
 
+// Thin classical products (the peeling fringes of Section 3.4: at most
+// M^L - 1 rows or N^L - 1 columns), where a 2-D tile would mostly compute
+// padding.  Both are deterministic: fixed k-slices reduced in a fixed order.
+
+// k <= 32 (the k-fringe): C = A B as a short sum per element; a warp covers
+// 32 consecutive columns of one row (A broadcast, B and C coalesced).
+__global__ void __launch_bounds__(256) thin_k_kernel(const double *A, int64_t lda, const double *B, int64_t ldb,
+                                                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n) {
+    const int64_t colb = (n + 31) / 32;
+    for (int64_t g = (int64_t)blockIdx.x * 8 + threadIdx.x / 32; g < m * colb; g += (int64_t)gridDim.x * 8) {
+        const int64_t i = g / colb, j = (g % colb) * 32 + threadIdx.x % 32;
+        if (j >= n) continue;
+        double acc = 0.0;
+        for (int64_t p = 0; p < k; ++p) acc = fma(__ldg(A + i * lda + p), __ldg(B + p * ldb + j), acc);
+        C[i * ldc + j] = acc;
+    }
+}
+
+// m <= 32 rows: CTA = 32 columns x 8 k-slices; rows in groups of 8.  grid ceil(n/32).
+__global__ void __launch_bounds__(256) thin_rows_kernel(const double *A, int64_t lda, const double *B, int64_t ldb,
+                                                        double *C, int64_t ldc, int64_t m, int64_t k, int64_t n) {
+    __shared__ double red[8][8][33];
+    const int col = threadIdx.x % 32, ks = threadIdx.x / 32;
+    const int64_t j = (int64_t)blockIdx.x * 32 + col;
+    for (int64_t i0 = 0; i0 < m; i0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.0;
+        if (j < n) {
+            for (int64_t p = ks; p < k; p += 8) {
+                const double b = B[p * ldb + j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i0 + i < m) acc[i] = fma(__ldg(A + (i0 + i) * lda + p), b, acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i) red[ks][i][col] = acc[i];
+        __syncthreads();
+        if (ks == 0 && j < n) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                double v = red[0][i][col];
+#pragma unroll
+                for (int t = 1; t < 8; ++t) v += red[t][i][col];
+                if (i0 + i < m) C[(i0 + i) * ldc + j] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// n <= 32 columns: one warp per row of C, lanes over k, columns in groups of
+// 8, butterfly reduction across the warp.  grid ceil(m/8), 256 threads.
+__global__ void __launch_bounds__(256) thin_cols_kernel(const double *A, int64_t lda, const double *B, int64_t ldb,
+                                                        double *C, int64_t ldc, int64_t m, int64_t k, int64_t n) {
+    const int lane = threadIdx.x % 32;
+    const int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.x / 32;
+    if (i >= m) return;
+    for (int64_t j0 = 0; j0 < n; j0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) acc[jj] = 0.0;
+        for (int64_t p = lane; p < k; p += 32) {
+            const double a = A[i * lda + p];
+            const double *b = B + p * ldb + j0;
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < n) acc[jj] = fma(a, __ldg(b + jj), acc[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj)
+            for (int o = 16; o > 0; o >>= 1) acc[jj] += __shfl_xor_sync(0xffffffffu, acc[jj], o);
+        if (lane == 0)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj)
+                if (j0 + jj < n) C[i * ldc + j0 + jj] = acc[jj];
+    }
+}
+
 cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
                              double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, int tile,
                              cudaStream_t s, int *launches) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (tile == FMM_TILE_AUTO && k > 0 && k <= 32 && m > 32 && n > 32) {
+        const int64_t warps = m * ((n + 31) / 32);
+        thin_k_kernel<<<(unsigned)std::min<int64_t>((warps + 7) / 8, 152 * 64), 256, 0, s>>>(A, lda, B, ldb, C, ldc,
+                                                                                          m, k, n);
+        ++*launches;
+        return cudaGetLastError();
+    }
+    if (tile == FMM_TILE_AUTO && k > 0 && (m <= 32 || n <= 32)) {
+        if (m <= 32)
+            thin_rows_kernel<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(A, lda, B, ldb, C, ldc, m, k, n);
+        else
+            thin_cols_kernel<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(A, lda, B, ldb, C, ldc, m, k, n);
+        ++*launches;
+        return cudaGetLastError();
+    }
     int *uptr, *ucode;
     double *ucoef;
     cudaError_t e;

@@ -49,6 +49,20 @@ __constant__ int c_wmod[OZ_MAX_MOD][OZ_MAX_MOD];          // (prod_{l<i} p_l) mo
 __constant__ int c_winv[OZ_MAX_MOD];                      // inverse of (prod_{l<j} p_l) mod p_j
 __constant__ unsigned c_magic[OZ_MAX_MOD];                // floor(2^32 / p)
 __constant__ unsigned c_r32[OZ_MAX_MOD];                  // 2^32 mod p
+__constant__ unsigned c_r21[OZ_MAX_MOD], c_r42[OZ_MAX_MOD];  // 2^21 and 2^42 mod p
+__constant__ float c_modf[OZ_MAX_MOD], c_invp[OZ_MAX_MOD];  // p and 1/p as floats
+constexpr int OZ_MAX_TERMS = 512, OZ_MAX_R = 64;           // limits of the staged term lists
+// CRT by a weighted sum: X = sum_q r_q c_q (mod P), c_q = (P/p_q) ((P/p_q)^-1 mod p_q)
+// mod P, held as eight 16-bit limbs so every limb sum fits an int32.
+// Tables for every moduli count n <= 16 (P = product of the first n moduli),
+// so plans with different counts can run concurrently.
+constexpr int OZ_CRT_MAX = 16;
+__constant__ int c_crt16[OZ_CRT_MAX + 1][OZ_CRT_MAX][8];
+__constant__ int c_P16[OZ_CRT_MAX + 1][8];                  // 16-bit limbs of P
+__constant__ float c_fw[OZ_CRT_MAX + 1][8];                 // 2^(16 l) / P (0 where negligible)
+__constant__ unsigned long long c_P[OZ_CRT_MAX + 1][2];     // P (lo, hi)
+__constant__ unsigned long long c_Phalf[OZ_CRT_MAX + 1][2]; // P div 2
+__constant__ unsigned long long c_Plow[OZ_CRT_MAX + 1][2];  // P div 2 - P
 
 // x mod p for any 32-bit x: quotient estimate from floor(2^32/p) is at most
 // one short, so one conditional subtraction finishes it.
@@ -98,7 +112,7 @@ constexpr int oz_smem() { return OzCfg<BN>::STAGES * (OZ_A_BYTES + BN * OZ_BK * 
 template <int BN>
 __global__ void __launch_bounds__(oz_threads<BN>(), 1)
 residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             int8_t *Z, int64_t m, int64_t n, int kblocks, int nmod, int tiles_m, int tiles_n,
+             int8_t *Z, int64_t m, int64_t n, int64_t ldz, int kblocks, int nmod, int tiles_m, int tiles_n,
              int64_t tiles_total, int *err) {
     constexpr int OZ_TBUF = OzCfg<BN>::TBUF, OZ_STAGES = OzCfg<BN>::STAGES;
     constexpr int DW = OzCfg<BN>::DRAIN_WARPS;
@@ -222,12 +236,14 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const int64_t row = (int64_t)tm * OZ_BM + lg * 32 + lane;
             if (row < m) {
                 const int64_t col0 = (int64_t)tn * OZ_BN + ch * 128;
-                int8_t *out = Z + ((int64_t)z * m + row) * n + col0;
-                const int64_t cols = min((int64_t)128, n - col0);
+                // rows of Z are padded to ldz (a multiple of 16); columns past n hold
+                // residues of zero (the TMA fills B rows past n with zeros)
+                int8_t *out = Z + ((int64_t)z * m + row) * ldz + col0;
+                const int64_t cols = min((int64_t)128, ldz - col0);
                 // |acc| < 2^28: shift positive by p 2^22 (< 2^31) for one Barrett step
-                if (cols == 128 && n % 16 == 0) {
 #pragma unroll
-                    for (int j0 = 0; j0 < 128; j0 += 16) {
+                for (int j0 = 0; j0 < 128; j0 += 16) {
+                    if (j0 < cols) {
                         __align__(16) int8_t h[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
@@ -236,10 +252,6 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                         }
                         *reinterpret_cast<uint4 *>(out + j0) = *reinterpret_cast<const uint4 *>(h);
                     }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 128; ++j)
-                        if (j < cols) out[j] = (int8_t)bal_mod(acc[j], p);
                 }
             }
         }
@@ -335,104 +347,132 @@ __global__ void split_cols_kernel(const double *Y, int64_t ldy, int64_t leaf_str
     }
 }
 
-// Correctly rounded conversion of a 128-bit integer to FP64: the top 64
-// significant bits with every lower bit folded into a sticky bit round like
-// the full value.
-__device__ __forceinline__ double int128_to_double(__int128 x) {
-    const bool neg = x < 0;
-    const unsigned __int128 u = neg ? (unsigned __int128)(-x) : (unsigned __int128)x;
-    const unsigned long long hi = (unsigned long long)(u >> 64);
-    double d;
-    if (hi == 0) {
-        d = __ull2double_rn((unsigned long long)u);
+// fl(X) 2^-e for an integer X = (hi, lo) (two's complement, |X| < 2^127):
+// X rounded once to FP64 (round to nearest even, from its integer bits), then
+// scaled exactly; only a result outside the normal range goes through ldexp
+// (which then rounds once more, as ldexp of the rounded value does).
+__device__ __forceinline__ double round_scale(long long hi_s, unsigned long long lo, int e) {
+    const bool neg = hi_s < 0;
+    unsigned long long uh = (unsigned long long)hi_s, ul = lo;
+    if (neg) {
+        ul = ~ul + 1ull;
+        uh = ~uh + (ul == 0ull ? 1ull : 0ull);
+    }
+    if ((uh | ul) == 0ull) return 0.0;
+    int nb;
+    unsigned long long top;
+    bool sticky;
+    if (uh != 0ull) {
+        const int lz = __clzll((long long)uh);
+        nb = 128 - lz;
+        top = lz ? (uh << lz) | (ul >> (64 - lz)) : uh;
+        sticky = lz ? (ul << (64 - lz)) != 0ull : ul != 0ull;   // the low lz bits of ul
     } else {
-        const int sh = 64 - __clzll((long long)hi);              // bits above the low 64
-        unsigned long long top = (unsigned long long)(u >> sh);
-        if ((u & (((unsigned __int128)1 << sh) - 1)) != 0) top |= 1ull;
-        d = ldexp(__ull2double_rn(top), sh);
+        const int lz = __clzll((long long)ul);
+        nb = 64 - lz;
+        top = ul << lz;
+        sticky = false;
+    }
+    // top: leading one at bit 63; 53 significant bits and 11 rounding bits
+    unsigned long long m = top >> 11;
+    const unsigned rb = (unsigned)(top & 0x7ffull);
+    if (rb > 0x400u || (rb == 0x400u && (sticky || (m & 1ull)))) ++m;
+    int E = nb - 1;
+    if (m >> 53) { m >>= 1; ++E; }
+    const unsigned long long frac = m & ((1ull << 52) - 1);
+    const int be = E - e + 1023;
+    double d;
+    if (be >= 1 && be <= 2046) {
+        d = __longlong_as_double((long long)(((unsigned long long)be << 52) | frac));
+    } else {
+        d = ldexp(__longlong_as_double((long long)(((unsigned long long)(E + 1023) << 52) | frac)), -e);
     }
     return neg ? -d : d;
 }
 
-// Exact scaling of an FP64 value by 2^e (x an integer-valued double, so no
-// rounding unless the result leaves the normal range; then ldexp).
-__device__ __forceinline__ double scale_pow2(double x, int e) {
-    if (e > -1022 && e < 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
-    return ldexp(x, e);
+// Add residue r (|r| < 2^8, any representative) of modulus q of n to the limb sums.
+__device__ __forceinline__ void crt_add(int (&L)[8], int r, int q, int n) {
+#pragma unroll
+    for (int l = 0; l < 8; ++l) L[l] += r * c_crt16[n][q][l];
 }
 
-// Z from its N residues (Garner's mixed-radix digits, exact 128-bit Horner,
-// one correct rounding) times 2^-(sa_i + sb_j); V consecutive columns per
-// thread (one 4-byte load per modulus when V == 4).
+// The integer X in [P div 2 - P, P div 2) congruent to the residues summed in
+// L, rounded once to FP64 and scaled by 2^-e.  S = sum_l L_l 2^(16 l); the
+// quotient t = round(S / P) comes from a float estimate (off by at most one
+// near a half-integer), X = S - t P exactly in limbs, then one correction.
+__device__ __forceinline__ double crt_finish(const int (&L)[8], int e, int n) {
+    float sf = 0.f;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) sf = fmaf((float)L[l], c_fw[n][l], sf);
+    // t = rint(sf) (|sf| < 2^22); xf estimates X / P to within 2^-10
+    const float sm = sf + 12582912.0f;
+    const int t = __float_as_int(sm) - 0x4B400000;
+    const float xf = sf - (sm - 12582912.0f);
+    int x[8];
+#pragma unroll
+    for (int l = 0; l < 8; ++l) x[l] = L[l] - t * c_P16[n][l];
+#pragma unroll
+    for (int l = 0; l < 7; ++l) {
+        const int carry = x[l] >> 16;
+        x[l] -= carry * 65536;
+        x[l + 1] += carry;
+    }
+    unsigned long long lo = (unsigned long long)(unsigned)x[0] | ((unsigned long long)(unsigned)x[1] << 16) |
+                            ((unsigned long long)(unsigned)x[2] << 32) | ((unsigned long long)(unsigned)x[3] << 48);
+    long long hi = (long long)(((unsigned long long)(long long)x[7] << 48) | ((unsigned long long)(unsigned)x[6] << 32) |
+                               ((unsigned long long)(unsigned)x[5] << 16) | (unsigned long long)(unsigned)x[4]);
+    if (fabsf(xf) > 0.49f) {
+        // near +-P/2 the estimate may have picked the neighbouring multiple of P
+        __int128 X = (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
+        const __int128 P = (__int128)(((unsigned __int128)c_P[n][1] << 64) | c_P[n][0]);
+        const __int128 Ph = (__int128)(((unsigned __int128)c_Phalf[n][1] << 64) | c_Phalf[n][0]);
+        const __int128 Pl = (__int128)(((unsigned __int128)c_Plow[n][1] << 64) | c_Plow[n][0]);
+        if (X >= Ph) X -= P;
+        else if (X < Pl) X += P;
+        lo = (unsigned long long)X;
+        hi = (long long)((unsigned __int128)X >> 64);
+    }
+    return round_scale(hi, lo, e);
+}
+
+// C[leaf][i][j] (+)= (Z from its residues) * 2^-(sa_i + sb_j), the leaf
+// products of the per-leaf emulation.  V consecutive columns per thread.
 template <int V>
-__device__ __forceinline__ void crt_values(const int8_t *Z, int64_t plane0, int64_t plane, int nmod,
-                                           double *vals) {
-    int v[V][OZ_MAX_MOD];
-#pragma unroll
-    for (int q = 0; q < OZ_MAX_MOD; ++q) {
-        if (q >= nmod) break;
-        int z[V];
-        if (V == 4) {
-            const int raw = *reinterpret_cast<const int *>(Z + plane0 + (int64_t)q * plane);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) z[e] = (int)(int8_t)(raw >> (8 * e));
-        } else {
-            z[0] = Z[plane0 + (int64_t)q * plane];
-        }
-        const int p = c_mod[q];
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            int sum = z[e];
-#pragma unroll
-            for (int l = 0; l < OZ_MAX_MOD; ++l) {
-                if (l >= q) break;
-                sum -= v[e][l] * c_wmod[l][q];
-            }
-            const unsigned t = mod_u32((unsigned)(sum + (p << 13)), q);
-            const int d = (int)mod_u32(t * (unsigned)c_winv[q], q);
-            v[e][q] = d >= (p + 1) / 2 ? d - p : d;
-        }
-    }
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-        __int128 x = v[e][nmod - 1];
-        for (int q = nmod - 2; q >= 0; --q) x = x * c_mod[q] + v[e][q];
-        vals[e] = int128_to_double(x);
-    }
-}
-
-// C[leaf][i][j] (+)= (Z from its residues) * 2^-(sa_i + sb_j).
-__global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t leaves, int nmod,
+__global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t ldz, int64_t leaves, int nmod,
                            const int *sa, const int *sb, double *C, int64_t ldc, int64_t leaf_stride,
                            int accumulate) {
-    const int64_t plane = m * n;
-    if (n % 4 == 0) {
-        const int64_t total = leaves * plane / 4;
-        for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-             g += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t e0 = g * 4;
-            const int64_t leaf = e0 / plane, rem = e0 % plane, i = rem / n, j = rem % n;
-            double vals[4];
-            crt_values<4>(Z, leaf * nmod * plane + rem, plane, nmod, vals);
-            double *out = C + leaf * leaf_stride + i * ldc + j;
-            const int ei = sa[leaf * m + i];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const double val = scale_pow2(vals[e], -(ei + sb[leaf * n + j + e]));
-                out[e] = accumulate ? out[e] + val : val;
-            }
-        }
-        return;
-    }
-    const int64_t total = leaves * plane;
+    const int64_t plane = m * ldz;
+    const int64_t total = leaves * m * n / V;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t leaf = g / plane, rem = g % plane, i = rem / n, j = rem % n;
-        double val;
-        crt_values<1>(Z, leaf * nmod * plane + rem, plane, nmod, &val);
-        val = scale_pow2(val, -(sa[leaf * m + i] + sb[leaf * n + j]));
+        const int64_t e0 = g * V;
+        const int64_t leaf = e0 / (m * n), rem0 = e0 % (m * n), i = rem0 / n, j = rem0 % n;
+        const int64_t rem = i * ldz + j;
+        int L[V][8];
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+#pragma unroll
+            for (int l = 0; l < 8; ++l) L[e][l] = 0;
+        const int8_t *z = Z + leaf * nmod * plane + rem;
+        for (int q = 0; q < nmod; ++q) {
+            int r[V];
+            if (V == 4) {
+                const int raw = *reinterpret_cast<const int *>(z + (int64_t)q * plane);
+#pragma unroll
+                for (int e = 0; e < V; ++e) r[e] = (int)(int8_t)(raw >> (8 * e));
+            } else {
+                r[0] = z[(int64_t)q * plane];
+            }
+#pragma unroll
+            for (int e = 0; e < V; ++e) crt_add(L[e], r[e], q, nmod);
+        }
         double *out = C + leaf * leaf_stride + i * ldc + j;
-        *out = accumulate ? *out + val : val;
+        const int ei = sa[leaf * m + i];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const double val = crt_finish(L[e], ei + sb[leaf * n + j + e], nmod);
+            out[e] = accumulate ? out[e] + val : val;
+        }
     }
 }
 
@@ -570,7 +610,7 @@ __global__ void res_form_kernel(const int8_t *parent, int64_t pr, int64_t pc, in
 // its M x N grid, modulus q = sum_t w_t child_{s*R + r_t} mod p.  VEC: eight
 // columns per thread (cols a multiple of 8).
 template <bool VEC>
-__global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, int R, int gridN,
+__global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, int64_t cld, int R, int gridN,
                              int MN, int nmod, int8_t *parent, int64_t o_base, const int *w_ptr,
                              const int *w_r, const int *w_icoef) {
     const int64_t o = o_base + blockIdx.y;
@@ -589,7 +629,7 @@ __global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, in
             for (int e = 0; e < W; ++e) v[e] = 0;
             for (int t = t0; t < t1; ++t) {
                 const int wc = w_icoef[t];
-                const int8_t *src = child + (((sp * R + w_r[t]) * nmod + q) * rows + i) * cols + j;
+                const int8_t *src = child + (((sp * R + w_r[t]) * nmod + q) * rows + i) * cld + j;
                 if (VEC) {
                     const uint2 raw = *reinterpret_cast<const uint2 *>(src);
                     const int8_t *bytes = reinterpret_cast<const int8_t *>(&raw);
@@ -611,6 +651,330 @@ __global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, in
     }
 }
 
+// ---------------------------------------------------------------------
+// Fused first level: the scaling of A (or B), the residues and the first
+// recursive level's combinations in one pass over the FP64 operand, so the
+// level-0 residue planes never reach HBM.  With L = 0 the "first level" is the
+// identity (one block, one child, coefficient 1) and the pass writes the GEMM
+// operand planes directly.
+
+// Residue in [0, p) of an integer |v| < 2^62: v = a 2^42 + b 2^21 + c (a
+// signed, b and c in [0, 2^21)), folded with 2^42 and 2^21 mod p into one
+// positive 31-bit value, then one Barrett step.
+__device__ __forceinline__ unsigned res_i64(long long v, int q) {
+    const int a = (int)(v >> 42);
+    const unsigned b = (unsigned)(v >> 21) & 0x1fffffu, c = (unsigned)v & 0x1fffffu;
+    const int x = a * (int)c_r42[q] + (int)(b * c_r21[q]) + (int)c + (c_mod[q] << 22);
+    return mod_u32((unsigned)x, q);
+}
+
+// Two small integers (|x| <= 256, exact in bfloat16) as a packed bfloat16
+// pair, lo in the low half: x = float(1.5 2^23 + x) - 1.5 2^23 exactly, and
+// the bfloat16 is the upper half of that float (its low 16 bits are zero).
+__device__ __forceinline__ unsigned bf16x2_of_ints(int lo, int hi) {
+    const float flo = __int_as_float(0x4B400000 + lo) - 12582912.0f;
+    const float fhi = __int_as_float(0x4B400000 + hi) - 12582912.0f;
+    return __byte_perm(__float_as_uint(flo), __float_as_uint(fhi), 0x7632);
+}
+
+// Balanced residue of a small combination |x| < 2^29.
+__device__ __forceinline__ int bal_small(int x, int q) {
+    const int p = c_mod[q];
+    const int r = (int)mod_u32((unsigned)(x + (p << 22)), q);
+    return r >= (p + 1) / 2 ? r - p : r;
+}
+
+// Integer-valued floats: x = float(1.5 2^23 + x) - 1.5 2^23 exactly for |x| < 2^22.
+constexpr float OZ_FMAGIC = 12582912.0f;
+constexpr int OZ_IMAGIC = 0x4B400000;
+
+// Limbs of an integer |v| < 2^62: v = a 2^42 + b 2^21 + c, a signed, b and c in [0, 2^21).
+__device__ __forceinline__ void limbs_of(long long v, int &a, unsigned &b, unsigned &c) {
+    a = (int)(v >> 42);
+    b = (unsigned)(v >> 21) & 0x1fffffu;
+    c = (unsigned)v & 0x1fffffu;
+}
+
+// The constants of one modulus, loaded once per modulus loop iteration.
+struct ModK {
+    int p, off;                 // p, p 2^22 (keeps the folded limbs positive)
+    unsigned magic, r21, r42;   // floor(2^32 / p), 2^21 mod p, 2^42 mod p
+    float pf, invp;             // p, 1/p
+};
+__device__ __forceinline__ ModK mod_consts(int q) {
+    ModK k;
+    k.p = c_mod[q];
+    k.off = k.p << 22;
+    k.magic = c_magic[q];
+    k.r21 = c_r21[q];
+    k.r42 = c_r42[q];
+    k.pf = c_modf[q];
+    k.invp = c_invp[q];
+    return k;
+}
+
+// Residue in [0, p) of a 2^42 + b 2^21 + c as an integer-valued float: the
+// limbs folded with 2^42, 2^21 mod p into one value in (0, 2^31), then one
+// Barrett step (quotient at most one short).
+__device__ __forceinline__ float res_f(int a, unsigned b, unsigned c, const ModK &k) {
+    const unsigned x = (unsigned)(a * (int)k.r42 + k.off) + b * k.r21 + c;
+    unsigned r = x - __umulhi(x, k.magic) * (unsigned)k.p;
+    r = r >= (unsigned)k.p ? r - (unsigned)k.p : r;
+    return __int_as_float(OZ_IMAGIC + (int)r) - OZ_FMAGIC;
+}
+
+// Nearest representative (|r| <= p/2) of an integer-valued float x, |x| < 2^22,
+// modulo p: r = x - rint(x / p) p, exact (the quotient estimate can only pick
+// the other neighbour at an exact half, where both are nearest).
+__device__ __forceinline__ float near_mod(float x, const ModK &k) {
+    const float t = fmaf(x, k.invp, OZ_FMAGIC) - OZ_FMAGIC;
+    return fmaf(-t, k.pf, x);
+}
+
+// Stage one level's term lists in shared memory: sterm[t] = (block index in
+// the thread's residue array, coefficient as float bits), sptr[o] = CSR.
+__device__ __forceinline__ void stage_terms(int R, int gridC, const int *ptr, const int *code, const int *icoef,
+                                            int2 *sterm, int *sptr) {
+    const int nterms = __ldg(ptr + R);
+    for (int t = threadIdx.x; t < nterms; t += blockDim.x) {
+        const int cd = __ldg(code + t);
+        sterm[t] = make_int2((cd >> 16) * gridC + (cd & 0xffff), __float_as_int((float)__ldg(icoef + t)));
+    }
+    for (int o = threadIdx.x; o <= R; o += blockDim.x) sptr[o] = __ldg(ptr + o);
+}
+
+// Children o = 0..R-1 of one level, modulus q, from the NB block residues the
+// thread keeps in shared memory (4 consecutive entries per float4):
+// child_o = sum_t c_t block(t) mod p (nearest representative), written to
+// out[(o nmod + q) plane + base .. + valid) as bfloat16 (FINAL, the GEMM
+// operand) or int8 (a later level's input; +-128 are one class mod 256).
+template <bool FINAL>
+__device__ __forceinline__ void emit_children(const float4 *sres, const int2 *sterm, const int *sptr, int R,
+                                              const ModK &k, char *dst, int64_t ostep, int valid) {
+    for (int o = 0; o < R; ++o, dst += ostep) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        const int t1 = sptr[o + 1];
+        for (int t = sptr[o]; t < t1; ++t) {
+            const int2 tm = sterm[t];
+            const float4 w = sres[tm.x * 256 + threadIdx.x];
+            const float c = __int_as_float(tm.y);
+            a0 = fmaf(c, w.x, a0);
+            a1 = fmaf(c, w.y, a1);
+            a2 = fmaf(c, w.z, a2);
+            a3 = fmaf(c, w.w, a3);
+        }
+        const float r0 = near_mod(a0, k), r1 = near_mod(a1, k), r2 = near_mod(a2, k), r3 = near_mod(a3, k);
+        if (FINAL) {
+            uint2 pk;
+            pk.x = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
+            pk.y = __byte_perm(__float_as_uint(r2), __float_as_uint(r3), 0x7632);
+            if (valid == 4) {
+                *reinterpret_cast<uint2 *>(dst) = pk;
+            } else {
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&pk);
+                for (int e = 0; e < valid; ++e) reinterpret_cast<__nv_bfloat16 *>(dst)[e] = h[e];
+            }
+        } else {
+            const unsigned b0 = (unsigned)(__float_as_int(r0 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
+            const unsigned b1 = (unsigned)(__float_as_int(r1 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
+            const unsigned b2 = (unsigned)(__float_as_int(r2 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
+            const unsigned b3 = (unsigned)(__float_as_int(r3 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
+            const unsigned word = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+            if (valid == 4 && ((uintptr_t)dst & 3) == 0) {
+                *reinterpret_cast<unsigned *>(dst) = word;
+            } else {
+                for (int e = 0; e < valid; ++e) reinterpret_cast<int8_t *>(dst)[e] = (int8_t)(word >> (8 * e));
+            }
+        }
+    }
+}
+
+// S side: A (peeled core, ld lda) as a grid of M x K blocks of rows x cols;
+// A' = trunc(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
+// consecutive columns of out_ld (columns >= cols are the zero padding of the
+// GEMM operand).  256 threads.
+template <int NB, bool FINAL>
+__global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t lda, const int *ea, int64_t rows,
+                                                       int64_t cols, int gridK, int R, int nmod, const int *ptr,
+                                                       const int *code, const int *icoef, void *out,
+                                                       int64_t out_ld) {
+    __shared__ float4 sres[NB * 256];
+    __shared__ int2 sterm[OZ_MAX_TERMS];
+    __shared__ int sptr[OZ_MAX_R + 1];
+    stage_terms(R, gridK, ptr, code, icoef, sterm, sptr);
+    __syncthreads();
+    const int64_t groups = (out_ld + 3) / 4;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= rows * groups) return;
+    const int64_t i = pos / groups, j0 = (pos % groups) * 4;
+    const int valid = (int)min((int64_t)4, out_ld - j0);
+    int la[NB][4];
+    unsigned lb[NB][4], lc[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int64_t row = (int64_t)(b / gridK) * rows + i;
+        const int s = ea[row];
+        const double *x = A + row * lda + (int64_t)(b % gridK) * cols + j0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) limbs_of((j0 + e < cols) ? scaled_trunc(x[e], s) : 0, la[b][e], lb[b][e], lc[b][e]);
+    }
+    const int64_t plane = rows * out_ld, base = i * out_ld + j0;
+    constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
+    char *dst = (char *)out + base * ES;
+    const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
+    for (int q = 0; q < nmod; ++q, dst += qstep) {
+        const ModK k = mod_consts(q);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            sres[b * 256 + threadIdx.x] = make_float4(res_f(la[b][0], lb[b][0], lc[b][0], k), res_f(la[b][1], lb[b][1], lc[b][1], k),
+                                                      res_f(la[b][2], lb[b][2], lc[b][2], k), res_f(la[b][3], lb[b][3], lc[b][3], k));
+        emit_children<FINAL>(sres, sterm, sptr, R, k, dst, ostep, valid);
+    }
+}
+
+// T side, transposed: B (peeled core, ld ldb) as a grid of K x N blocks of
+// krows x ncols; B' = trunc(B_ij 2^eb_j).  Output rows are columns of B
+// (T^T, K-major for the GEMM).  CTA: 32 k x 32 n positions of the child
+// blocks through shared memory (dynamic: NB x 32 x 33 int64, reused for the
+// residues); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
+// ceil(ncols / 32)), 256 threads.
+template <int NB, bool FINAL>
+__global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_t ldb, const int *eb, int64_t krows,
+                                                         int64_t ncols, int gridN, int R, int nmod, const int *ptr,
+                                                         const int *code, const int *icoef, void *out,
+                                                         int64_t out_ld) {
+    extern __shared__ long long sv[];   // [NB][32][33], then float4 residues [NB][256]
+    __shared__ int2 sterm[OZ_MAX_TERMS];
+    __shared__ int sptr[OZ_MAX_R + 1];
+    stage_terms(R, gridN, ptr, code, icoef, sterm, sptr);
+    const int64_t k0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int64_t bk = b / gridN, bn = b % gridN;
+        const int64_t n = n0 + tx;
+        const int s = n < ncols ? eb[bn * ncols + n] : 0;
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t k = k0 + r;
+            sv[(b * 32 + r) * 33 + tx] =
+                (k < krows && n < ncols) ? scaled_trunc(B[(bk * krows + k) * ldb + bn * ncols + n], s) : 0;
+        }
+    }
+    __syncthreads();
+    const int nn = threadIdx.x / 8, kk = (threadIdx.x % 8) * 4;
+    int la[NB][4];
+    unsigned lb[NB][4], lc[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) limbs_of(sv[(b * 32 + kk + e) * 33 + nn], la[b][e], lb[b][e], lc[b][e]);
+    __syncthreads();   // sv is reused for the residues below
+    float4 *sres = reinterpret_cast<float4 *>(sv);
+    const int64_t n = n0 + nn, k = k0 + kk;
+    if (n >= ncols || k >= out_ld) return;
+    const int valid = FINAL ? 4 : (int)min((int64_t)4, krows - k);
+    const int64_t plane = ncols * out_ld, base = n * out_ld + k;
+    constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
+    char *dst = (char *)out + base * ES;
+    const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
+    for (int q = 0; q < nmod; ++q, dst += qstep) {
+        const ModK k = mod_consts(q);
+#pragma unroll
+        for (int b = 0; b < NB; ++b)
+            sres[b * 256 + threadIdx.x] = make_float4(res_f(la[b][0], lb[b][0], lc[b][0], k), res_f(la[b][1], lb[b][1], lc[b][1], k),
+                                                      res_f(la[b][2], lb[b][2], lc[b][2], k), res_f(la[b][3], lb[b][3], lc[b][3], k));
+        emit_children<FINAL>(sres, sterm, sptr, R, k, dst, ostep, valid);
+    }
+}
+
+// Top recursion level of the W combination fused with the CRT: output block
+// qb = (a, c) of the M x N grid, modulus q: Z_qb = sum_t w_t child(r_t) mod p;
+// C'_qb from its residues, times 2^-(ea_i + eb_j), stored (or added) in C.
+// With L = 0 the one child is the product itself.  Thread: one row of the
+// child blocks, V consecutive columns.
+template <int V, bool REDUCE>
+__global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t rows, int64_t cols, int64_t cld,
+                                                    int gridN, int MN, int nmod, const int *w_ptr, const int *w_r,
+                                                    const int *w_icoef, const int *ea, const int *eb, double *C,
+                                                    int64_t ldc, int accumulate) {
+    __shared__ int2 swt[OZ_MAX_TERMS];   // (child r, coefficient)
+    __shared__ int swp[OZ_MAX_R + 1];
+    {
+        const int nterms = __ldg(w_ptr + MN);
+        for (int t = threadIdx.x; t < nterms; t += blockDim.x) swt[t] = make_int2(__ldg(w_r + t), __ldg(w_icoef + t));
+        for (int o = threadIdx.x; o <= MN; o += blockDim.x) swp[o] = __ldg(w_ptr + o);
+    }
+    __syncthreads();
+    const int64_t groups = (cols + V - 1) / V;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= rows * groups) return;
+    const int64_t i = pos / groups, j0 = (pos % groups) * V;
+    const int valid = (int)min((int64_t)V, cols - j0);
+    const int64_t plane = rows * cld;
+    const int8_t *zrow = Z + i * cld + j0;
+    for (int qb = 0; qb < MN; ++qb) {
+        const int a = qb / gridN, c = qb % gridN;
+        int L[V][8];
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+#pragma unroll
+            for (int l = 0; l < 8; ++l) L[e][l] = 0;
+        const int t0 = swp[qb], t1 = swp[qb + 1];
+#pragma unroll 2
+        for (int q = 0; q < nmod; ++q) {
+            int acc[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] = 0;
+            for (int t = t0; t < t1; ++t) {
+                const int2 wt = swt[t];
+                const int8_t *z = zrow + ((int64_t)wt.x * nmod + q) * plane;
+                if (V == 8) {
+                    const uint2 raw = *reinterpret_cast<const uint2 *>(z);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        acc[e] += wt.y * (int)(int8_t)(raw.x >> (8 * e));
+                        acc[e + 4] += wt.y * (int)(int8_t)(raw.y >> (8 * e));
+                    }
+                } else {
+                    acc[0] += wt.y * (int)z[0];
+                }
+            }
+            // the limb sums take any representative: the raw combination when it
+            // is small enough for them to stay below 2^30 (host-checked bound)
+#pragma unroll
+            for (int e = 0; e < V; ++e) crt_add(L[e], REDUCE ? bal_small(acc[e], q) : acc[e], q, nmod);
+        }
+        const int64_t row = (int64_t)a * rows + i;
+        const int er = ea[row];
+        double *out = C + row * ldc + (int64_t)c * cols + j0;
+        const int *ebc = eb + (int64_t)c * cols + j0;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            if (e < valid) {
+                const double val = crt_finish(L[e], er + ebc[e], nmod);
+                out[e] = accumulate ? out[e] + val : val;
+            }
+        }
+    }
+}
+
+// Row exponents s_i = beta - 1 - floor(log2 max_j |A_ij|) (0 for a zero row),
+// one warp per row.
+__global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64_t cols, int beta, int *exps) {
+    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int lane = threadIdx.x % 32;
+    if (row >= rows) return;
+    const double *x = A + row * lda;
+    double mx = 0.0;
+    for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) exps[row] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+}
+
+__device__ const int g_ident_ptr[2] = {0, 1};
+__device__ const int g_ident_code[1] = {0};
+__device__ const int g_ident_coef[1] = {1};
+
 typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -619,7 +983,6 @@ typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, voi
 std::mutex g_oz_mu;
 EncodeFn g_encode = nullptr;
 bool g_tables[64] = {};
-int g_tables_n[64] = {};
 
 cudaError_t encode_fn(EncodeFn *out) {
     std::lock_guard<std::mutex> g(g_oz_mu);
@@ -675,20 +1038,26 @@ long long mod_pow_inv(long long a, long long p) {
     return t < 0 ? t + p : t;
 }
 
+// The constant tables (moduli, Barrett constants, CRT weights for every
+// moduli count) do not depend on the plan: uploaded once per device.
 cudaError_t ensure_tables(int nmod) {
+    if (nmod < 1 || nmod > OZ_CRT_MAX) return cudaErrorInvalidValue;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> g(g_oz_mu);
-    if (dev < 64 && g_tables[dev] && g_tables_n[dev] == nmod) return cudaSuccess;
+    if (dev < 64 && g_tables[dev]) return cudaSuccess;
     int mods[OZ_MAX_MOD] = {}, wmod[OZ_MAX_MOD][OZ_MAX_MOD] = {}, winv[OZ_MAX_MOD] = {};
-    unsigned magic[OZ_MAX_MOD] = {}, r32[OZ_MAX_MOD] = {};
-    for (int i = 0; i < nmod; ++i) {
+    unsigned magic[OZ_MAX_MOD] = {}, r32[OZ_MAX_MOD] = {}, r21[OZ_MAX_MOD] = {}, r42[OZ_MAX_MOD] = {};
+    for (int i = 0; i < OZ_MAX_MOD; ++i) {
+        const unsigned long long p = (unsigned long long)kOzakiModuli[i];
         mods[i] = kOzakiModuli[i];
-        magic[i] = (unsigned)((1ull << 32) / (unsigned long long)mods[i]);
-        r32[i] = (unsigned)((1ull << 32) % (unsigned long long)mods[i]);
+        magic[i] = (unsigned)((1ull << 32) / p);
+        r32[i] = (unsigned)((1ull << 32) % p);
+        r21[i] = (unsigned)((1ull << 21) % p);
+        r42[i] = (unsigned)((1ull << 42) % p);
     }
-    for (int j = 0; j < nmod; ++j) {
+    for (int j = 0; j < OZ_MAX_MOD; ++j) {
         long long w = 1 % mods[j];
         for (int i = 0; i < j; ++i) {
             wmod[i][j] = int(w);
@@ -696,12 +1065,60 @@ cudaError_t ensure_tables(int nmod) {
         }
         winv[j] = int(mod_pow_inv(w, mods[j]));   // w = (prod_{l<j} p_l) mod p_j
     }
+    static int crt16[OZ_CRT_MAX + 1][OZ_CRT_MAX][8];
+    static int P16[OZ_CRT_MAX + 1][8];
+    static float fw[OZ_CRT_MAX + 1][8];
+    static unsigned long long Pw[OZ_CRT_MAX + 1][2], Ph[OZ_CRT_MAX + 1][2], Pl[OZ_CRT_MAX + 1][2];
+    std::memset(crt16, 0, sizeof(crt16));
+    std::memset(P16, 0, sizeof(P16));
+    std::memset(fw, 0, sizeof(fw));
+    std::memset(Pw, 0, sizeof(Pw));
+    std::memset(Ph, 0, sizeof(Ph));
+    std::memset(Pl, 0, sizeof(Pl));
+    for (int n = 1; n <= OZ_CRT_MAX; ++n) {
+        unsigned __int128 P = 1;
+        for (int i = 0; i < n; ++i) P *= (unsigned)mods[i];
+        for (int q = 0; q < n; ++q) {
+            const unsigned __int128 Mq = P / (unsigned)mods[q];
+            const long long y = mod_pow_inv((long long)(Mq % (unsigned)mods[q]), mods[q]);
+            const unsigned __int128 c = (Mq * (unsigned __int128)y) % P;   // Mq y < P p / p_q
+            for (int l = 0; l < 8; ++l) crt16[n][q][l] = int((c >> (16 * l)) & 0xffff);
+        }
+        for (int l = 0; l < 8; ++l) {
+            P16[n][l] = int((P >> (16 * l)) & 0xffff);
+            const long double wl = ldexpl(1.0L, 16 * l) / (long double)P;
+            fw[n][l] = wl < ldexpl(1.0L, -60) ? 0.f : (float)wl;
+        }
+        const unsigned __int128 half = P / 2;
+        const __int128 low = (__int128)half - (__int128)P;
+        Pw[n][0] = (unsigned long long)P; Pw[n][1] = (unsigned long long)(P >> 64);
+        Ph[n][0] = (unsigned long long)half; Ph[n][1] = (unsigned long long)(half >> 64);
+        Pl[n][0] = (unsigned long long)(unsigned __int128)low;
+        Pl[n][1] = (unsigned long long)((unsigned __int128)low >> 64);
+    }
     if ((e = cudaMemcpyToSymbol(c_mod, mods, sizeof(mods))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_wmod, wmod, sizeof(wmod))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_winv, winv, sizeof(winv))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_magic, magic, sizeof(magic))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_r32, r32, sizeof(r32))) != cudaSuccess) return e;
-    if (dev < 64) { g_tables[dev] = true; g_tables_n[dev] = nmod; }
+    if ((e = cudaMemcpyToSymbol(c_r21, r21, sizeof(r21))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_r42, r42, sizeof(r42))) != cudaSuccess) return e;
+    {
+        float modf[OZ_MAX_MOD], invp[OZ_MAX_MOD];
+        for (int i = 0; i < OZ_MAX_MOD; ++i) {
+            modf[i] = (float)mods[i];
+            invp[i] = 1.0f / (float)mods[i];
+        }
+        if ((e = cudaMemcpyToSymbol(c_modf, modf, sizeof(modf))) != cudaSuccess) return e;
+        if ((e = cudaMemcpyToSymbol(c_invp, invp, sizeof(invp))) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemcpyToSymbol(c_crt16, crt16, sizeof(crt16))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_P16, P16, sizeof(P16))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_fw, fw, sizeof(fw))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_P, Pw, sizeof(Pw))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_Phalf, Ph, sizeof(Ph))) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(c_Plow, Pl, sizeof(Pl))) != cudaSuccess) return e;
+    if (dev < 64) g_tables[dev] = true;
     return cudaSuccess;
 }
 
@@ -720,6 +1137,10 @@ cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Row pitch of the product residues Z: n rounded up to 16 bytes, so the drain
+// always stores whole 16-byte chunks.
+int64_t z_pitch(int64_t n) { return (n + 15) / 16 * 16; }
+
 // One persistent launch over all tiles of all planes; N = 256 tiles when the
 // planes are at least 256 wide.
 cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64_t m, int64_t n,
@@ -736,12 +1157,13 @@ cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64
     const int64_t tiles = tn * tmb * planes;
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
     cudaEvent_t t0 = timing_mark(s);
+    const int64_t ldz = z_pitch(n);
     if (wide)
         residue_gemm<256><<<ctas, oz_threads<256>(), oz_smem<256>(), s>>>(
-            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
     else
         residue_gemm<128><<<ctas, oz_threads<128>(), oz_smem<128>(), s>>>(
-            ta, tb, Z, m, n, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
@@ -763,9 +1185,12 @@ cudaError_t read_device_error(int *flag, bool clear) {
 
 // Largest beta <= 62 with k 2^(2 beta + 1) < P (P = product of the moduli,
 // < 2^127 for N <= 16), so that |S'T'| < P/2 and the CRT is unambiguous.
+static cudaError_t configure_split_form();
+
 cudaError_t ozaki_prepare(int nmod) {
     cudaError_t e = ensure_tables(nmod);
     if (e != cudaSuccess) return e;
+    if ((e = configure_split_form()) != cudaSuccess) return e;
     EncodeFn enc;
     if ((e = encode_fn(&enc)) != cudaSuccess) return e;
     int *err = nullptr;
@@ -788,24 +1213,39 @@ size_t ozaki_workspace(int64_t leaves, int nmod, int64_t m, int64_t k, int64_t n
     const int64_t kpad = (k + OZ_BK - 1) / OZ_BK * OZ_BK;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     return al(size_t(leaves) * nmod * m * kpad * 2) + al(size_t(leaves) * nmod * n * kpad * 2) +
-           al(size_t(leaves) * m * 4) + al(size_t(leaves) * n * 4) + al(size_t(leaves) * nmod * m * n);
+           al(size_t(leaves) * m * 4) + al(size_t(leaves) * n * 4) + al(size_t(leaves) * nmod * m * z_pitch(n));
 }
 
 struct ResLayout {
-    size_t ra0, rb0, ea, eb, zres, cres, total;
-    std::vector<size_t> la, lb, lw;   // per level l = 1..L (lw: l = 1..L-1)
+    size_t ra0 = 0, rb0 = 0, ea = 0, eb = 0, zres = 0, total = 0;
+    std::vector<size_t> la, lb, lw;   // per level l = 1..L (lw: l = 1..L-1); L = 0: la/lb = GEMM operands
 };
+
+// Block counts of the fused first-level kernels with a compiled instance.
+static bool fused_nb(int nb) { return nb == 1 || nb == 4 || nb == 6 || nb == 8 || nb == 9; }
+
+static bool first_level_fused(const ResPlan &rp) {
+    return rp.L == 0 || (fused_nb(rp.M * rp.K) && fused_nb(rp.K * rp.N));
+}
 
 static ResLayout res_layout(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod) {
     ResLayout w;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
-    w.ra0 = take(size_t(nmod) * mp * kp);
-    w.rb0 = take(size_t(nmod) * kp * np);
+    if (!first_level_fused(rp)) {
+        w.ra0 = take(size_t(nmod) * mp * kp);
+        w.rb0 = take(size_t(nmod) * kp * np);
+    }
     w.ea = take(size_t(mp) * 4);
     w.eb = take(size_t(np) * 4);
     int64_t cnt = 1, ml = mp, kl = kp, nl = np;
+    if (rp.L == 0) {
+        const int64_t kpad = (kp + OZ_BK - 1) / OZ_BK * OZ_BK;
+        w.la.push_back(take(size_t(nmod) * mp * kpad * 2));
+        w.lb.push_back(take(size_t(nmod) * np * kpad * 2));
+        w.zres = take(size_t(nmod) * mp * z_pitch(np));
+    }
     for (int l = 1; l <= rp.L; ++l) {
         cnt *= rp.R;
         ml /= rp.M; kl /= rp.K; nl /= rp.N;
@@ -817,10 +1257,9 @@ static ResLayout res_layout(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
         } else {
             w.la.push_back(take(size_t(cnt) * nmod * ml * kpad * 2));
             w.lb.push_back(take(size_t(cnt) * nmod * nl * kpad * 2));
-            w.zres = take(size_t(cnt) * nmod * ml * nl);
+            w.zres = take(size_t(cnt) * nmod * ml * z_pitch(nl));
         }
     }
-    w.cres = take(size_t(nmod) * mp * np);
     w.total = off;
     return w;
 }
@@ -829,35 +1268,116 @@ size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
     return res_layout(rp, mp, kp, np, nmod).total;
 }
 
+template <bool FINAL>
+static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, const int *ea, int64_t rows,
+                                          int64_t cols, int gridK, int R, int nmod, const int *ptr, const int *code,
+                                          const int *icoef, void *out, int64_t out_ld, cudaStream_t s) {
+    const int64_t threads = rows * ((out_ld + 3) / 4);
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+#define FMM_SFR(NB) split_form_rows<NB, FINAL><<<blocks, 256, 0, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
+    switch (nb) {
+        case 1: FMM_SFR(1); break;
+        case 4: FMM_SFR(4); break;
+        case 6: FMM_SFR(6); break;
+        case 8: FMM_SFR(8); break;
+        case 9: FMM_SFR(9); break;
+        default: return cudaErrorNotSupported;
+    }
+#undef FMM_SFR
+    return cudaGetLastError();
+}
+
+template <bool FINAL>
+static cudaError_t launch_split_form_cols_t(int nb, const double *B, int64_t ldb, const int *eb, int64_t krows,
+                                            int64_t ncols, int gridN, int R, int nmod, const int *ptr,
+                                            const int *code, const int *icoef, void *out, int64_t out_ld,
+                                            cudaStream_t s) {
+    const dim3 grid((unsigned)((out_ld + 31) / 32), (unsigned)((ncols + 31) / 32));
+    const size_t smem = size_t(nb) * 32 * 33 * 8;   // >= nb * 256 * 16 (the residues reuse it)
+#define FMM_SFC(NB) split_form_cols_t<NB, FINAL><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
+    switch (nb) {
+        case 1: FMM_SFC(1); break;
+        case 4: FMM_SFC(4); break;
+        case 6: FMM_SFC(6); break;
+        case 8: FMM_SFC(8); break;
+        case 9: FMM_SFC(9); break;
+        default: return cudaErrorNotSupported;
+    }
+#undef FMM_SFC
+    return cudaGetLastError();
+}
+
+// Shared-memory limits of the transposing split (NB x 8448 bytes); once per device.
+static cudaError_t configure_split_form() {
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 64 || configured[dev]) return cudaSuccess;
+#define FMM_CFG(NB)                                                                                          \
+    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                  NB * 32 * 33 * 8)) != cudaSuccess)                                         \
+        return e;                                                                                            \
+    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  NB * 32 * 33 * 8)) != cudaSuccess)                                         \
+        return e;
+    FMM_CFG(1) FMM_CFG(4) FMM_CFG(6) FMM_CFG(8) FMM_CFG(9)
+#undef FMM_CFG
+    configured[dev] = true;
+    return cudaSuccess;
+}
+
 // C[:mp,:np] (+)= the fast algorithm run entirely in residue space on the
-// once-scaled A' and B', rebuilt by one CRT (see the residue-space kernels).
+// once-scaled A' and B' (L = 0: the classical product), rebuilt by the CRT
+// fused into the top level of the W combination.
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
                        int accumulate, void *ws, cudaStream_t s, int *launches) {
     cudaError_t e = ensure_tables(nmod);
     if (e != cudaSuccess) return e;
+    if ((e = configure_split_form()) != cudaSuccess) return e;
     int *err = nullptr;
     if ((e = cudaGetSymbolAddress((void **)&err, g_device_error)) != cudaSuccess) return e;
+    const int *id_ptr = nullptr, *id_code = nullptr, *id_coef = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&id_ptr, g_ident_ptr)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&id_code, g_ident_code)) != cudaSuccess) return e;
+    if ((e = cudaGetSymbolAddress((void **)&id_coef, g_ident_coef)) != cudaSuccess) return e;
     const ResLayout w = res_layout(rp, mp, kp, np, nmod);
+    const bool fused = first_level_fused(rp);
     char *b = (char *)ws;
-    int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
     int *ea = (int *)(b + w.ea), *eb = (int *)(b + w.eb);
     const int beta = ozaki_beta(nmod, kp);
     auto check = [&]() { ++*launches; return cudaGetLastError(); };
 
-    split_rows_i8<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, nmod, ra0, ea);
+    row_exp_kernel<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, ea);
     if ((e = check()) != cudaSuccess) return e;
     col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, 8), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
     if ((e = check()) != cudaSuccess) return e;
-    // B is kept transposed from here on (residues of B^T, n x k): every T_r is
-    // then formed directly in the K-major layout the residue GEMM reads
-    split_cols_t_i8<<<dim3((unsigned)((kp + 31) / 32), (unsigned)((np + 31) / 32)), dim3(32, 8), 0, s>>>(
-        B, ldb, kp, np, nmod, eb, rb0);
-    if ((e = check()) != cudaSuccess) return e;
-    // S and T^T level by level
-    int64_t parents = 1, pm = mp, pk = kp, pn = np;
-    const int8_t *pa = ra0, *pb = rb0;
-    auto form = [&](const int8_t *par, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
+
+    // level 1 (or the GEMM operands when L = 0) straight from A and B; B is
+    // kept transposed from here on, so every T_r is formed directly in the
+    // K-major layout the residue GEMM reads
+    {
+        const int64_t ml = mp / (rp.L ? rp.M : 1), kl = kp / (rp.L ? rp.K : 1), nl = np / (rp.L ? rp.N : 1);
+        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
+        const bool last = rp.L <= 1;
+        const int64_t out_ld = last ? kpad : kl;
+        const int R1 = rp.L ? rp.R : 1;
+        const int gK = rp.L ? rp.K : 1, gN = rp.L ? rp.N : 1, nbA = rp.L ? rp.M * rp.K : 1, nbB = rp.L ? rp.K * rp.N : 1;
+        const int *up = rp.L ? rp.u_ptr : id_ptr, *uc = rp.L ? rp.u_code : id_code, *ui = rp.L ? rp.u_icoef : id_coef;
+        const int *vp = rp.L ? rp.v_ptr : id_ptr, *vc = rp.L ? rp.v_code : id_code, *vi = rp.L ? rp.v_icoef : id_coef;
+        if (fused) {
+            e = last ? launch_split_form_rows<true>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s)
+                     : launch_split_form_rows<false>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s);
+            ++*launches;
+            if (e != cudaSuccess) return e;
+            e = last ? launch_split_form_cols_t<true>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s)
+                     : launch_split_form_cols_t<false>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s);
+            ++*launches;
+            if (e != cudaSuccess) return e;
+        }
+    }
+    auto form = [&](const int8_t *par, int64_t parents, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
                     const int *uptr, const int *ucode, const int *ucoef, void *out, bool last,
                     int64_t out_ld) -> cudaError_t {
         const int64_t outs = parents * rp.R;
@@ -879,19 +1399,38 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         }
         return cudaSuccess;
     };
-    for (int l = 1; l <= rp.L; ++l) {
+    if (!fused) {
+        // a base case without a fused first-level instance: level-0 residues, then level 1
+        int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
+        split_rows_i8<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, nmod, ra0, ea);
+        if ((e = check()) != cudaSuccess) return e;
+        split_cols_t_i8<<<dim3((unsigned)((kp + 31) / 32), (unsigned)((np + 31) / 32)), dim3(32, 8), 0, s>>>(
+            B, ldb, kp, np, nmod, eb, rb0);
+        if ((e = check()) != cudaSuccess) return e;
+        const int64_t ml = mp / rp.M, kl = kp / rp.K, nl = np / rp.N;
+        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
+        const bool last = rp.L == 1;
+        if ((e = form(ra0, 1, mp, kp, ml, kl, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[0], last,
+                      last ? kpad : kl)) != cudaSuccess)
+            return e;
+        if ((e = form(rb0, 1, np, kp, nl, kl, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last,
+                      last ? kpad : kl)) != cudaSuccess)
+            return e;
+    }
+    // levels 2..L: S and T^T level by level
+    int64_t parents = rp.L ? rp.R : 1;
+    int64_t pm = mp / (rp.L ? rp.M : 1), pk = kp / (rp.L ? rp.K : 1), pn = np / (rp.L ? rp.N : 1);
+    for (int l = 2; l <= rp.L; ++l) {
         const int64_t ml = pm / rp.M, kl = pk / rp.K, nl = pn / rp.N;
         const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
         const bool last = l == rp.L;
-        if ((e = form(pa, pm, pk, ml, kl, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[l - 1], last,
-                      last ? kpad : kl)) != cudaSuccess)
+        if ((e = form((const int8_t *)(b + w.la[l - 2]), parents, pm, pk, ml, kl, rp.u_ptr, rp.u_code,
+                      rp.u_icoef, b + w.la[l - 1], last, last ? kpad : kl)) != cudaSuccess)
             return e;
         // B^T: parent n x k, child nl x kl, block codes with rows and columns swapped
-        if ((e = form(pb, pn, pk, nl, kl, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[l - 1], last,
-                      last ? kpad : kl)) != cudaSuccess)
+        if ((e = form((const int8_t *)(b + w.lb[l - 2]), parents, pn, pk, nl, kl, rp.v_ptr, rp.vt_code,
+                      rp.v_icoef, b + w.lb[l - 1], last, last ? kpad : kl)) != cudaSuccess)
             return e;
-        pa = (const int8_t *)(b + w.la[l - 1]);
-        pb = (const int8_t *)(b + w.lb[l - 1]);
         parents *= rp.R;
         pm = ml; pk = kl; pn = nl;
     }
@@ -902,35 +1441,47 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, leaves * nmod, nmod,
                                  err, s, launches)) != cudaSuccess)
         return e;
-    // W level by level, down to the residues of C'
-    int64_t cm = mL, cn = nL;
+    // W levels L..2 on residues, down to the level-1 products
+    int64_t cm = mL, cn = nL, cld = z_pitch(nL);
     const int8_t *child = Z;
-    int64_t lp = leaves / rp.R;
-    for (int l = rp.L; l >= 1; --l) {
-        int8_t *parent = (l == 1) ? (int8_t *)(b + w.cres) : (int8_t *)(b + w.lw[l - 2]);
+    int64_t lp = leaves / (rp.L ? rp.R : 1);
+    for (int l = rp.L; l >= 2; --l) {
+        int8_t *parent = (int8_t *)(b + w.lw[l - 2]);
         const int64_t outs = lp * rp.M * rp.N;
         const bool vec = cn % 8 == 0;
         for (int64_t ob = 0; ob < outs; ob += 65535) {
             const unsigned cnt = (unsigned)std::min<int64_t>(65535, outs - ob);
             dim3 grid((unsigned)std::min<int64_t>(cm, 1024), cnt, (unsigned)nmod);
             if (vec)
-                res_w_kernel<true><<<grid, 128, 0, s>>>(child, cm, cn, rp.R, rp.N, rp.M * rp.N, nmod, parent,
+                res_w_kernel<true><<<grid, 128, 0, s>>>(child, cm, cn, cld, rp.R, rp.N, rp.M * rp.N, nmod, parent,
                                                         ob, rp.w_ptr, rp.w_r, rp.w_icoef);
             else
-                res_w_kernel<false><<<grid, 128, 0, s>>>(child, cm, cn, rp.R, rp.N, rp.M * rp.N, nmod, parent,
+                res_w_kernel<false><<<grid, 128, 0, s>>>(child, cm, cn, cld, rp.R, rp.N, rp.M * rp.N, nmod, parent,
                                                          ob, rp.w_ptr, rp.w_r, rp.w_icoef);
             if ((e = check()) != cudaSuccess) return e;
         }
         child = parent;
         cm *= rp.M;
         cn *= rp.N;
+        cld = cn;
         lp /= rp.R;
     }
+    // top level of W fused with the CRT, straight into C
     {
-        const int64_t total = mp * np;
-        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        crt_kernel<<<blocks, 256, 0, s>>>((const int8_t *)(b + w.cres), mp, np, 1, nmod, ea, eb, C, ldc,
-                                          0, accumulate);
+        const int gN = rp.L ? rp.N : 1, MN = rp.L ? rp.M * rp.N : 1;
+        const int *wp = rp.L ? rp.w_ptr : id_ptr, *wr = rp.L ? rp.w_r : id_code, *wc = rp.L ? rp.w_icoef : id_coef;
+        // |limb sum| <= (sum_t |w_t|) 128 (2^16 - 1) nmod
+        const bool reduce = double(rp.L ? rp.w_absmax : 1) * 128.0 * 65535.0 * nmod >= 1073741824.0;
+        const bool v8 = cld % 8 == 0;
+        const int64_t threads = v8 ? cm * ((cn + 7) / 8) : cm * cn;
+        const unsigned blocks = (unsigned)((threads + 255) / 256);
+#define FMM_WCRT(V, RED) w_crt_kernel<V, RED><<<blocks, 256, 0, s>>>(child, cm, cn, cld, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
+        if (v8) {
+            if (reduce) FMM_WCRT(8, true); else FMM_WCRT(8, false);
+        } else {
+            if (reduce) FMM_WCRT(1, true); else FMM_WCRT(1, false);
+        }
+#undef FMM_WCRT
         if ((e = check()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -986,7 +1537,10 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
     {
         const int64_t total = leaves * m * n;
         const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
-        crt_kernel<<<blocks, 256, 0, s>>>(Z, m, n, leaves, nmod, ea, eb, Out, ldo, os, 0);
+        if (n % 4 == 0)
+            crt_kernel<4><<<blocks, 256, 0, s>>>(Z, m, n, z_pitch(n), leaves, nmod, ea, eb, Out, ldo, os, 0);
+        else
+            crt_kernel<1><<<blocks, 256, 0, s>>>(Z, m, n, z_pitch(n), leaves, nmod, ea, eb, Out, ldo, os, 0);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
