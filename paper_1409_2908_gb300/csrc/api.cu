@@ -137,6 +137,14 @@ ResPlan res_plan(const fmm_plan *p) {
         for (int r = 0; r < p->R; ++r) sum += std::fabs(p->W[size_t(q) * p->R + r]);
         rp.w_absmax = std::max(rp.w_absmax, int(sum));
     }
+    rp.u_absmax = rp.v_absmax = 0;
+    for (int r = 0; r < p->R; ++r) {
+        double su = 0, sv = 0;
+        for (int i = 0; i < p->M * p->K; ++i) su += std::fabs(p->U[size_t(i) * p->R + r]);
+        for (int j = 0; j < p->K * p->N; ++j) sv += std::fabs(p->V[size_t(j) * p->R + r]);
+        rp.u_absmax = std::max(rp.u_absmax, int(su));
+        rp.v_absmax = std::max(rp.v_absmax, int(sv));
+    }
     return rp;
 }
 

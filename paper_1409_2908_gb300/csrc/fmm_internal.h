@@ -168,6 +168,7 @@ struct ResPlan {
     const int *vt_code;                      // B block codes with row and column swapped (B^T)
     const int *w_ptr, *w_r, *w_icoef;
     int w_absmax;                            // max over C blocks of sum_r |W_qr|
+    int u_absmax, v_absmax;                  // max over r of sum_i |U_ir|, of sum_j |V_jr|
 };
 size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod);
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,

@@ -51,6 +51,7 @@ __constant__ unsigned c_magic[OZ_MAX_MOD];                // floor(2^32 / p)
 __constant__ unsigned c_r32[OZ_MAX_MOD];                  // 2^32 mod p
 __constant__ unsigned c_r21[OZ_MAX_MOD], c_r42[OZ_MAX_MOD];  // 2^21 and 2^42 mod p
 __constant__ float c_modf[OZ_MAX_MOD], c_invp[OZ_MAX_MOD];  // p and 1/p as floats
+__constant__ float c_k13[OZ_MAX_MOD][5];                   // 2^(13 i) mod p as floats
 constexpr int OZ_MAX_TERMS = 512, OZ_MAX_R = 64;           // limits of the staged term lists
 // CRT by a weighted sum: X = sum_q r_q c_q (mod P), c_q = (P/p_q) ((P/p_q)^-1 mod p_q)
 // mod P, held as eight 16-bit limbs so every limb sum fits an int32.
@@ -658,25 +659,6 @@ __global__ void res_w_kernel(const int8_t *child, int64_t rows, int64_t cols, in
 // identity (one block, one child, coefficient 1) and the pass writes the GEMM
 // operand planes directly.
 
-// Residue in [0, p) of an integer |v| < 2^62: v = a 2^42 + b 2^21 + c (a
-// signed, b and c in [0, 2^21)), folded with 2^42 and 2^21 mod p into one
-// positive 31-bit value, then one Barrett step.
-__device__ __forceinline__ unsigned res_i64(long long v, int q) {
-    const int a = (int)(v >> 42);
-    const unsigned b = (unsigned)(v >> 21) & 0x1fffffu, c = (unsigned)v & 0x1fffffu;
-    const int x = a * (int)c_r42[q] + (int)(b * c_r21[q]) + (int)c + (c_mod[q] << 22);
-    return mod_u32((unsigned)x, q);
-}
-
-// Two small integers (|x| <= 256, exact in bfloat16) as a packed bfloat16
-// pair, lo in the low half: x = float(1.5 2^23 + x) - 1.5 2^23 exactly, and
-// the bfloat16 is the upper half of that float (its low 16 bits are zero).
-__device__ __forceinline__ unsigned bf16x2_of_ints(int lo, int hi) {
-    const float flo = __int_as_float(0x4B400000 + lo) - 12582912.0f;
-    const float fhi = __int_as_float(0x4B400000 + hi) - 12582912.0f;
-    return __byte_perm(__float_as_uint(flo), __float_as_uint(fhi), 0x7632);
-}
-
 // Balanced residue of a small combination |x| < 2^29.
 __device__ __forceinline__ int bal_small(int x, int q) {
     const int p = c_mod[q];
@@ -688,117 +670,95 @@ __device__ __forceinline__ int bal_small(int x, int q) {
 constexpr float OZ_FMAGIC = 12582912.0f;
 constexpr int OZ_IMAGIC = 0x4B400000;
 
-// Limbs of an integer |v| < 2^62: v = a 2^42 + b 2^21 + c, a signed, b and c in [0, 2^21).
-__device__ __forceinline__ void limbs_of(long long v, int &a, unsigned &b, unsigned &c) {
-    a = (int)(v >> 42);
-    b = (unsigned)(v >> 21) & 0x1fffffu;
-    c = (unsigned)v & 0x1fffffu;
+// One child of the first level: S' = sum_t c_t X'_t over the thread's NB
+// block values (int64 in shared memory, [b][e][thread], 4 consecutive
+// entries e), exact in int64 (host-checked: 2^beta sum |c_t| < 2^63); then
+// per modulus q the residue from 13-bit limbs of |S'|,
+//   x = sum_i d_i (2^(13 i) mod p)   (|x| < 2^23.3, exact in float),
+// reduced to its nearest representative (|r| <= p/2 + 1) and written to
+// dst + q qstep as bfloat16 (FINAL, the GEMM operand; |r| <= 129 is exact and
+// keeps the GEMM's 512-long FP32 chunks exact) or int8 (a later level's input;
+// representatives that wrap stay in the same class: only p = 256 reaches 128).
+template <bool FINAL>
+__device__ __forceinline__ void emit_child(const long long *sv, const int2 *sterm, int t0, int t1, int nmod,
+                                           char *dst, int64_t qstep, int valid) {
+    long long S[4] = {0, 0, 0, 0};
+    for (int t = t0; t < t1; ++t) {
+        const int2 tm = sterm[t];
+        const long long *src = sv + tm.x * 4 * 256 + threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) S[e] += (long long)tm.y * src[e * 256];
+    }
+    float d[4][5];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const bool neg = S[e] < 0;
+        const unsigned long long u = neg ? (unsigned long long)(-S[e]) : (unsigned long long)S[e];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const float f = __int_as_float(OZ_IMAGIC + (int)((u >> (13 * i)) & 0x1fffull)) - OZ_FMAGIC;
+            d[e][i] = neg ? -f : f;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < OZ_CRT_MAX; ++q) {
+        if (q >= nmod) break;
+        float r[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            float x = d[e][0];
+#pragma unroll
+            for (int i = 1; i < 5; ++i) x = fmaf(d[e][i], c_k13[q][i], x);
+            const float tq = fmaf(x, c_invp[q], OZ_FMAGIC) - OZ_FMAGIC;
+            r[e] = fmaf(-tq, c_modf[q], x);
+        }
+        char *out = dst + q * qstep;
+        if (FINAL) {
+            uint2 pk;
+            pk.x = __byte_perm(__float_as_uint(r[0]), __float_as_uint(r[1]), 0x7632);
+            pk.y = __byte_perm(__float_as_uint(r[2]), __float_as_uint(r[3]), 0x7632);
+            if (valid == 4) {
+                *reinterpret_cast<uint2 *>(out) = pk;
+            } else {
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&pk);
+                for (int e = 0; e < valid; ++e) reinterpret_cast<__nv_bfloat16 *>(out)[e] = h[e];
+            }
+        } else {
+            unsigned word = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                word |= ((unsigned)(__float_as_int(r[e] + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu) << (8 * e);
+            if (valid == 4 && ((uintptr_t)out & 3) == 0) {
+                *reinterpret_cast<unsigned *>(out) = word;
+            } else {
+                for (int e = 0; e < valid; ++e) reinterpret_cast<int8_t *>(out)[e] = (int8_t)(word >> (8 * e));
+            }
+        }
+    }
 }
 
-// The constants of one modulus, loaded once per modulus loop iteration.
-struct ModK {
-    int p, off;                 // p, p 2^22 (keeps the folded limbs positive)
-    unsigned magic, r21, r42;   // floor(2^32 / p), 2^21 mod p, 2^42 mod p
-    float pf, invp;             // p, 1/p
-};
-__device__ __forceinline__ ModK mod_consts(int q) {
-    ModK k;
-    k.p = c_mod[q];
-    k.off = k.p << 22;
-    k.magic = c_magic[q];
-    k.r21 = c_r21[q];
-    k.r42 = c_r42[q];
-    k.pf = c_modf[q];
-    k.invp = c_invp[q];
-    return k;
-}
-
-// Residue in [0, p) of a 2^42 + b 2^21 + c as an integer-valued float: the
-// limbs folded with 2^42, 2^21 mod p into one value in (0, 2^31), then one
-// Barrett step (quotient at most one short).
-__device__ __forceinline__ float res_f(int a, unsigned b, unsigned c, const ModK &k) {
-    const unsigned x = (unsigned)(a * (int)k.r42 + k.off) + b * k.r21 + c;
-    unsigned r = x - __umulhi(x, k.magic) * (unsigned)k.p;
-    r = r >= (unsigned)k.p ? r - (unsigned)k.p : r;
-    return __int_as_float(OZ_IMAGIC + (int)r) - OZ_FMAGIC;
-}
-
-// Nearest representative (|r| <= p/2) of an integer-valued float x, |x| < 2^22,
-// modulo p: r = x - rint(x / p) p, exact (the quotient estimate can only pick
-// the other neighbour at an exact half, where both are nearest).
-__device__ __forceinline__ float near_mod(float x, const ModK &k) {
-    const float t = fmaf(x, k.invp, OZ_FMAGIC) - OZ_FMAGIC;
-    return fmaf(-t, k.pf, x);
-}
-
-// Stage one level's term lists in shared memory: sterm[t] = (block index in
-// the thread's residue array, coefficient as float bits), sptr[o] = CSR.
+// Stage one level's term lists in shared memory: sterm[t] = (block index,
+// integer coefficient), sptr[o] = CSR over the children.
 __device__ __forceinline__ void stage_terms(int R, int gridC, const int *ptr, const int *code, const int *icoef,
                                             int2 *sterm, int *sptr) {
     const int nterms = __ldg(ptr + R);
     for (int t = threadIdx.x; t < nterms; t += blockDim.x) {
         const int cd = __ldg(code + t);
-        sterm[t] = make_int2((cd >> 16) * gridC + (cd & 0xffff), __float_as_int((float)__ldg(icoef + t)));
+        sterm[t] = make_int2((cd >> 16) * gridC + (cd & 0xffff), __ldg(icoef + t));
     }
     for (int o = threadIdx.x; o <= R; o += blockDim.x) sptr[o] = __ldg(ptr + o);
-}
-
-// Children o = 0..R-1 of one level, modulus q, from the NB block residues the
-// thread keeps in shared memory (4 consecutive entries per float4):
-// child_o = sum_t c_t block(t) mod p (nearest representative), written to
-// out[(o nmod + q) plane + base .. + valid) as bfloat16 (FINAL, the GEMM
-// operand) or int8 (a later level's input; +-128 are one class mod 256).
-template <bool FINAL>
-__device__ __forceinline__ void emit_children(const float4 *sres, const int2 *sterm, const int *sptr, int R,
-                                              const ModK &k, char *dst, int64_t ostep, int valid) {
-    for (int o = 0; o < R; ++o, dst += ostep) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        const int t1 = sptr[o + 1];
-        for (int t = sptr[o]; t < t1; ++t) {
-            const int2 tm = sterm[t];
-            const float4 w = sres[tm.x * 256 + threadIdx.x];
-            const float c = __int_as_float(tm.y);
-            a0 = fmaf(c, w.x, a0);
-            a1 = fmaf(c, w.y, a1);
-            a2 = fmaf(c, w.z, a2);
-            a3 = fmaf(c, w.w, a3);
-        }
-        const float r0 = near_mod(a0, k), r1 = near_mod(a1, k), r2 = near_mod(a2, k), r3 = near_mod(a3, k);
-        if (FINAL) {
-            uint2 pk;
-            pk.x = __byte_perm(__float_as_uint(r0), __float_as_uint(r1), 0x7632);
-            pk.y = __byte_perm(__float_as_uint(r2), __float_as_uint(r3), 0x7632);
-            if (valid == 4) {
-                *reinterpret_cast<uint2 *>(dst) = pk;
-            } else {
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&pk);
-                for (int e = 0; e < valid; ++e) reinterpret_cast<__nv_bfloat16 *>(dst)[e] = h[e];
-            }
-        } else {
-            const unsigned b0 = (unsigned)(__float_as_int(r0 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
-            const unsigned b1 = (unsigned)(__float_as_int(r1 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
-            const unsigned b2 = (unsigned)(__float_as_int(r2 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
-            const unsigned b3 = (unsigned)(__float_as_int(r3 + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
-            const unsigned word = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-            if (valid == 4 && ((uintptr_t)dst & 3) == 0) {
-                *reinterpret_cast<unsigned *>(dst) = word;
-            } else {
-                for (int e = 0; e < valid; ++e) reinterpret_cast<int8_t *>(dst)[e] = (int8_t)(word >> (8 * e));
-            }
-        }
-    }
 }
 
 // S side: A (peeled core, ld lda) as a grid of M x K blocks of rows x cols;
 // A' = trunc(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
 // consecutive columns of out_ld (columns >= cols are the zero padding of the
-// GEMM operand).  256 threads.
+// GEMM operand).  256 threads; dynamic shared memory NB x 4 x 256 int64.
 template <int NB, bool FINAL>
 __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t lda, const int *ea, int64_t rows,
                                                        int64_t cols, int gridK, int R, int nmod, const int *ptr,
                                                        const int *code, const int *icoef, void *out,
                                                        int64_t out_ld) {
-    __shared__ float4 sres[NB * 256];
+    extern __shared__ long long sv[];   // [NB][4][256]
     __shared__ int2 sterm[OZ_MAX_TERMS];
     __shared__ int sptr[OZ_MAX_R + 1];
     stage_terms(R, gridK, ptr, code, icoef, sterm, sptr);
@@ -808,42 +768,34 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
     if (pos >= rows * groups) return;
     const int64_t i = pos / groups, j0 = (pos % groups) * 4;
     const int valid = (int)min((int64_t)4, out_ld - j0);
-    int la[NB][4];
-    unsigned lb[NB][4], lc[NB][4];
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
         const int64_t row = (int64_t)(b / gridK) * rows + i;
         const int s = ea[row];
         const double *x = A + row * lda + (int64_t)(b % gridK) * cols + j0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) limbs_of((j0 + e < cols) ? scaled_trunc(x[e], s) : 0, la[b][e], lb[b][e], lc[b][e]);
+        for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = (j0 + e < cols) ? scaled_trunc(x[e], s) : 0;
     }
-    const int64_t plane = rows * out_ld, base = i * out_ld + j0;
     constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
-    char *dst = (char *)out + base * ES;
+    const int64_t plane = rows * out_ld;
+    char *dst = (char *)out + (i * out_ld + j0) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
-    for (int q = 0; q < nmod; ++q, dst += qstep) {
-        const ModK k = mod_consts(q);
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-            sres[b * 256 + threadIdx.x] = make_float4(res_f(la[b][0], lb[b][0], lc[b][0], k), res_f(la[b][1], lb[b][1], lc[b][1], k),
-                                                      res_f(la[b][2], lb[b][2], lc[b][2], k), res_f(la[b][3], lb[b][3], lc[b][3], k));
-        emit_children<FINAL>(sres, sterm, sptr, R, k, dst, ostep, valid);
-    }
+    for (int o = 0; o < R; ++o, dst += ostep)
+        emit_child<FINAL>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
 }
 
 // T side, transposed: B (peeled core, ld ldb) as a grid of K x N blocks of
 // krows x ncols; B' = trunc(B_ij 2^eb_j).  Output rows are columns of B
 // (T^T, K-major for the GEMM).  CTA: 32 k x 32 n positions of the child
-// blocks through shared memory (dynamic: NB x 32 x 33 int64, reused for the
-// residues); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
+// blocks through shared memory (dynamic: NB x 32 x 33 int64, then reused as
+// [NB][4][256]); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
 // ceil(ncols / 32)), 256 threads.
 template <int NB, bool FINAL>
 __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_t ldb, const int *eb, int64_t krows,
                                                          int64_t ncols, int gridN, int R, int nmod, const int *ptr,
                                                          const int *code, const int *icoef, void *out,
                                                          int64_t out_ld) {
-    extern __shared__ long long sv[];   // [NB][32][33], then float4 residues [NB][256]
+    extern __shared__ long long sv[];
     __shared__ int2 sterm[OZ_MAX_TERMS];
     __shared__ int sptr[OZ_MAX_R + 1];
     stage_terms(R, gridN, ptr, code, icoef, sterm, sptr);
@@ -862,29 +814,25 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
     }
     __syncthreads();
     const int nn = threadIdx.x / 8, kk = (threadIdx.x % 8) * 4;
-    int la[NB][4];
-    unsigned lb[NB][4], lc[NB][4];
+    long long v[NB][4];
 #pragma unroll
     for (int b = 0; b < NB; ++b)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) limbs_of(sv[(b * 32 + kk + e) * 33 + nn], la[b][e], lb[b][e], lc[b][e]);
-    __syncthreads();   // sv is reused for the residues below
-    float4 *sres = reinterpret_cast<float4 *>(sv);
+        for (int e = 0; e < 4; ++e) v[b][e] = sv[(b * 32 + kk + e) * 33 + nn];
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = v[b][e];
     const int64_t n = n0 + nn, k = k0 + kk;
     if (n >= ncols || k >= out_ld) return;
     const int valid = FINAL ? 4 : (int)min((int64_t)4, krows - k);
-    const int64_t plane = ncols * out_ld, base = n * out_ld + k;
-    constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
-    char *dst = (char *)out + base * ES;
+    constexpr int ES = FINAL ? 2 : 1;
+    const int64_t plane = ncols * out_ld;
+    char *dst = (char *)out + (n * out_ld + k) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
-    for (int q = 0; q < nmod; ++q, dst += qstep) {
-        const ModK k = mod_consts(q);
-#pragma unroll
-        for (int b = 0; b < NB; ++b)
-            sres[b * 256 + threadIdx.x] = make_float4(res_f(la[b][0], lb[b][0], lc[b][0], k), res_f(la[b][1], lb[b][1], lc[b][1], k),
-                                                      res_f(la[b][2], lb[b][2], lc[b][2], k), res_f(la[b][3], lb[b][3], lc[b][3], k));
-        emit_children<FINAL>(sres, sterm, sptr, R, k, dst, ostep, valid);
-    }
+    for (int o = 0; o < R; ++o, dst += ostep)
+        emit_child<FINAL>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
 }
 
 // Top recursion level of the W combination fused with the CRT: output block
@@ -920,7 +868,7 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
 #pragma unroll
             for (int l = 0; l < 8; ++l) L[e][l] = 0;
         const int t0 = swp[qb], t1 = swp[qb + 1];
-#pragma unroll 2
+#pragma unroll 4
         for (int q = 0; q < nmod; ++q) {
             int acc[V];
 #pragma unroll
@@ -928,13 +876,10 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
             for (int t = t0; t < t1; ++t) {
                 const int2 wt = swt[t];
                 const int8_t *z = zrow + ((int64_t)wt.x * nmod + q) * plane;
-                if (V == 8) {
-                    const uint2 raw = *reinterpret_cast<const uint2 *>(z);
+                if (V == 4) {
+                    const unsigned raw = *reinterpret_cast<const unsigned *>(z);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        acc[e] += wt.y * (int)(int8_t)(raw.x >> (8 * e));
-                        acc[e + 4] += wt.y * (int)(int8_t)(raw.y >> (8 * e));
-                    }
+                    for (int e = 0; e < 4; ++e) acc[e] += wt.y * (int)(int8_t)(raw >> (8 * e));
                 } else {
                     acc[0] += wt.y * (int)z[0];
                 }
@@ -1111,6 +1056,14 @@ cudaError_t ensure_tables(int nmod) {
         }
         if ((e = cudaMemcpyToSymbol(c_modf, modf, sizeof(modf))) != cudaSuccess) return e;
         if ((e = cudaMemcpyToSymbol(c_invp, invp, sizeof(invp))) != cudaSuccess) return e;
+        float k13[OZ_MAX_MOD][5];
+        for (int i = 0; i < OZ_MAX_MOD; ++i)
+            for (int l = 0; l < 5; ++l) {
+                unsigned long long w = 1;
+                for (int t = 0; t < 13 * l; ++t) w = (w * 2) % (unsigned long long)mods[i];
+                k13[i][l] = (float)w;
+            }
+        if ((e = cudaMemcpyToSymbol(c_k13, k13, sizeof(k13))) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyToSymbol(c_crt16, crt16, sizeof(crt16))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_P16, P16, sizeof(P16))) != cudaSuccess) return e;
@@ -1224,7 +1177,14 @@ struct ResLayout {
 // Block counts of the fused first-level kernels with a compiled instance.
 static bool fused_nb(int nb) { return nb == 1 || nb == 4 || nb == 6 || nb == 8 || nb == 9; }
 
-static bool first_level_fused(const ResPlan &rp) {
+// The fused first level combines the scaled integers (|X'| < 2^beta) in
+// int64: 2^beta sum_t |c_t| must stay below 2^62.
+static bool first_level_fused(const ResPlan &rp, int nmod, int64_t kp) {
+    const int beta = ozaki_beta(nmod, kp);
+    const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
+    int lg = 0;
+    while ((1 << lg) < cmax) ++lg;
+    if (beta + lg > 62) return false;
     return rp.L == 0 || (fused_nb(rp.M * rp.K) && fused_nb(rp.K * rp.N));
 }
 
@@ -1233,7 +1193,7 @@ static ResLayout res_layout(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
-    if (!first_level_fused(rp)) {
+    if (!first_level_fused(rp, nmod, kp)) {
         w.ra0 = take(size_t(nmod) * mp * kp);
         w.rb0 = take(size_t(nmod) * kp * np);
     }
@@ -1274,7 +1234,8 @@ static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, 
                                           const int *icoef, void *out, int64_t out_ld, cudaStream_t s) {
     const int64_t threads = rows * ((out_ld + 3) / 4);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
-#define FMM_SFR(NB) split_form_rows<NB, FINAL><<<blocks, 256, 0, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
+    const size_t smem = size_t(nb) * 4 * 256 * 8;
+#define FMM_SFR(NB) split_form_rows<NB, FINAL><<<blocks, 256, smem, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
     switch (nb) {
         case 1: FMM_SFR(1); break;
         case 4: FMM_SFR(4); break;
@@ -1293,7 +1254,7 @@ static cudaError_t launch_split_form_cols_t(int nb, const double *B, int64_t ldb
                                             const int *code, const int *icoef, void *out, int64_t out_ld,
                                             cudaStream_t s) {
     const dim3 grid((unsigned)((out_ld + 31) / 32), (unsigned)((ncols + 31) / 32));
-    const size_t smem = size_t(nb) * 32 * 33 * 8;   // >= nb * 256 * 16 (the residues reuse it)
+    const size_t smem = size_t(nb) * 32 * 33 * 8;   // >= nb * 4 * 256 * 8 (reused after the transpose)
 #define FMM_SFC(NB) split_form_cols_t<NB, FINAL><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
     switch (nb) {
         case 1: FMM_SFC(1); break;
@@ -1320,6 +1281,12 @@ static cudaError_t configure_split_form() {
         return e;                                                                                            \
     if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   NB * 32 * 33 * 8)) != cudaSuccess)                                         \
+        return e;                                                                                            \
+    if ((e = cudaFuncSetAttribute(split_form_rows<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                  NB * 4 * 256 * 8)) != cudaSuccess)                                         \
+        return e;                                                                                            \
+    if ((e = cudaFuncSetAttribute(split_form_rows<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                  NB * 4 * 256 * 8)) != cudaSuccess)                                         \
         return e;
     FMM_CFG(1) FMM_CFG(4) FMM_CFG(6) FMM_CFG(8) FMM_CFG(9)
 #undef FMM_CFG
@@ -1343,7 +1310,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     if ((e = cudaGetSymbolAddress((void **)&id_code, g_ident_code)) != cudaSuccess) return e;
     if ((e = cudaGetSymbolAddress((void **)&id_coef, g_ident_coef)) != cudaSuccess) return e;
     const ResLayout w = res_layout(rp, mp, kp, np, nmod);
-    const bool fused = first_level_fused(rp);
+    const bool fused = first_level_fused(rp, nmod, kp);
     char *b = (char *)ws;
     int *ea = (int *)(b + w.ea), *eb = (int *)(b + w.eb);
     const int beta = ozaki_beta(nmod, kp);
@@ -1472,12 +1439,12 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         const int *wp = rp.L ? rp.w_ptr : id_ptr, *wr = rp.L ? rp.w_r : id_code, *wc = rp.L ? rp.w_icoef : id_coef;
         // |limb sum| <= (sum_t |w_t|) 128 (2^16 - 1) nmod
         const bool reduce = double(rp.L ? rp.w_absmax : 1) * 128.0 * 65535.0 * nmod >= 1073741824.0;
-        const bool v8 = cld % 8 == 0;
-        const int64_t threads = v8 ? cm * ((cn + 7) / 8) : cm * cn;
+        const bool v4 = cld % 4 == 0;
+        const int64_t threads = v4 ? cm * ((cn + 3) / 4) : cm * cn;
         const unsigned blocks = (unsigned)((threads + 255) / 256);
 #define FMM_WCRT(V, RED) w_crt_kernel<V, RED><<<blocks, 256, 0, s>>>(child, cm, cn, cld, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
-        if (v8) {
-            if (reduce) FMM_WCRT(8, true); else FMM_WCRT(8, false);
+        if (v4) {
+            if (reduce) FMM_WCRT(4, true); else FMM_WCRT(4, false);
         } else {
             if (reduce) FMM_WCRT(1, true); else FMM_WCRT(1, false);
         }
