@@ -22,12 +22,14 @@ from dataclasses import asdict, dataclass
 
 import paper_1409_2908_gb300 as fmm
 
-# measured on GB300 (bench runs, profiles/): FP64 DFMA ceiling and the
-# emulated path's per-element costs, used only to rank candidates
+# measured on GB300 (benchmark runs at 8192^3), used only to rank candidates:
+# the classical FP64 DFMA GEMM, the residue GEMM, and the emulated path's
+# memory passes as achieved bytes per second
 FP64_TFLOPS = 1.22
-TC_TFLOPS = 690.0
-SPLIT_NS_PER_ELEM_MOD = 0.0016       # per operand element and modulus
-CRT_NS_PER_ELEM = 0.061              # per output element (15 moduli)
+TC_TFLOPS = 1850.0                   # residue GEMM (tcgen05, bf16 residues)
+SPLIT_GBS = 3900.0                   # fused scaling + residues + first level
+LEVEL_GBS = 2200.0                   # later levels of S/T and W on int8 residues
+CRT_PS_PER_ELEM_MOD = 1.9            # top W level fused with the CRT
 HBM_GBS = 6700.0
 
 
@@ -60,8 +62,9 @@ def algorithms():
 
 
 def moduli_for(tol, k):
-    """Fewest moduli whose truncation error 2^(1-beta) (with a factor 16 of
-    slack for accumulation) meets the relative tolerance."""
+    """Fewest moduli whose truncation error 2^(1-beta) (with a factor 4 of
+    slack; measured e_F on uniform data is about 0.9 x 2^(1-beta)) meets the
+    relative tolerance."""
     for n in range(6, 17):
         P = 1
         for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
@@ -69,7 +72,7 @@ def moduli_for(tol, k):
         beta = 62
         while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
             beta -= 1
-        if 16 * 2.0 ** (1 - beta) <= tol:
+        if 4 * 2.0 ** (1 - beta) <= tol:
             return n
     return None
 
@@ -143,12 +146,20 @@ class Autotuner:
             flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
         else:
             kpad = -(-kL // 64) * 64
-            t = 2.0 * leaves * nmod * mL * kpad * nL / (TC_TFLOPS * 1e12 * classical_efficiency(mL, nL))
-            t += (mp * kp + kp * np_) * nmod * SPLIT_NS_PER_ELEM_MOD * 1e-9 * 8
-            t += mp * np_ * CRT_NS_PER_ELEM * 1e-9 * (nmod / 15.0)
-            for l in range(1, L + 1):
-                t += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
-                               + (mp // M ** l) * (np_ // N ** l)) * nmod * 3 / (HBM_GBS * 1e9)
+            t = 2.0 * leaves * nmod * mL * kpad * nL / (TC_TFLOPS * 1e12 * classical_efficiency(mL, nL, 256))
+            # exponents, then the fused first level: FP64 in, R/(MK) residue
+            # planes out per operand element (bfloat16 when it is the last level)
+            grow_a = R / (M * K) if L else 1.0
+            grow_b = R / (K * N) if L else 1.0
+            width = 2 if L <= 1 else 1
+            t += (mp * kp + kp * np_) * 8 * 2 / (HBM_GBS * 1e9)
+            t += (mp * kp * (8 + grow_a * nmod * width) + kp * np_ * (8 + grow_b * nmod * width)) / (SPLIT_GBS * 1e9)
+            for l in range(2, L + 1):
+                w = 2 if l == L else 1
+                ml, kl, nl = mp // M ** l, kp // K ** l, np_ // N ** l
+                t += R ** l * (ml * kl + kl * nl) * nmod * (2 + w) / (LEVEL_GBS * 1e9)
+                t += R ** (l - 1) * M * N * ml * nl * nmod * 3 / (LEVEL_GBS * 1e9)
+            t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12
             flags = fmm.FLAGS_DEFAULT
         t += fringe / (FP64_TFLOPS * 1e12)
         return Choice(name, L, flags, prec, nmod or 15, "auto", 1e3 * t)

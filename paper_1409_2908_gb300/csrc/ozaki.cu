@@ -219,27 +219,37 @@ __device__ __forceinline__ double round_scale(long long hi_s, unsigned long long
     return neg ? -d : d;
 }
 
-// Add residue r (|r| < 2^8, any representative) of modulus q of n to the limb sums.
-__device__ __forceinline__ void crt_add(int (&L)[8], int r, int q, int n) {
+// 16-bit limbs needed for P of n moduli (ceil(bits(P) / 16)); 8 for n = 0
+// (a count known only at run time).
+__host__ __device__ constexpr int crt_limbs(int n) { return n <= 0 ? 8 : (n <= 2 ? 1 : (n + 1) / 2); }
+
+// Add residue r (|r| < 2^8, any representative) of modulus q of n to the limb
+// sums (NL limbs: limbs of c_q above those of P are zero).
+template <int NL>
+__device__ __forceinline__ void crt_add(int (&L)[NL], int r, int q, int n) {
 #pragma unroll
-    for (int l = 0; l < 8; ++l) L[l] += r * c_crt16[n][q][l];
+    for (int l = 0; l < NL; ++l) L[l] += r * c_crt16[n][q][l];
 }
 
 // The integer X in [P div 2 - P, P div 2) congruent to the residues summed in
 // L, rounded once to FP64 and scaled by 2^-e.  S = sum_l L_l 2^(16 l); the
 // quotient t = round(S / P) comes from a float estimate (off by at most one
 // near a half-integer), X = S - t P exactly in limbs, then one correction.
-__device__ __forceinline__ double crt_finish(const int (&L)[8], int e, int n) {
+// NL: limbs held; TIGHT: NL is exactly the limb count of P (n known at compile
+// time), so only the top three limbs matter for the quotient (the others
+// weigh below 2^-40 and their sums stay below 2^31); otherwise all are used.
+template <int NL, bool TIGHT>
+__device__ __forceinline__ double crt_finish(const int (&L)[NL], int e, int n) {
     float sf = 0.f;
 #pragma unroll
-    for (int l = 0; l < 8; ++l) sf = fmaf((float)L[l], c_fw[n][l], sf);
+    for (int l = (TIGHT && NL > 3 ? NL - 3 : 0); l < NL; ++l) sf = fmaf((float)L[l], c_fw[n][l], sf);
     // t = rint(sf) (|sf| < 2^22); xf estimates X / P to within 2^-10
     const float sm = sf + 12582912.0f;
     const int t = __float_as_int(sm) - 0x4B400000;
     const float xf = sf - (sm - 12582912.0f);
     int x[8];
 #pragma unroll
-    for (int l = 0; l < 8; ++l) x[l] = L[l] - t * c_P16[n][l];
+    for (int l = 0; l < 8; ++l) x[l] = l < NL ? L[l] - t * c_P16[n][l] : 0;
 #pragma unroll
     for (int l = 0; l < 7; ++l) {
         const int carry = x[l] >> 16;
@@ -299,7 +309,7 @@ __global__ void crt_kernel(const int8_t *Z, int64_t m, int64_t n, int64_t ldz, i
         const int ei = sa[leaf * m + i];
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            const double val = crt_finish(L[e], ei + sb[leaf * n + j + e], nmod);
+            const double val = crt_finish<8, false>(L[e], ei + sb[leaf * n + j + e], nmod);
             out[e] = accumulate ? out[e] + val : val;
         }
     }
@@ -668,11 +678,15 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
 // C'_qb from its residues, times 2^-(ea_i + eb_j), stored (or added) in C.
 // With L = 0 the one child is the product itself.  Thread: one row of the
 // child blocks, V consecutive columns.
-template <int V, bool REDUCE>
+template <int V, bool REDUCE, int NMOD>
 __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t rows, int64_t cols, int64_t cld,
-                                                    int gridN, int MN, int nmod, const int *w_ptr, const int *w_r,
+                                                    int gridN, int MN, int nmod_rt, const int *w_ptr, const int *w_r,
                                                     const int *w_icoef, const int *ea, const int *eb, double *C,
                                                     int64_t ldc, int accumulate) {
+    // NMOD > 0: the moduli count is a compile-time constant (loops unrolled,
+    // CRT constants as immediate operands, only the limbs P needs)
+    const int nmod = NMOD ? NMOD : nmod_rt;
+    constexpr int NL = crt_limbs(NMOD);
     __shared__ int2 swt[OZ_MAX_TERMS];   // (child r, coefficient)
     __shared__ int swp[OZ_MAX_R + 1];
     {
@@ -690,13 +704,13 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
     const int8_t *zrow = Z + i * cld + j0;
     for (int qb = 0; qb < MN; ++qb) {
         const int a = qb / gridN, c = qb % gridN;
-        int L[V][8];
+        int L[V][NL];
 #pragma unroll
         for (int e = 0; e < V; ++e)
 #pragma unroll
-            for (int l = 0; l < 8; ++l) L[e][l] = 0;
+            for (int l = 0; l < NL; ++l) L[e][l] = 0;
         const int t0 = swp[qb], t1 = swp[qb + 1];
-#pragma unroll 4
+#pragma unroll (NMOD ? NMOD : 4)
         for (int q = 0; q < nmod; ++q) {
             int acc[V];
 #pragma unroll
@@ -724,7 +738,7 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             if (e < valid) {
-                const double val = crt_finish(L[e], er + ebc[e], nmod);
+                const double val = crt_finish<NL, (NMOD > 0)>(L[e], er + ebc[e], nmod);
                 out[e] = accumulate ? out[e] + val : val;
             }
         }
@@ -1270,12 +1284,22 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         const bool v4 = cld % 4 == 0;
         const int64_t threads = v4 ? cm * ((cn + 3) / 4) : cm * cn;
         const unsigned blocks = (unsigned)((threads + 255) / 256);
-#define FMM_WCRT(V, RED) w_crt_kernel<V, RED><<<blocks, 256, 0, s>>>(child, cm, cn, cld, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
+#define FMM_WCRT(V, RED, NM) w_crt_kernel<V, RED, NM><<<blocks, 256, 0, s>>>(child, cm, cn, cld, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
+#define FMM_WCRT_N(V, RED)                                        \
+    switch (nmod) {                                               \
+        case 12: FMM_WCRT(V, RED, 12); break;                     \
+        case 13: FMM_WCRT(V, RED, 13); break;                     \
+        case 14: FMM_WCRT(V, RED, 14); break;                     \
+        case 15: FMM_WCRT(V, RED, 15); break;                     \
+        case 16: FMM_WCRT(V, RED, 16); break;                     \
+        default: FMM_WCRT(V, RED, 0); break;                      \
+    }
         if (v4) {
-            if (reduce) FMM_WCRT(4, true); else FMM_WCRT(4, false);
+            if (reduce) { FMM_WCRT_N(4, true) } else { FMM_WCRT_N(4, false) }
         } else {
-            if (reduce) FMM_WCRT(1, true); else FMM_WCRT(1, false);
+            if (reduce) { FMM_WCRT(1, true, 0); } else { FMM_WCRT(1, false, 0); }
         }
+#undef FMM_WCRT_N
 #undef FMM_WCRT
         if ((e = check()) != cudaSuccess) return e;
     }
