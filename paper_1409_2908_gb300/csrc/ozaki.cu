@@ -710,26 +710,52 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
 #pragma unroll
             for (int l = 0; l < NL; ++l) L[e][l] = 0;
         const int t0 = swp[qb], t1 = swp[qb + 1];
-#pragma unroll (NMOD ? NMOD : 4)
-        for (int q = 0; q < nmod; ++q) {
-            int acc[V];
+        if (NMOD > 0 && V == 4) {
+            // all moduli of a term loaded together, then combined
+            constexpr int NQ = NMOD > 0 ? NMOD : 1;
+            int acc[NQ][4];
 #pragma unroll
-            for (int e = 0; e < V; ++e) acc[e] = 0;
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q][e] = 0;
             for (int t = t0; t < t1; ++t) {
                 const int2 wt = swt[t];
-                const int8_t *z = zrow + ((int64_t)wt.x * nmod + q) * plane;
-                if (V == 4) {
-                    const unsigned raw = *reinterpret_cast<const unsigned *>(z);
+                const int8_t *z = zrow + (int64_t)wt.x * NQ * plane;
+                unsigned raw[NQ];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[e] += wt.y * (int)(int8_t)(raw >> (8 * e));
-                } else {
-                    acc[0] += wt.y * (int)z[0];
-                }
+                for (int q = 0; q < NQ; ++q) raw[q] = *reinterpret_cast<const unsigned *>(z + q * plane);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[q][e] += wt.y * (int)(int8_t)(raw[q] >> (8 * e));
             }
-            // the limb sums take any representative: the raw combination when it
-            // is small enough for them to stay below 2^30 (host-checked bound)
 #pragma unroll
-            for (int e = 0; e < V; ++e) crt_add(L[e], REDUCE ? bal_small(acc[e], q) : acc[e], q, nmod);
+            for (int q = 0; q < NQ; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    crt_add(L[e], REDUCE ? bal_small(acc[q][e], q) : acc[q][e], q, NQ);
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < nmod; ++q) {
+                int acc[V];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = 0;
+                for (int t = t0; t < t1; ++t) {
+                    const int2 wt = swt[t];
+                    const int8_t *z = zrow + ((int64_t)wt.x * nmod + q) * plane;
+                    if (V == 4) {
+                        const unsigned raw = *reinterpret_cast<const unsigned *>(z);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] += wt.y * (int)(int8_t)(raw >> (8 * e));
+                    } else {
+                        acc[0] += wt.y * (int)z[0];
+                    }
+                }
+                // the limb sums take any representative: the raw combination when it
+                // is small enough for them to stay below 2^30 (host-checked bound)
+#pragma unroll
+                for (int e = 0; e < V; ++e) crt_add(L[e], REDUCE ? bal_small(acc[e], q) : acc[e], q, nmod);
+            }
         }
         const int64_t row = (int64_t)a * rows + i;
         const int er = ea[row];
