@@ -75,6 +75,26 @@ def _mat(t, name):
     return ctypes.c_void_p(t.data_ptr()), max(t.stride(0), t.shape[1]), t.shape[0], t.shape[1]
 
 
+def algorithm_factors(name):
+    """(M, K, N, U, V, W) of a shipped algorithm file: U is MK x R, V is KN x R,
+    W is MN x R (rows in row-order vec of A, B, C; Section 2.2.2).  Entries
+    may be written as fractions a/b."""
+    import numpy as np
+    from fractions import Fraction
+    with open(algorithm_path(name)) as fh:
+        toks = [ln.split("#", 1)[0].split() for ln in fh]
+    toks = [t for t in toks if t]
+    M, K, N, R = (int(x) for x in toks[0])
+    mats, cur = {}, None
+    for t in toks[1:]:
+        if len(t) == 1 and t[0] in ("U", "V", "W"):
+            cur = mats.setdefault(t[0], [])
+        else:
+            cur.append([float(Fraction(x)) for x in t])
+    U, V, W = (np.array(mats[k], dtype=np.float64).reshape(-1, R) for k in ("U", "V", "W"))
+    return M, K, N, U, V, W
+
+
 class Plan:
     """A fast-multiplication plan: base case [[U,V,W]] unrolled over `levels`
     recursive steps (fmm_plan_create / fmm_plan_load)."""

@@ -29,7 +29,10 @@ FP64_TFLOPS = 1.22
 TC_TFLOPS = 1850.0                   # residue GEMM (tcgen05, bf16 residues)
 SPLIT_GBS = 3900.0                   # fused scaling + residues + first level
 LEVEL_GBS = 2200.0                   # later levels of S/T and W on int8 residues
-CRT_PS_PER_ELEM_MOD = 1.9            # top W level fused with the CRT
+CRT_PS_PER_ELEM_MOD = 0.98           # CRT per output element and modulus (L = 0)
+W_TERM_FACTOR = 0.1                  # extra CRT cost per additional W term of an output block
+LAUNCH_US = 4.0                      # per kernel launch (6 launches for the emulated path)
+NUM_SMS = 152
 HBM_GBS = 6700.0
 
 
@@ -77,12 +80,17 @@ def moduli_for(tol, k):
     return None
 
 
-def classical_efficiency(m, n, tile=128):
-    """Fraction of the DFMA ceiling a leaf of m x n reaches: tile fill (the
-    classical curve is flat above one tile on this GPU; below it the padded
-    tile wastes work)."""
-    fill = (m * n) / (math.ceil(m / tile) * tile * math.ceil(n / tile) * tile)
-    return max(fill, 0.05)
+def classical_efficiency(m, n, tile=128, tile_n=None, planes=1):
+    """Fraction of the peak a grouped launch of `planes` products of m x n
+    reaches: tile fill (the classical curve is flat above one tile on this
+    GPU; below it the padded tile wastes work) times wave quantisation over
+    the SMs."""
+    tile_n = tile_n or tile
+    tm, tn = math.ceil(m / tile), math.ceil(n / tile_n)
+    fill = (m * n) / (tm * tile * tn * tile_n)
+    tiles = tm * tn * planes
+    waves = tiles / (math.ceil(tiles / NUM_SMS) * NUM_SMS)
+    return max(fill * waves, 0.02)
 
 
 class Autotuner:
@@ -146,7 +154,8 @@ class Autotuner:
             flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
         else:
             kpad = -(-kL // 64) * 64
-            t = 2.0 * leaves * nmod * mL * kpad * nL / (TC_TFLOPS * 1e12 * classical_efficiency(mL, nL, 256))
+            t = 2.0 * leaves * nmod * mL * kpad * nL / (
+                TC_TFLOPS * 1e12 * classical_efficiency(mL, nL, 128, 256 if nL >= 256 else 128, leaves * nmod))
             # exponents, then the fused first level: FP64 in, R/(MK) residue
             # planes out per operand element (bfloat16 when it is the last level)
             grow_a = R / (M * K) if L else 1.0
@@ -159,10 +168,21 @@ class Autotuner:
                 ml, kl, nl = mp // M ** l, kp // K ** l, np_ // N ** l
                 t += R ** l * (ml * kl + kl * nl) * nmod * (2 + w) / (LEVEL_GBS * 1e9)
                 t += R ** (l - 1) * M * N * ml * nl * nmod * 3 / (LEVEL_GBS * 1e9)
-            t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12
+            terms = (self._w_terms(name) / (M * N)) if L else 1.0
+            t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12 * (1.0 + W_TERM_FACTOR * (terms - 1.0))
+            t += (6 + 3 * max(L - 1, 0)) * LAUNCH_US * 1e-6
             flags = fmm.FLAGS_DEFAULT
         t += fringe / (FP64_TFLOPS * 1e12)
         return Choice(name, L, flags, prec, nmod or 15, "auto", 1e3 * t)
+
+    def _w_terms(self, name):
+        """Nonzeros of the base case's W (terms of the top-level W combination)."""
+        if not hasattr(self, "_wnnz"):
+            self._wnnz = {}
+        if name not in self._wnnz:
+            from . import algorithm_factors
+            self._wnnz[name] = int((algorithm_factors(name)[5] != 0).sum())
+        return self._wnnz[name]
 
     # ----------------------------------------------------------- choice
     def choose(self, m, k, n):

@@ -46,8 +46,11 @@ def base_case(name):
     return M, K, N, R
 
 
-@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (7, 13, 5), (128, 128, 128), (130, 257, 66), (300, 17, 513)])
+@pytest.mark.parametrize("m,k,n", [(1, 1, 1), (7, 13, 5), (128, 128, 128), (130, 257, 66), (300, 17, 513),
+                                   (40, 300, 7), (2, 5000, 300), (300, 3, 400), (33, 65, 31), (1000, 900, 32),
+                                   (32, 700, 1000)])
 def test_classical_integer_exact(m, k, n):
+    # includes the thin shapes of the peeling fringes (<= 32 rows, columns or k)
     A, B = synth.operands(m, k, n, 1409, kind="integer")
     import torch
     C = fmm.classical_gemm(to_dev(A), to_dev(B))
@@ -226,3 +229,47 @@ def test_batched_one_grouped_launch(name, levels, shape):
     if m % 2 ** levels == 0 and n % 2 ** levels == 0 and k % 2 ** levels == 0 and name == "strassen_222_7":
         # no fringe: one memset per product, then a single leaf launch for all products
         assert fmm.last_launch_count() == 1
+
+
+FULL_SIZE = [
+    # (algorithm, levels, precision, moduli, (m, k, n)): the benchmark's workloads
+    ("strassen_222_7", 1, "ozaki_bf16", 12, (8192, 8192, 8192)),
+    ("fmm_424_26", 3, "fp64", None, (8192, 8192, 8192)),
+    ("fmm_333_23", 2, "fp64", None, (8192, 8192, 8192)),
+    ("fmm_424_26", 1, "fp64", None, (16384, 2048, 16384)),
+    ("strassen_222_7", 1, "ozaki_bf16", 12, (16384, 2048, 16384)),
+    ("fmm_423_20", 1, "fp64", None, (16384, 2048, 2048)),
+    ("fmm_323_15", 1, "ozaki_bf16", 12, (16384, 2048, 2048)),
+]
+
+
+@pytest.mark.parametrize("name,levels,precision,moduli,shape", FULL_SIZE)
+def test_full_size_workloads_sampled(name, levels, precision, moduli, shape):
+    # full-size products in the benchmark's launch configuration (level-by-
+    # level scheme for FP64 plans, residue space for the emulated variant),
+    # checked on sampled entries: within tolerance on uniform[-1,1], bit-exact
+    # on the integer copy
+    import torch
+    m, k, n = shape
+    flags = fmm.FLAG_LEVELWISE if precision == "fp64" else fmm.FLAGS_DEFAULT
+    p = fmm.Plan(name, levels=levels, flags=flags, precision=precision, moduli=moduli)
+    A, B = synth.operands(m, k, n, 1410)
+    Ad, Bd = to_dev(A), to_dev(B)
+    C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    wsz = p.workspace_size(m, k, n)
+    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+    fmm.gemm(p, Ad, Bd, C=C, workspace=ws)
+    torch.cuda.synchronize()
+    fmm.check_device_error()
+    rows, cols = synth.sample_indices(m, n, 512, 78)
+    ri, ci = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
+    e64, eld = oracle.gemm_entries(A, B, rows, cols)
+    got = C[ri, ci].cpu().numpy()
+    assert np.linalg.norm(got - eld) / np.linalg.norm(eld) <= TOL_F
+    Ai, Bi = np.rint(4 * A), np.rint(4 * B)
+    Ad.copy_(torch.from_numpy(Ai))
+    Bd.copy_(torch.from_numpy(Bi))
+    fmm.gemm(p, Ad, Bd, C=C, workspace=ws)
+    torch.cuda.synchronize()
+    ei64, _ = oracle.gemm_entries(Ai, Bi, rows, cols)
+    assert np.array_equal(C[ri, ci].cpu().numpy(), ei64)
