@@ -51,7 +51,7 @@ __constant__ unsigned c_magic[OZ_MAX_MOD];                // floor(2^32 / p)
 __constant__ unsigned c_r32[OZ_MAX_MOD];                  // 2^32 mod p
 __constant__ unsigned c_r21[OZ_MAX_MOD], c_r42[OZ_MAX_MOD];  // 2^21 and 2^42 mod p
 __constant__ float c_modf[OZ_MAX_MOD], c_invp[OZ_MAX_MOD];  // p and 1/p as floats
-__constant__ float c_k13[OZ_MAX_MOD][5];                   // 2^(13 i) mod p as floats
+__constant__ float c_klimb[2][OZ_MAX_MOD][5];              // 2^(13 i), 2^(14 i) mod p as floats
 constexpr int OZ_MAX_TERMS = 512, OZ_MAX_R = 64;           // limits of the staged term lists
 // CRT by a weighted sum: X = sum_q r_q c_q (mod P), c_q = (P/p_q) ((P/p_q)^-1 mod p_q)
 // mod P, held as eight 16-bit limbs so every limb sum fits an int32.
@@ -517,9 +517,12 @@ constexpr int OZ_IMAGIC = 0x4B400000;
 // dst + q qstep as bfloat16 (FINAL, the GEMM operand; |r| <= 129 is exact and
 // keeps the GEMM's 512-long FP32 chunks exact) or int8 (a later level's input;
 // representatives that wrap stay in the same class: only p = 256 reaches 128).
-template <bool FINAL>
+template <bool FINAL, int LB, int NLB>
 __device__ __forceinline__ void emit_child(const long long *sv, const int2 *sterm, int t0, int t1, int nmod,
                                            char *dst, int64_t qstep, int valid) {
+    // LB-bit limbs, NLB of them (|S'| < 2^(LB NLB), host-checked); the
+    // weighted limb sum stays below NLB 2^LB 2^8 <= 2^24, exact in float
+    static_assert(LB == 13 || LB == 14, "limb width");
     long long S[4] = {0, 0, 0, 0};
     for (int t = t0; t < t1; ++t) {
         const int2 tm = sterm[t];
@@ -527,14 +530,14 @@ __device__ __forceinline__ void emit_child(const long long *sv, const int2 *ster
 #pragma unroll
         for (int e = 0; e < 4; ++e) S[e] += (long long)tm.y * src[e * 256];
     }
-    float d[4][5];
+    float d[4][NLB];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const bool neg = S[e] < 0;
         const unsigned long long u = neg ? (unsigned long long)(-S[e]) : (unsigned long long)S[e];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const float f = __int_as_float(OZ_IMAGIC + (int)((u >> (13 * i)) & 0x1fffull)) - OZ_FMAGIC;
+        for (int i = 0; i < NLB; ++i) {
+            const float f = __int_as_float(OZ_IMAGIC + (int)((u >> (LB * i)) & ((1ull << LB) - 1))) - OZ_FMAGIC;
             d[e][i] = neg ? -f : f;
         }
     }
@@ -546,7 +549,7 @@ __device__ __forceinline__ void emit_child(const long long *sv, const int2 *ster
         for (int e = 0; e < 4; ++e) {
             float x = d[e][0];
 #pragma unroll
-            for (int i = 1; i < 5; ++i) x = fmaf(d[e][i], c_k13[q][i], x);
+            for (int i = 1; i < NLB; ++i) x = fmaf(d[e][i], c_klimb[LB - 13][q][i], x);
             const float tq = fmaf(x, c_invp[q], OZ_FMAGIC) - OZ_FMAGIC;
             r[e] = fmaf(-tq, c_modf[q], x);
         }
@@ -591,7 +594,13 @@ __device__ __forceinline__ void stage_terms(int R, int gridC, const int *ptr, co
 // A' = trunc(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
 // consecutive columns of out_ld (columns >= cols are the zero padding of the
 // GEMM operand).  256 threads; dynamic shared memory NB x 4 x 256 int64.
-template <int NB, bool FINAL>
+// Limb layouts of the combined integers: LC 0 = 3 x 14 bits, 1 = 4 x 14, 2 = 5 x 13.
+template <int LC> struct LimbCfg;
+template <> struct LimbCfg<0> { static constexpr int LB = 14, N = 3; };
+template <> struct LimbCfg<1> { static constexpr int LB = 14, N = 4; };
+template <> struct LimbCfg<2> { static constexpr int LB = 13, N = 5; };
+
+template <int NB, bool FINAL, int LC>
 __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t lda, const int *ea, int64_t rows,
                                                        int64_t cols, int gridK, int R, int nmod, const int *ptr,
                                                        const int *code, const int *icoef, void *out,
@@ -619,7 +628,7 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
     char *dst = (char *)out + (i * out_ld + j0) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
     for (int o = 0; o < R; ++o, dst += ostep)
-        emit_child<FINAL>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
+        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
 }
 
 // T side, transposed: B (peeled core, ld ldb) as a grid of K x N blocks of
@@ -628,7 +637,7 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
 // blocks through shared memory (dynamic: NB x 32 x 33 int64, then reused as
 // [NB][4][256]); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
 // ceil(ncols / 32)), 256 threads.
-template <int NB, bool FINAL>
+template <int NB, bool FINAL, int LC>
 __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_t ldb, const int *eb, int64_t krows,
                                                          int64_t ncols, int gridN, int R, int nmod, const int *ptr,
                                                          const int *code, const int *icoef, void *out,
@@ -670,7 +679,7 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
     char *dst = (char *)out + (n * out_ld + k) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
     for (int o = 0; o < R; ++o, dst += ostep)
-        emit_child<FINAL>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
+        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
 }
 
 // Top recursion level of the W combination fused with the CRT: output block
@@ -924,14 +933,15 @@ cudaError_t ensure_tables(int nmod) {
         }
         if ((e = cudaMemcpyToSymbol(c_modf, modf, sizeof(modf))) != cudaSuccess) return e;
         if ((e = cudaMemcpyToSymbol(c_invp, invp, sizeof(invp))) != cudaSuccess) return e;
-        float k13[OZ_MAX_MOD][5];
-        for (int i = 0; i < OZ_MAX_MOD; ++i)
-            for (int l = 0; l < 5; ++l) {
-                unsigned long long w = 1;
-                for (int t = 0; t < 13 * l; ++t) w = (w * 2) % (unsigned long long)mods[i];
-                k13[i][l] = (float)w;
-            }
-        if ((e = cudaMemcpyToSymbol(c_k13, k13, sizeof(k13))) != cudaSuccess) return e;
+        float klimb[2][OZ_MAX_MOD][5];
+        for (int wdt = 0; wdt < 2; ++wdt)
+            for (int i = 0; i < OZ_MAX_MOD; ++i)
+                for (int l = 0; l < 5; ++l) {
+                    unsigned long long w = 1;
+                    for (int t = 0; t < (13 + wdt) * l; ++t) w = (w * 2) % (unsigned long long)mods[i];
+                    klimb[wdt][i][l] = (float)w;
+                }
+        if ((e = cudaMemcpyToSymbol(c_klimb, klimb, sizeof(klimb))) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyToSymbol(c_crt16, crt16, sizeof(crt16))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_P16, P16, sizeof(P16))) != cudaSuccess) return e;
@@ -1096,14 +1106,14 @@ size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
     return res_layout(rp, mp, kp, np, nmod).total;
 }
 
-template <bool FINAL>
+template <bool FINAL, int LC>
 static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, const int *ea, int64_t rows,
                                           int64_t cols, int gridK, int R, int nmod, const int *ptr, const int *code,
                                           const int *icoef, void *out, int64_t out_ld, cudaStream_t s) {
     const int64_t threads = rows * ((out_ld + 3) / 4);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     const size_t smem = size_t(nb) * 4 * 256 * 8;
-#define FMM_SFR(NB) split_form_rows<NB, FINAL><<<blocks, 256, smem, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
+#define FMM_SFR(NB) split_form_rows<NB, FINAL, LC><<<blocks, 256, smem, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
     switch (nb) {
         case 1: FMM_SFR(1); break;
         case 4: FMM_SFR(4); break;
@@ -1116,14 +1126,14 @@ static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, 
     return cudaGetLastError();
 }
 
-template <bool FINAL>
+template <bool FINAL, int LC>
 static cudaError_t launch_split_form_cols_t(int nb, const double *B, int64_t ldb, const int *eb, int64_t krows,
                                             int64_t ncols, int gridN, int R, int nmod, const int *ptr,
                                             const int *code, const int *icoef, void *out, int64_t out_ld,
                                             cudaStream_t s) {
     const dim3 grid((unsigned)((out_ld + 31) / 32), (unsigned)((ncols + 31) / 32));
     const size_t smem = size_t(nb) * 32 * 33 * 8;   // >= nb * 4 * 256 * 8 (reused after the transpose)
-#define FMM_SFC(NB) split_form_cols_t<NB, FINAL><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
+#define FMM_SFC(NB) split_form_cols_t<NB, FINAL, LC><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
     switch (nb) {
         case 1: FMM_SFC(1); break;
         case 4: FMM_SFC(4); break;
@@ -1143,20 +1153,17 @@ static cudaError_t configure_split_form() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 64 || configured[dev]) return cudaSuccess;
-#define FMM_CFG(NB)                                                                                          \
-    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                  NB * 32 * 33 * 8)) != cudaSuccess)                                         \
-        return e;                                                                                            \
-    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                  NB * 32 * 33 * 8)) != cudaSuccess)                                         \
-        return e;                                                                                            \
-    if ((e = cudaFuncSetAttribute(split_form_rows<NB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                  NB * 4 * 256 * 8)) != cudaSuccess)                                         \
-        return e;                                                                                            \
-    if ((e = cudaFuncSetAttribute(split_form_rows<NB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                  NB * 4 * 256 * 8)) != cudaSuccess)                                         \
+#define FMM_CFG1(NB, F, LC)                                                                                  \
+    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, F, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                  NB * 32 * 33 * 8)) != cudaSuccess)                                           \
+        return e;                                                                                              \
+    if ((e = cudaFuncSetAttribute(split_form_rows<NB, F, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                  NB * 4 * 256 * 8)) != cudaSuccess)                                           \
         return e;
+#define FMM_CFG(NB) FMM_CFG1(NB, true, 0) FMM_CFG1(NB, false, 0) FMM_CFG1(NB, true, 1) FMM_CFG1(NB, false, 1) \
+                    FMM_CFG1(NB, true, 2) FMM_CFG1(NB, false, 2)
     FMM_CFG(1) FMM_CFG(4) FMM_CFG(6) FMM_CFG(8) FMM_CFG(9)
+#undef FMM_CFG1
 #undef FMM_CFG
     configured[dev] = true;
     return cudaSuccess;
@@ -1202,14 +1209,26 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         const int *up = rp.L ? rp.u_ptr : id_ptr, *uc = rp.L ? rp.u_code : id_code, *ui = rp.L ? rp.u_icoef : id_coef;
         const int *vp = rp.L ? rp.v_ptr : id_ptr, *vc = rp.L ? rp.v_code : id_code, *vi = rp.L ? rp.v_icoef : id_coef;
         if (fused) {
-            e = last ? launch_split_form_rows<true>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s)
-                     : launch_split_form_rows<false>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s);
-            ++*launches;
-            if (e != cudaSuccess) return e;
-            e = last ? launch_split_form_cols_t<true>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s)
-                     : launch_split_form_cols_t<false>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s);
-            ++*launches;
-            if (e != cudaSuccess) return e;
+            // limbs of |S'| < 2^(beta + ceil(log2 max sum|c|)): 3 x 14, 4 x 14 or 5 x 13 bits
+            const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
+            int bits = beta;
+            while ((1 << (bits - beta)) < cmax) ++bits;
+            const int lc = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
+#define FMM_SPLITS(F, LC)                                                                                               \
+    do {                                                                                                                \
+        e = launch_split_form_rows<F, LC>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s);   \
+        ++*launches;                                                                                                    \
+        if (e != cudaSuccess) return e;                                                                                 \
+        e = launch_split_form_cols_t<F, LC>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s); \
+        ++*launches;                                                                                                    \
+        if (e != cudaSuccess) return e;                                                                                 \
+    } while (0)
+            if (last) {
+                if (lc == 0) FMM_SPLITS(true, 0); else if (lc == 1) FMM_SPLITS(true, 1); else FMM_SPLITS(true, 2);
+            } else {
+                if (lc == 0) FMM_SPLITS(false, 0); else if (lc == 1) FMM_SPLITS(false, 1); else FMM_SPLITS(false, 2);
+            }
+#undef FMM_SPLITS
         }
     }
     auto form = [&](const int8_t *par, int64_t parents, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
