@@ -682,6 +682,109 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
         emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
 }
 
+// ---------------------------------------------------------------------
+// Streaming levels (levels >= 2 of S and T, int8 residues in HBM): each
+// parent element is read once and every child that uses it is written from
+// the same thread (Section 3.2's streaming additions, one level at a time).
+
+// 8 signed bytes of w (little-endian), e-th.
+__device__ __forceinline__ int sbyte8(uint2 w, int e) {
+    return (int)(int8_t)((e < 4 ? w.x : w.y) >> (8 * (e & 3)));
+}
+
+// Nearest representative modulo moduli[q] of a small integer |x| < 2^22.
+__device__ __forceinline__ float near_mod_i(int x, int q) {
+    const float f = __int_as_float(OZ_IMAGIC + x) - OZ_FMAGIC;
+    const float t = fmaf(f, c_invp[q], OZ_FMAGIC) - OZ_FMAGIC;
+    return fmaf(-t, c_modf[q], f);
+}
+
+// One level of S (or T^T): parent planes P[s][q] (prow x pcol int8) as a grid
+// of gridR x gridC blocks of rows x cols; child o = s R + r, modulus q:
+// sum_t c_t block(t) mod p, written to out[(o nmod + q)][rows][out_ld] as
+// bfloat16 (FINAL) or int8.  Thread: (s, q, row i, 8 columns); 256 threads.
+template <int NB, bool FINAL, bool ALIGNED>
+__global__ void __launch_bounds__(256) res_stream_form(const int8_t *P, int64_t prow, int64_t pcol, int64_t rows,
+                                                       int64_t cols, int gridC, int R, int nmod, int64_t parents,
+                                                       const int *ptr, const int *code, const int *icoef, void *out,
+                                                       int64_t out_ld) {
+    __shared__ uint2 sres[NB * 256];
+    __shared__ int2 sterm[OZ_MAX_TERMS];
+    __shared__ int sptr[OZ_MAX_R + 1];
+    stage_terms(R, gridC, ptr, code, icoef, sterm, sptr);
+    __syncthreads();
+    const int64_t groups = (out_ld + 7) / 8;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= parents * nmod * rows * groups) return;
+    const int64_t jg = pos % groups;
+    int64_t rest = pos / groups;
+    const int64_t i = rest % rows;
+    rest /= rows;
+    const int q = (int)(rest % nmod);
+    const int64_t sp = rest / nmod;
+    const int64_t j0 = jg * 8;
+    const int8_t *base = P + (sp * nmod + q) * prow * pcol;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const int8_t *src = base + ((int64_t)(b / gridC) * rows + i) * pcol + (int64_t)(b % gridC) * cols + j0;
+        uint2 w;
+        if (ALIGNED && j0 + 8 <= cols) {
+            w = *reinterpret_cast<const uint2 *>(src);
+        } else {
+            unsigned lo = 0, hi = 0;
+            for (int e = 0; e < 8; ++e) {
+                const unsigned v = (j0 + e < cols) ? (unsigned)(uint8_t)src[e] : 0u;
+                if (e < 4) lo |= v << (8 * e); else hi |= v << (8 * (e - 4));
+            }
+            w = make_uint2(lo, hi);
+        }
+        sres[b * 256 + threadIdx.x] = w;
+    }
+    const int valid = (int)min((int64_t)8, out_ld - j0);
+    constexpr int ES = FINAL ? 2 : 1;
+    char *dst = (char *)out + ((((sp * R) * nmod + q) * rows + i) * out_ld + j0) * ES;
+    const int64_t ostep = (int64_t)nmod * rows * out_ld * ES;
+    for (int r = 0; r < R; ++r, dst += ostep) {
+        int acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const int t1 = sptr[r + 1];
+        for (int t = sptr[r]; t < t1; ++t) {
+            const int2 tm = sterm[t];
+            const uint2 w = sres[tm.x * 256 + threadIdx.x];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) acc[e] += tm.y * sbyte8(w, e);
+        }
+        float rr[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) rr[e] = near_mod_i(acc[e], q);
+        if (FINAL) {
+            uint4 pk;
+            pk.x = __byte_perm(__float_as_uint(rr[0]), __float_as_uint(rr[1]), 0x7632);
+            pk.y = __byte_perm(__float_as_uint(rr[2]), __float_as_uint(rr[3]), 0x7632);
+            pk.z = __byte_perm(__float_as_uint(rr[4]), __float_as_uint(rr[5]), 0x7632);
+            pk.w = __byte_perm(__float_as_uint(rr[6]), __float_as_uint(rr[7]), 0x7632);
+            if (valid == 8) {
+                *reinterpret_cast<uint4 *>(dst) = pk;
+            } else {
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&pk);
+                for (int e = 0; e < valid; ++e) reinterpret_cast<__nv_bfloat16 *>(dst)[e] = h[e];
+            }
+        } else {
+            unsigned lo = 0, hi = 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const unsigned v = (unsigned)(__float_as_int(rr[e] + OZ_FMAGIC) - OZ_IMAGIC) & 0xffu;
+                if (e < 4) lo |= v << (8 * e); else hi |= v << (8 * (e - 4));
+            }
+            if (ALIGNED && valid == 8) {
+                *reinterpret_cast<uint2 *>(dst) = make_uint2(lo, hi);
+            } else {
+                for (int e = 0; e < valid; ++e)
+                    reinterpret_cast<int8_t *>(dst)[e] = (int8_t)((e < 4 ? lo : hi) >> (8 * (e & 3)));
+            }
+        }
+    }
+}
+
 // Top recursion level of the W combination fused with the CRT: output block
 // qb = (a, c) of the M x N grid, modulus q: Z_qb = sum_t w_t child(r_t) mod p;
 // C'_qb from its residues, times 2^-(ea_i + eb_j), stored (or added) in C.
@@ -1234,6 +1337,30 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     auto form = [&](const int8_t *par, int64_t parents, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
                     const int *uptr, const int *ucode, const int *ucoef, void *out, bool last,
                     int64_t out_ld) -> cudaError_t {
+        const int nbl = int((prr / rows) * (pcc / cols));
+        if (nbl == 4 || nbl == 6 || nbl == 8 || nbl == 9) {
+            // streaming: every parent element read once
+            const bool al = (cols % 8 == 0) && (pcc % 8 == 0) && (out_ld % 8 == 0);
+            const int gC = int(pcc / cols);
+            const int64_t total = parents * nmod * rows * ((out_ld + 7) / 8);
+            const unsigned blocks = (unsigned)((total + 255) / 256);
+#define FMM_RSF(NB, F, AL) res_stream_form<NB, F, AL><<<blocks, 256, 0, s>>>(par, prr, pcc, rows, cols, gC, rp.R, nmod, parents, uptr, ucode, ucoef, out, out_ld)
+#define FMM_RSF_NB(F, AL)                                                             \
+    switch (nbl) {                                                                    \
+        case 4: FMM_RSF(4, F, AL); break;                                             \
+        case 6: FMM_RSF(6, F, AL); break;                                             \
+        case 8: FMM_RSF(8, F, AL); break;                                             \
+        default: FMM_RSF(9, F, AL); break;                                            \
+    }
+            if (last) {
+                if (al) { FMM_RSF_NB(true, true) } else { FMM_RSF_NB(true, false) }
+            } else {
+                if (al) { FMM_RSF_NB(false, true) } else { FMM_RSF_NB(false, false) }
+            }
+#undef FMM_RSF_NB
+#undef FMM_RSF
+            return check();
+        }
         const int64_t outs = parents * rp.R;
         const bool vec = (cols % 8 == 0) && (pcc % 8 == 0) && (out_ld % 8 == 0);
         const unsigned threads = 128;

@@ -98,6 +98,7 @@ class Server:
         self._graphs = OrderedDict()      # (plan key, shape, slot) -> _Graph
         self._graph_bytes = 0
         self._seen = {}
+        self._slot_ws = [None] * slots     # per-slot workspace, grown on demand
         self.used = 0
         self.stats = Stats()
 
@@ -151,6 +152,20 @@ class Server:
         self.stats.graphs_captured += 1
         return g
 
+    def _workspace(self, slot, nbytes):
+        """The slot's workspace, grown to `nbytes` if needed.  It is allocated
+        on the slot's stream, so work queued there uses it in order and a
+        replaced buffer is only reused by later work on that stream."""
+        import torch
+        if not nbytes:
+            return None
+        ws = self._slot_ws[slot]
+        if ws is None or ws.numel() < nbytes:
+            with torch.cuda.stream(self.streams[slot]):
+                ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            self._slot_ws[slot] = ws
+        return ws
+
     def _launch(self, group_reqs, plan, slot):
         import torch
         stream = self.streams[slot]
@@ -171,9 +186,8 @@ class Server:
                     r.C.copy_(g.C, non_blocking=True)
                     self.stats.graph_replays += 1
                 else:
-                    wsz = plan.workspace_size(m, k, n)
-                    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
-                    fmm.gemm(plan, r.A, r.B, C=r.C, workspace=ws, stream=stream)
+                    fmm.gemm(plan, r.A, r.B, C=r.C, workspace=self._workspace(slot, plan.workspace_size(m, k, n)),
+                             stream=stream)
                 nbytes += self._bytes(plan, m, k, n)
             ev = torch.cuda.Event()
             ev.record(stream)
@@ -183,13 +197,18 @@ class Server:
     def run(self, requests, max_group=8):
         """Serve `requests` (sorted by arrival); returns the stats summary."""
         pending = deque(sorted(requests, key=lambda r: r.arrival))
-        queue = deque()
+        queue = deque()                 # admission order (entries already admitted are skipped)
+        by_shape = {}                   # shape -> deque of waiting requests, in arrival order
+        waiting = 0
         inflight = []
         t0 = time.perf_counter()
-        while pending or queue or inflight:
+        while pending or waiting or inflight:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
-                queue.append(pending.popleft())
+                r = pending.popleft()
+                queue.append(r)
+                by_shape.setdefault(r.shape, deque()).append(r)
+                waiting += 1
             # retire finished groups
             still = []
             for g in inflight:
@@ -206,27 +225,30 @@ class Server:
                     still.append(g)
             inflight = still
             # admit and group by (plan, shape) while memory and slots allow
-            while queue and self.free_slots:
+            while waiting and self.free_slots:
+                while queue[0].t_admit >= 0:
+                    queue.popleft()
                 head = queue[0]
                 plan = self._plan(*head.shape)
                 need = self._bytes(plan, *head.shape)
                 if self.used + need > self.budget and inflight:
                     break
-                group = [queue.popleft()]
-                for r in list(queue):
-                    if len(group) >= max_group:
-                        break
-                    if r.shape == head.shape and self.used + need * (len(group) + 1) <= self.budget:
-                        group.append(r)
-                        queue.remove(r)
+                same = by_shape[head.shape]
+                group = []
+                while same and len(group) < max_group and (not group or self.used + need * (len(group) + 1)
+                                                           <= self.budget):
+                    group.append(same.popleft())
+                if not same:
+                    del by_shape[head.shape]
                 for r in group:
                     r.t_admit = now
+                waiting -= len(group)
                 slot = self.free_slots.popleft()
                 g = self._launch(group, plan, slot)
                 self.used += g.nbytes
                 inflight.append(g)
                 self.stats.max_inflight = max(self.stats.max_inflight, len(inflight))
-            if not queue and not inflight and pending:
+            if not waiting and not inflight and pending:
                 time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.001)))
         self.stats.wall_s = time.perf_counter() - t0
         return self.stats.summary()
