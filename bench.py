@@ -542,6 +542,7 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "rel_err_F": err, "rel_err_note": "e_F over the cpu_baseline's sampled rows vs the FP64 oracle",
             "classical": ({"value": ws * flops / ms_c / 1e9, "ms_per_step": ms_c, "rel_err_F": err_c,
+                           "frac_of_fp64_peak": flops / ms_c / 1e9 / FP64_PEAK_TFLOPS,
                            "what": "the library's classical FP64 GEMM (DFMA)"} if ms_c else None),
             "classical_emulated": ({"value": classical_same[0]["tflops"], "ms": classical_same[0]["ms"],
                                     "rel_err_F": classical_same[0]["rel_err_F"], "plan": classical_same[0]["plan"],

@@ -75,13 +75,6 @@ __device__ __forceinline__ unsigned mod_u32(unsigned x, int q) {
 
 using namespace tc;
 
-// Balanced residue of x (|x| < 2^31) modulo p.
-__device__ __forceinline__ int bal_mod(int x, int p) {
-    int r = x % p;
-    if (r < 0) r += p;
-    return r >= (p + 1) / 2 ? r - p : r;
-}
-
 // Balanced residue modulo moduli[q] of |x| < 2^20 (combinations of a few
 // residues): shift positive by p * 2^13, then one Barrett reduction.
 __device__ __forceinline__ int bal_mod_q(int x, int q) {
@@ -247,19 +240,33 @@ __device__ __forceinline__ double crt_finish(const int (&L)[NL], int e, int n) {
     const float sm = sf + 12582912.0f;
     const int t = __float_as_int(sm) - 0x4B400000;
     const float xf = sf - (sm - 12582912.0f);
-    int x[8];
+    // X = S - t P in NL limbs; carries leave limbs 0..NL-2 in [0, 2^16) and
+    // the sign in the top limb, which then sign-extends into (hi, lo)
+    int x[NL];
 #pragma unroll
-    for (int l = 0; l < 8; ++l) x[l] = l < NL ? L[l] - t * c_P16[n][l] : 0;
+    for (int l = 0; l < NL; ++l) x[l] = L[l] - t * c_P16[n][l];
 #pragma unroll
-    for (int l = 0; l < 7; ++l) {
+    for (int l = 0; l < NL - 1; ++l) {
         const int carry = x[l] >> 16;
         x[l] -= carry * 65536;
         x[l + 1] += carry;
     }
-    unsigned long long lo = (unsigned long long)(unsigned)x[0] | ((unsigned long long)(unsigned)x[1] << 16) |
-                            ((unsigned long long)(unsigned)x[2] << 32) | ((unsigned long long)(unsigned)x[3] << 48);
-    long long hi = (long long)(((unsigned long long)(long long)x[7] << 48) | ((unsigned long long)(unsigned)x[6] << 32) |
-                               ((unsigned long long)(unsigned)x[5] << 16) | (unsigned long long)(unsigned)x[4]);
+    unsigned long long lo = 0ull;
+    long long hi;
+    if constexpr (NL <= 4) {
+#pragma unroll
+        for (int l = 0; l < NL - 1; ++l) lo |= (unsigned long long)(unsigned)x[l] << (16 * l);
+        const long long top = (long long)x[NL - 1] * (1ll << (16 * (NL - 1)));
+        lo = (unsigned long long)((long long)lo + top);
+        hi = (long long)lo >> 63;
+    } else {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) lo |= (unsigned long long)(unsigned)x[l] << (16 * l);
+        unsigned long long h = 0ull;
+#pragma unroll
+        for (int l = 4; l < NL - 1; ++l) h |= (unsigned long long)(unsigned)x[l] << (16 * (l - 4));
+        hi = (long long)h + (long long)x[NL - 1] * (1ll << (16 * (NL - 5)));
+    }
     if (fabsf(xf) > 0.49f) {
         // near +-P/2 the estimate may have picked the neighbouring multiple of P
         __int128 X = (__int128)(((unsigned __int128)(unsigned long long)hi << 64) | lo);
