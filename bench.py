@@ -299,7 +299,7 @@ def run_serving(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
     ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS) + ["serving"])
