@@ -11,6 +11,23 @@
 // drain roles walk the same tile sequence, so stage and TMEM-buffer phases
 // continue across tiles and the tensor core never waits for a tile's final
 // reduction (four TMEM buffers of slack).
+// Tile t of the persistent sequence -> (plane z, tile row tm, tile column tn).
+// Within a plane, tiles go in groups of OZ_GROUP tile rows, column by column,
+// so the CTAs of one wave share a few A row panels and B column panels in L2
+// (a plane of 8192 x 8192 bf16 residues, 128 MB per operand, does not fit).
+constexpr int OZ_GROUP = 16;
+__device__ __forceinline__ void tile_coords(int64_t tile, int64_t per_plane, int tiles_m, int tiles_n, int &z,
+                                            int &tm, int &tn) {
+    z = int(tile / per_plane);
+    const int rem = int(tile % per_plane);
+    const int g = rem / (OZ_GROUP * tiles_n);
+    const int tm0 = g * OZ_GROUP;
+    const int gsz = min(OZ_GROUP, tiles_m - tm0);
+    const int within = rem - g * OZ_GROUP * tiles_n;
+    tn = within / gsz;
+    tm = tm0 + within % gsz;
+}
+
 template <int BN>
 struct OzCfg;
 template <>
@@ -65,9 +82,8 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             int64_t g = 0;   // global k-block counter: stage and phase
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
-                const int z = int(tile / per_plane);
-                const int rem = int(tile % per_plane);
-                const int tm = rem / tiles_n, tn = rem % tiles_n;
+                int z, tm, tn;
+                tile_coords(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = int(g % OZ_STAGES);
                     if (g >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((g / OZ_STAGES) - 1) & 1))) {
@@ -122,9 +138,8 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         bool ok = true;
         int64_t cg = 0;
         for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
-            const int z = int(tile / per_plane);
-            const int rem = int(tile % per_plane);
-            const int tm = rem / tiles_n, tn = rem % tiles_n;
+            int z, tm, tn;
+            tile_coords(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
             const int q = z % nmod;
             const int p = c_mod[q];
             int acc[128];
