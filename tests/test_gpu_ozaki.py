@@ -82,3 +82,27 @@ def test_fast_emulated_uniform(name, levels, mode):
     A, B = synth.operands(300, 700, 290, 45)
     e = norms.rel_frobenius(run(p, A, B), oracle.gemm(A, B))
     assert e <= 1e-13
+
+
+@pytest.mark.parametrize("nmod", [12, 13, 14, 16, 9])
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 1), ("fmm_424_26", 1), ("strassen_222_7", 2)])
+def test_fast_emulated_every_moduli_count(name, levels, nmod):
+    # each moduli count has its own compiled W + CRT instance and its own limb
+    # layout in the split; all must give the oracle's emulation bit for bit
+    M, K, N = {"strassen_222_7": (2, 2, 2), "fmm_424_26": (4, 2, 4)}[name]
+    m, k, n = M ** levels * 40, K ** levels * 200, N ** levels * 40
+    A, B = synth.operands(m, k, n, 47)
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=nmod)
+    assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, nmod))
+    Ai, Bi = synth.operands(m + 3, k + 1, n + 2, 48, kind="integer")
+    assert np.array_equal(run(p, Ai, Bi), oracle.gemm(Ai, Bi))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 1), ("fmm_333_23", 1)])
+def test_fast_emulated_loguniform(name, levels):
+    # magnitudes over eight decades: the per-row and per-column exponents keep
+    # the scaled integers full; the result is the oracle's emulation exactly
+    M, K, N = {"strassen_222_7": (2, 2, 2), "fmm_333_23": (3, 3, 3)}[name]
+    A, B = synth.operands(M * 90, K * 200, N * 80, 49, kind="loguniform")
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=16)
+    assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, 16))
