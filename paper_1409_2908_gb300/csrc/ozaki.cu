@@ -188,7 +188,7 @@ __device__ __forceinline__ double round_scale(long long hi_s, unsigned long long
         const int lz = __clzll((long long)uh);
         nb = 128 - lz;
         top = lz ? (uh << lz) | (ul >> (64 - lz)) : uh;
-        sticky = lz ? (ul << (64 - lz)) != 0ull : ul != 0ull;   // the low lz bits of ul
+        sticky = lz ? (ul << lz) != 0ull : ul != 0ull;   // the bits of ul below the window: its low 64 - lz
     } else {
         const int lz = __clzll((long long)ul);
         nb = 64 - lz;

@@ -5,9 +5,10 @@
 // products are widened back to FP64 for the W combination.  Expected
 // relative error ~ 2^-11 per operand; stated per result by the benchmark.
 //
-// Same pipeline as the emulated-FP64 residue GEMM: persistent CTAs, TMA
-// (128-byte swizzle) into a 6-stage mbarrier ring, one load thread, one MMA
-// thread, four drain warps; two TMEM accumulators let a tile's drain overlap
+// Same pipeline as the emulated-FP64 residue GEMM: persistent CTAs over
+// 128 x 256 tiles (128 x 128 for narrow products) in groups of 16 tile rows,
+// TMA (128-byte swizzle) into an mbarrier ring, one load thread, one MMA
+// thread, eight drain warps; two TMEM accumulators let a tile's drain overlap
 // the next tile's MMAs.  Every wait is bounded.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -27,34 +28,63 @@ namespace {
 
 using namespace tc;
 
-constexpr int TB_M = 128, TB_N = 128, TB_K = 32, TB_STAGES = 6;   // TB_K fp32 = 128 bytes
-constexpr int TB_A = TB_M * TB_K * 4, TB_B = TB_N * TB_K * 4, TB_STAGE = TB_A + TB_B;
-constexpr int TB_TBUF = 2;
-constexpr int TB_THREADS = 192;
-constexpr int TB_SMEM = TB_STAGES * TB_STAGE + 1024 + 256;
+constexpr int TB_M = 128, TB_K = 32;   // TB_K fp32 = 128 bytes: one swizzled row
+constexpr int TB_A = TB_M * TB_K * 4;
 
-__global__ void __launch_bounds__(TB_THREADS, 1)
+// BN = 256: 8 drain warps (two column halves), 4 stages of 48 KB; BN = 128:
+// 4 drain warps, 6 stages of 32 KB.  Two TMEM accumulators of BN columns.
+template <int BN>
+struct TfCfg;
+template <>
+struct TfCfg<256> { static constexpr int DW = 8, STAGES = 4; };
+template <>
+struct TfCfg<128> { static constexpr int DW = 4, STAGES = 6; };
+constexpr int TB_TBUF = 2;
+template <int BN>
+constexpr int tf_threads() { return (TfCfg<BN>::DW + 2) * 32; }
+template <int BN>
+constexpr int tf_smem() { return TfCfg<BN>::STAGES * (TB_A + BN * TB_K * 4) + 1024 + 256; }
+
+// Tile t of the persistent sequence -> (plane, tile row, tile column), in
+// groups of 16 tile rows taken column by column (panels shared in L2).
+__device__ __forceinline__ void tf_tile(int64_t tile, int64_t per_plane, int tiles_m, int tiles_n, int &z, int &tm,
+                                        int &tn) {
+    constexpr int G = 16;
+    z = int(tile / per_plane);
+    const int rem = int(tile % per_plane);
+    const int g = rem / (G * tiles_n);
+    const int tm0 = g * G;
+    const int gsz = min(G, tiles_m - tm0);
+    const int within = rem - g * G * tiles_n;
+    tn = within / gsz;
+    tm = tm0 + within % gsz;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(tf_threads<BN>(), 1)
 tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           double *Out, int64_t m, int64_t n, int kblocks, int tiles_m, int tiles_n,
           int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err) {
+    constexpr int DW = TfCfg<BN>::DW, STAGES = TfCfg<BN>::STAGES;
+    constexpr int TB_B = BN * TB_K * 4, STAGE = TB_A + TB_B;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *full = (uint64_t *)(smem + TB_STAGES * TB_STAGE);
-    uint64_t *empty = full + TB_STAGES;
-    uint64_t *tfull = empty + TB_STAGES;
+    uint64_t *full = (uint64_t *)(smem + STAGES * STAGE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + TB_TBUF;
     uint32_t *tmem_slot = (uint32_t *)(tempty + TB_TBUF);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t per_plane = (int64_t)tiles_m * tiles_n;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TB_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int b = 0; b < TB_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], 128); }
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int b = 0; b < TB_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], DW * 32); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"(su32(tmem_slot)), "r"(TB_TBUF * TB_N) : "memory");
+                     ::"r"(su32(tmem_slot)), "r"(TB_TBUF * BN) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -62,33 +92,32 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
+    if (warp == DW) {
         if (lane == 0) {
             int64_t g = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
-                const int z = int(tile / per_plane);
-                const int rem = int(tile % per_plane);
-                const int tm = rem / tiles_n, tn = rem % tiles_n;
+                int z, tm, tn;
+                tf_tile(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
-                    const int s = int(g % TB_STAGES);
-                    if (g >= TB_STAGES && !mbar_wait(&empty[s], uint32_t(((g / TB_STAGES) - 1) & 1))) {
+                    const int s = int(g % STAGES);
+                    if (g >= STAGES && !mbar_wait(&empty[s], uint32_t(((g / STAGES) - 1) & 1))) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
                     }
-                    unsigned char *sa = smem + s * TB_STAGE, *sb = sa + TB_A;
-                    mbar_expect_tx(&full[s], TB_STAGE);
+                    unsigned char *sa = smem + s * STAGE, *sb = sa + TB_A;
+                    mbar_expect_tx(&full[s], STAGE);
                     tma_load_3d(sa, &tmA, kb * TB_K, tm * TB_M, z, &full[s]);
-                    tma_load_3d(sb, &tmB, kb * TB_K, tn * TB_N, z, &full[s]);
+                    tma_load_3d(sb, &tmB, kb * TB_K, tn * BN, z, &full[s]);
                 }
             }
         }
-    } else if (warp == 5) {
+    } else if (warp == DW + 1) {
         if (lane == 0) {
             // FP32 accumulator, TF32 A and B, both K-major
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
-                                   ((uint32_t)(TB_N >> 3) << 17) | ((uint32_t)(TB_M >> 4) << 24);
+                                   ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TB_M >> 4) << 24);
             bool ok = true;
             int64_t g = 0, it = 0;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
@@ -98,12 +127,12 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t acc = tmem + (uint32_t)(b * TB_N);
+                const uint32_t acc = tmem + (uint32_t)(b * BN);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
-                    const int s = int(g % TB_STAGES);
-                    if (!mbar_wait(&full[s], uint32_t((g / TB_STAGES) & 1))) { ok = false; break; }
+                    const int s = int(g % STAGES);
+                    if (!mbar_wait(&full[s], uint32_t((g / STAGES) & 1))) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = su32(smem + s * TB_STAGE), b0 = a0 + TB_A;
+                    const uint32_t a0 = su32(smem + s * STAGE), b0 = a0 + TB_A;
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)   // K = 8 tf32 (32 bytes) per MMA
                         mma_tf32(acc, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
@@ -115,33 +144,52 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             if (!ok) atomicExch(err, 1);
         }
     } else {
+        // drain warps: warp w reads TMEM lanes 32*(w%4)..+31 (rows of the tile)
+        // and the 128-column slice w/4 of the accumulator
+        const int lg = warp % 4, ch = warp / 4;
         bool ok = true;
         int64_t it = 0;
         for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
-            const int z = int(tile / per_plane);
-            const int rem = int(tile % per_plane);
-            const int tm = rem / tiles_n, tn = rem % tiles_n;
+            int z, tm, tn;
+            tf_tile(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
             const int b = int(it % TB_TBUF);
             if (!mbar_wait(&tfull[b], uint32_t((it / TB_TBUF) & 1))) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * TB_N);
-            const int64_t row = (int64_t)tm * TB_M + warp * 32 + lane;
-            const int64_t cols = min((int64_t)TB_N, n - (int64_t)tn * TB_N);
-            double *out = Out + (int64_t)z * out_stride + row * ldo + (int64_t)tn * TB_N;
+            const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * 128);
+            const int64_t row = (int64_t)tm * TB_M + lg * 32 + lane;
+            const int64_t col0 = (int64_t)tn * BN + ch * 128;
+            const int64_t cols = min((int64_t)128, n - col0);
+            double *out = Out + (int64_t)z * out_stride + row * ldo + col0;
+            const bool pairs = ((((uintptr_t)out) & 15) == 0);
 #pragma unroll
-            for (int c0 = 0; c0 < TB_N; c0 += 16) {
+            for (int c0 = 0; c0 < 128; c0 += 16) {
                 uint32_t r[16];
                 asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
                                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
                              : "r"(base + (uint32_t)c0));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < m) {
+                if (row < m && c0 < cols) {
+                    if (pairs && c0 + 16 <= cols) {
+                        // 16 consecutive columns as eight 16-byte stores
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (c0 + j < cols) {
-                            const double v = (double)__uint_as_float(r[j]);
-                            out[c0 + j] = accumulate ? out[c0 + j] + v : v;
+                        for (int j = 0; j < 16; j += 2) {
+                            double2 v = make_double2((double)__uint_as_float(r[j]), (double)__uint_as_float(r[j + 1]));
+                            double2 *dst = reinterpret_cast<double2 *>(out + c0 + j);
+                            if (accumulate) {
+                                const double2 o = *dst;
+                                v.x += o.x;
+                                v.y += o.y;
+                            }
+                            *dst = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (c0 + j < cols) {
+                                const double v = (double)__uint_as_float(r[j]);
+                                out[c0 + j] = accumulate ? out[c0 + j] + v : v;
+                            }
                         }
                     }
                 }
@@ -154,7 +202,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TB_TBUF * TB_N) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TB_TBUF * BN) : "memory");
 }
 
 __device__ __forceinline__ float to_tf32(double x) {
@@ -201,7 +249,7 @@ typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, voi
 std::mutex g_tf_mu;
 EncodeFn g_tf_encode = nullptr;
 
-cudaError_t map3d_f32(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int64_t planes) {
+cudaError_t map3d_f32(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int64_t planes, int box_rows) {
     {
         std::lock_guard<std::mutex> g(g_tf_mu);
         if (!g_tf_encode) {
@@ -216,7 +264,7 @@ cudaError_t map3d_f32(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int
     }
     cuuint64_t gdim[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
     cuuint64_t gstr[2] = {(cuuint64_t)kpad * 4, (cuuint64_t)(kpad * rows * 4)};
-    cuuint32_t box[3] = {(cuuint32_t)TB_K, 128, 1};
+    cuuint32_t box[3] = {(cuuint32_t)TB_K, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = g_tf_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ptr, gdim, gstr, box, es,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -245,8 +293,11 @@ cudaError_t tf32_prepare() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 64 && !configured[dev]) {
-        if ((e = cudaFuncSetAttribute(tf32_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, TB_SMEM)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(tf32_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<256>())) != cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(tf32_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<128>())) != cudaSuccess)
             return e;
         configured[dev] = true;
     }
@@ -291,14 +342,20 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     CUtensorMap ta, tb;
-    if ((e = map3d_f32(&ta, fa, kpad, m, leaves)) != cudaSuccess) return e;
-    if ((e = map3d_f32(&tb, fb, kpad, n, leaves)) != cudaSuccess) return e;
-    const int64_t tm = (m + TB_M - 1) / TB_M, tn = (n + TB_N - 1) / TB_N;
+    const bool wide = n >= 256;
+    const int bn = wide ? 256 : 128;
+    if ((e = map3d_f32(&ta, fa, kpad, m, leaves, TB_M)) != cudaSuccess) return e;
+    if ((e = map3d_f32(&tb, fb, kpad, n, leaves, bn)) != cudaSuccess) return e;
+    const int64_t tm = (m + TB_M - 1) / TB_M, tn = (n + bn - 1) / bn;
     const int64_t tiles = tm * tn * leaves;
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, sm_count());
     cudaEvent_t t0 = timing_mark(s);
-    tf32_gemm<<<ctas, TB_THREADS, TB_SMEM, s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm), int(tn),
-                                                tiles, ldo, os, accumulate, err);
+    if (wide)
+        tf32_gemm<256><<<ctas, tf_threads<256>(), tf_smem<256>(), s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm),
+                                                                       int(tn), tiles, ldo, os, accumulate, err);
+    else
+        tf32_gemm<128><<<ctas, tf_threads<128>(), tf_smem<128>(), s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm),
+                                                                       int(tn), tiles, ldo, os, accumulate, err);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
