@@ -53,14 +53,21 @@ class Choice:
                         moduli=self.moduli if self.precision != "fp64" else None)
 
 
+_ALGS = None
+
+
 def algorithms():
-    """Shipped base cases: name -> (M, K, N, R)."""
+    """Shipped base cases: name -> (M, K, N, R) (read once)."""
+    global _ALGS
+    if _ALGS is not None:
+        return _ALGS
     out = {}
     for path in sorted(glob.glob(os.path.join(fmm.ALGORITHM_DIR, "*.fmm"))):
         with open(path) as fh:
             lines = [ln.split("#", 1)[0].strip() for ln in fh]
         M, K, N, R = (int(t) for t in next(ln for ln in lines if ln).split())
         out[os.path.basename(path)[:-4]] = (M, K, N, R)
+    _ALGS = out
     return out
 
 
@@ -115,8 +122,13 @@ class Autotuner:
         out = []
         algs = algorithms()
         nmod = moduli_for(self.tol, k) if "ozaki_bf16" in self.precisions else None
+        emulated = "ozaki_bf16" in self.precisions and nmod is not None
         for prec in self.precisions:
             if prec == "ozaki_bf16" and nmod is None:
+                continue
+            # the DFMA pipe is ~1/100 of the emulated rate: FP64 plans only
+            # compete on products too small for the tensor-core path to fill
+            if prec == "fp64" and emulated and min(m, k, n) >= 64:
                 continue
             out.append(self._model(m, k, n, "strassen_222_7", (2, 2, 2, 7), 0, prec, nmod))
             for name, base in algs.items():

@@ -56,6 +56,7 @@ class _Graph:
     C: object
     ws: object
     nbytes: int
+    done: object = None       # event after the last replay (its buffers are free once it has passed)
 
 
 @dataclass
@@ -115,20 +116,25 @@ class Server:
 
     # ------------------------------------------------------------ launch
     def _graph_for(self, plan, shape, slot):
+        """The graph of (plan, shape), captured on first use; None while its
+        previous replay (on any stream) may still be using its buffers."""
         import torch
-        key = (id(plan), shape, slot)
+        key = (id(plan), shape)
         g = self._graphs.get(key)
         if g is not None:
+            if g.done is not None and not g.done.query():
+                return None
             self._graphs.move_to_end(key)
             return g
         m, k, n = shape
         nbytes = 8 * (m * k + k * n + m * n) + plan.workspace_size(m, k, n)
-        # evict least recently used graphs whose slot is idle (a busy slot's
-        # graph buffers may still be read by its stream)
+        # evict least recently used graphs that are idle (a graph whose last
+        # replay has not passed may still be reading its buffers)
         for old_key in list(self._graphs):
             if self._graph_bytes + nbytes <= self.graph_cache_bytes:
                 break
-            if old_key[2] in self.free_slots or old_key[2] == slot:
+            old = self._graphs[old_key]
+            if old.done is None or old.done.query():
                 self._graph_bytes -= self._graphs.pop(old_key).nbytes
         A = torch.empty((m, k), dtype=torch.float64, device="cuda")
         B = torch.empty((k, n), dtype=torch.float64, device="cuda")
@@ -178,12 +184,14 @@ class Server:
                 self._seen[shape_key] = self._seen.get(shape_key, 0) + 1
                 # a shape seen before is replayed from a captured graph; the
                 # first occurrence runs directly (capturing a one-off shape buys nothing)
-                if self.use_graphs and self._seen[shape_key] > 1:
-                    g = self._graph_for(plan, (m, k, n), slot)
+                g = self._graph_for(plan, (m, k, n), slot) if (self.use_graphs and self._seen[shape_key] > 1) else None
+                if g is not None:
                     g.A.copy_(r.A, non_blocking=True)
                     g.B.copy_(r.B, non_blocking=True)
                     g.graph.replay()
                     r.C.copy_(g.C, non_blocking=True)
+                    g.done = torch.cuda.Event()
+                    g.done.record(stream)
                     self.stats.graph_replays += 1
                 else:
                     fmm.gemm(plan, r.A, r.B, C=r.C, workspace=self._workspace(slot, plan.workspace_size(m, k, n)),
@@ -254,13 +262,18 @@ class Server:
         return self.stats.summary()
 
 
-def request_shapes(count, lo=256, hi=8192, seed=1409):
-    """m, k, n of each request, each log-uniform in [lo, hi]."""
+def request_shapes(count, lo=256, hi=8192, seed=1409, shape_pool=0):
+    """m, k, n of each request, each log-uniform in [lo, hi]; with
+    shape_pool > 0 the requests draw (uniformly) from that many such shapes,
+    so shapes recur as they do when a service sees a fixed set of models."""
     g = np.random.default_rng(seed)
+    if shape_pool:
+        pool = np.exp(g.uniform(np.log(lo), np.log(hi), size=(shape_pool, 3))).astype(int)
+        return pool[g.integers(0, shape_pool, size=count)]
     return np.exp(g.uniform(np.log(lo), np.log(hi), size=(count, 3))).astype(int)
 
 
-def poisson_requests(count, rate_per_s, lo=256, hi=8192, seed=1409, device="cuda", pool=None):
+def poisson_requests(count, rate_per_s, lo=256, hi=8192, seed=1409, device="cuda", pool=None, shape_pool=0):
     """Requests with Poisson arrivals and m, k, n each log-uniform in
     [lo, hi]; operands uniform[-1, 1] on the device.  With `pool` (a 1-D
     float64 device tensor of at least hi*hi elements) the operands are views
@@ -269,7 +282,7 @@ def poisson_requests(count, rate_per_s, lo=256, hi=8192, seed=1409, device="cuda
     import torch
     g = np.random.default_rng(seed + 1)
     t = np.cumsum(g.exponential(1.0 / rate_per_s, size=count))
-    dims = request_shapes(count, lo, hi, seed)
+    dims = request_shapes(count, lo, hi, seed, shape_pool)
     gen = torch.Generator(device=device)
     gen.manual_seed(seed)
     reqs = []

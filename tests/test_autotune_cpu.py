@@ -5,13 +5,19 @@ from paper_1409_2908_gb300 import autotune
 
 
 def test_candidates_cover_algorithms_levels_precisions():
-    t = autotune.Autotuner(tol=1e-11, measure=False)
+    t = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False)
     cands = t.candidates(8192, 8192, 8192)
     names = {(c.algorithm, c.levels, c.precision) for c in cands}
     assert ("strassen_222_7", 0, "fp64") in names
     assert ("strassen_222_7", 3, "fp64") in names
-    assert any(c.precision == "ozaki_bf16" and c.levels >= 1 for c in cands)
     assert cands == sorted(cands, key=lambda c: c.model_ms)
+    t = autotune.Autotuner(tol=1e-11, measure=False)
+    cands = t.candidates(8192, 8192, 8192)
+    assert any(c.precision == "ozaki_bf16" and c.levels >= 1 for c in cands)
+    assert any(c.precision == "ozaki_bf16" and c.levels == 0 for c in cands)
+    # with the emulated variant available, FP64 plans only compete on tiny products
+    assert all(c.precision == "ozaki_bf16" for c in cands)
+    assert any(c.precision == "fp64" for c in t.candidates(40, 3000, 40))
 
 
 def test_recursion_stops_when_leaves_get_small():
