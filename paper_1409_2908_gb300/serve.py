@@ -88,13 +88,15 @@ class Stats:
 
 
 class Server:
-    def __init__(self, tuner, memory_budget_bytes, slots=4, graph_cache_bytes=None, use_graphs=True):
+    def __init__(self, tuner, memory_budget_bytes, slots=4, graph_cache_bytes=None, use_graphs=True,
+                 keep_results=True):
         import torch
         self.tuner = tuner
         self.budget = int(memory_budget_bytes)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.free_slots = deque(range(slots))
         self.use_graphs = use_graphs
+        self.keep_results = keep_results   # False: a result is dropped once complete (handed off)
         self.graph_cache_bytes = graph_cache_bytes if graph_cache_bytes is not None else self.budget // 2
         self._graphs = OrderedDict()      # (plan key, shape, slot) -> _Graph
         self._graph_bytes = 0
@@ -224,6 +226,8 @@ class Server:
                     done = time.perf_counter() - t0
                     for r in g.reqs:
                         r.t_done = done
+                        if not self.keep_results:
+                            r.C = None
                         self.stats.latencies.append(done - r.arrival)
                         self.stats.flops += r.flops
                         self.stats.completed += 1
