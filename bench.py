@@ -541,7 +541,9 @@ def main():
         ems = max_over_ranks(torch, ws, max(ems, wall)) / args.steps
         e2e = {"value": ws * flops / ems / 1e9, "unit": "TFLOP/s", "ms_per_step": ems,
                "h2d_bytes_per_step": 8 * (m * k + k * n), "d2h_bytes_per_step": 8 * m * n,
-               "api": "fmm_gemm_host (pinned host A, B, C; H2D + product + D2H per step)"}
+               "api": "fmm_gemm_host (pinned host A, B, C; H2D + product + D2H per step)",
+               "pipeline": ("B copied in while the kernels reading only A run; residue products in row "
+                            "bands, each combined and copied out while the next band is multiplied")}
         del hws
 
     # the fastest FP64 fast plan within the target, against the FP64 classical GEMM

@@ -259,9 +259,24 @@ fmm_status fmm_classical_gemm(const double *A, int64_t lda, const double *B,
  * Host buffers should be page-locked for full copy speed.  dev_ws is a
  * device buffer of at least fmm_host_workspace_size() bytes, 256-byte
  * aligned, holding the device copies and the plan's workspace.
+ * Work is issued on `stream` and on one internal stream per calling thread
+ * and device: for the emulated-FP64 residue path without a fringe, the
+ * copy of B overlaps the kernels that read only A, and C is copied out in
+ * row bands while the last pass writes the following bands.  On return
+ * (success or error) nothing the call issued is still in flight.
  */
 fmm_status fmm_host_workspace_size(fmm_plan_t plan, int64_t m, int64_t k,
                                    int64_t n, size_t *bytes);
+/*
+ * fmm_set_host_pipeline - depth of that overlap for later fmm_gemm_host calls
+ * on the calling thread: C leaves in `bands` row bands, and (emulated FP64 at
+ * most one recursive level deep, no fringe) the residue products are made in
+ * `gemm_bands` row bands, each combined and copied out while the next band
+ * is multiplied.  0 for either: chosen from the sizes.  The result does not
+ * depend on either count.
+ * Errors: FMM_ERR_ARG for a count below 0 or above 64.
+ */
+fmm_status fmm_set_host_pipeline(int bands, int gemm_bands);
 fmm_status fmm_gemm_host(fmm_plan_t plan, const double *A, int64_t lda,
                          const double *B, int64_t ldb, double *C, int64_t ldc,
                          int64_t m, int64_t k, int64_t n, void *dev_ws,

@@ -276,6 +276,13 @@ def gemm_host(plan, A, B, C, dev_ws, stream=None):
     return C
 
 
+def set_host_pipeline(bands=0, gemm_bands=0):
+    """Overlap depth of later gemm_host calls on this thread
+    (fmm_set_host_pipeline): C copied out in `bands` row bands, residue
+    products made in `gemm_bands` row bands; 0 = chosen from the sizes."""
+    _check(_lib.lib().fmm_set_host_pipeline(int(bands), int(gemm_bands)), "set_host_pipeline")
+
+
 def host_workspace_size(plan, m, k, n):
     b = ctypes.c_size_t()
     h = plan.handle if plan is not None else ctypes.c_void_p()

@@ -49,6 +49,8 @@ def _declare(L):
     L.fmm_classical_gemm.restype = st
     L.fmm_host_workspace_size.argtypes = [c_p, c_i64, c_i64, c_i64, ctypes.POINTER(ctypes.c_size_t)]
     L.fmm_host_workspace_size.restype = st
+    L.fmm_set_host_pipeline.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.fmm_set_host_pipeline.restype = st
     L.fmm_gemm_host.argtypes = [c_p, c_p, c_i64, c_p, c_i64, c_p, c_i64, c_i64, c_i64, c_i64,
                                 c_p, ctypes.c_size_t, c_p]
     L.fmm_gemm_host.restype = st

@@ -252,13 +252,111 @@ cudaError_t timed(cudaStream_t s, F &&f) {
     return e;
 }
 
+// Where a path has no place for the host overlap: wait for B now and drop
+// the hooks (the caller then copies C out after the whole product).
+cudaError_t settle_pipe(const HostPipe *&pipe, cudaStream_t s) {
+    if (!pipe) return cudaSuccess;
+    const cudaError_t e = pipe->b_ready ? cudaStreamWaitEvent(s, pipe->b_ready, 0) : cudaSuccess;
+    pipe = nullptr;
+    return e;
+}
+
+// Side stream and events of the host entry point, one set per thread and
+// device (created on first use).
+struct HostSide {
+    int device = -1;
+    cudaStream_t side = nullptr;
+    cudaEvent_t a_in = nullptr, b_in = nullptr, band = nullptr, side_done = nullptr;
+    void release() {
+        for (cudaEvent_t *ev : {&a_in, &b_in, &band, &side_done})
+            if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
+        if (side) cudaStreamDestroy(side), side = nullptr;
+        device = -1;
+    }
+    ~HostSide() { release(); }
+};
+thread_local HostSide t_host;
+
+HostSide *host_side() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (t_host.device == dev) return &t_host;
+    t_host.release();
+    if (cudaStreamCreateWithFlags(&t_host.side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    for (cudaEvent_t *ev : {&t_host.a_in, &t_host.b_in, &t_host.band, &t_host.side_done})
+        if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+            t_host.release();
+            return nullptr;
+        }
+    t_host.device = dev;
+    return &t_host;
+}
+
+// rows x cols doubles between host and device, one flat copy when both sides
+// are packed
+cudaError_t copy_rows(void *dst, int64_t dld, const void *src, int64_t sld, int64_t rows, int64_t cols,
+                      cudaMemcpyKind kind, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (dld == cols && sld == cols) return cudaMemcpyAsync(dst, src, size_t(rows * cols * 8), kind, s);
+    return cudaMemcpy2DAsync(dst, size_t(dld * 8), src, size_t(sld * 8), size_t(cols * 8), size_t(rows), kind, s);
+}
+
+// fmm_set_host_pipeline (0: from the sizes)
+thread_local int t_bands = 0, t_gemm_bands = 0;
+
+// Row bands of C copied out while the last pass still writes the next ones:
+// about 32 MiB of C per band, at most 8.
+int host_bands(int64_t m, int64_t n) {
+    if (t_bands > 0) return t_bands;
+    const double mib = double(m) * double(n) * 8.0 / 1048576.0;
+    return (int)std::min(8.0, std::max(1.0, std::floor(mib / 32.0)));
+}
+
+// Row bands of the residue products: each band of S is multiplied by all of
+// T, so T is read once per band.
+int host_gemm_bands(int bands) {
+    if (t_gemm_bands > 0) return t_gemm_bands;
+    return std::min(bands, 4);
+}
+
+struct BandCopy {
+    cudaStream_t s, side;
+    cudaEvent_t ev;
+    double *hostC;
+    int64_t ldc;
+    const double *devC;
+    int64_t n;
+    int64_t rows_done;
+};
+
+// HostPipe::band_done of the host entry point: the band's rows of every
+// block row, copied on the side stream after the pass that wrote them.
+cudaError_t copy_band(void *ctx, int64_t r0, int64_t r1, int64_t block_rows, int count) {
+    BandCopy *b = (BandCopy *)ctx;
+    cudaError_t e;
+    if ((e = cudaEventRecord(b->ev, b->s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->side, b->ev, 0)) != cudaSuccess) return e;
+    for (int a = 0; a < count; ++a) {
+        const int64_t row = a * block_rows + r0;
+        if ((e = copy_rows(b->hostC + row * b->ldc, b->ldc, b->devC + row * b->n, b->n, r1 - r0, b->n,
+                           cudaMemcpyDeviceToHost, b->side)) != cudaSuccess)
+            return e;
+    }
+    b->rows_done += (r1 - r0) * count;
+    return cudaSuccess;
+}
+
 // Emulated-FP64 leaves: FP64 level-by-level S/T, tensor-core residue
 // products, FP64 level-by-level W; classical FP64 fringe.
 fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, const double *A,
                           int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
                           int64_t m, int64_t k, int64_t n, char *wsb, cudaStream_t s,
-                          int *launches) {
+                          int *launches, const HostPipe *pipe) {
     cudaError_t e;
+    // the overlap hooks reach only the residue-space path without a fringe
+    const bool fringe = g.mp < m || g.kp < k || g.np < n;
+    if (p->prec == FMM_PREC_TF32 || (p->L > 0 && (!residue_space(p) || fringe)))
+        if ((e = settle_pipe(pipe, s)) != cudaSuccess) return cuda_status(e);
     // (the timing pair, when enabled, brackets the tensor-core GEMM inside)
     const bool tf = p->prec == FMM_PREC_TF32;
     auto leaf_products = [&](const double *S_, int64_t lds, int64_t ss, const double *T_, int64_t ldt,
@@ -272,14 +370,14 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     if (p->L == 0)
         return cuda_status(tf ? leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n)
                               : ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, m, k, n, p->nmod, 0, wsb, s,
-                                           launches));
+                                           launches, pipe));
     if (!tf && residue_space(p)) {
         const bool kfr = g.kp < k;
         if (kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
                                          g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
             return cuda_status(e);
         if ((e = ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, g.mp, g.kp, g.np, p->nmod,
-                            kfr ? 1 : 0, wsb + wl.oz, s, launches)) != cudaSuccess)
+                            kfr ? 1 : 0, wsb + wl.oz, s, launches, pipe)) != cudaSuccess)
             return cuda_status(e);
         if (g.mp < m &&
             (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
@@ -340,12 +438,19 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     return FMM_OK;
 }
 
-// The fast core plus the classical fringe, all on one stream.
+// The fast core plus the classical fringe, all on one stream.  pipe: the
+// host entry point's overlap hooks (or null); paths that cannot use them wait
+// for B first and drop them.
 fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
-                    size_t ws_bytes, cudaStream_t s, int *launches) {
+                    size_t ws_bytes, cudaStream_t s, int *launches, const HostPipe *pipe = nullptr) {
     const Geometry g = geometry(p, m, k, n);
-    if ((p->prec == FMM_PREC_OZAKI_BF16 || p->prec == FMM_PREC_TF32) && (p->L == 0 || g.fast)) {
+    const bool emulated = (p->prec == FMM_PREC_OZAKI_BF16 || p->prec == FMM_PREC_TF32) && (p->L == 0 || g.fast);
+    if (!emulated) {
+        const cudaError_t pe = settle_pipe(pipe, s);
+        if (pe != cudaSuccess) return cuda_status(pe);
+    }
+    if (emulated) {
         // int32 drain sums stay below 2^31 for k_L <= 65536 (2^23 per 512-chunk)
         if (g.kL > 65536) return FMM_ERR_UNSUPPORTED;
         const WsLayout wl = ws_layout(p, g);
@@ -353,7 +458,7 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
         if (wl.total > 0 && ((uintptr_t)ws & 255)) return FMM_ERR_ARG;
         const fmm_status us = ensure_uploaded(p);
         if (us != FMM_OK) return us;
-        return run_gemm_ozaki(p, g, wl, A, lda, B, ldb, C, ldc, m, k, n, (char *)ws, s, launches);
+        return run_gemm_ozaki(p, g, wl, A, lda, B, ldb, C, ldc, m, k, n, (char *)ws, s, launches, pipe);
     }
     if (!g.fast)
         return cuda_status(timed(s, [&] {
@@ -788,6 +893,13 @@ fmm_status fmm_host_workspace_size(fmm_plan_t p, int64_t m, int64_t k, int64_t n
     return FMM_OK;
 }
 
+fmm_status fmm_set_host_pipeline(int bands, int gemm_bands) {
+    if (bands < 0 || bands > 64 || gemm_bands < 0 || gemm_bands > 64) return FMM_ERR_ARG;
+    t_bands = bands;
+    t_gemm_bands = gemm_bands;
+    return FMM_OK;
+}
+
 fmm_status fmm_gemm_host(fmm_plan_t p, const double *A, int64_t lda, const double *B,
                          int64_t ldb, double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                          void *dev_ws, size_t ws_bytes, void *stream) {
@@ -798,27 +910,54 @@ fmm_status fmm_gemm_host(fmm_plan_t p, const double *A, int64_t lda, const doubl
     size_t need = 0;
     fmm_host_workspace_size(p, m, k, n, &need);
     if (ws_bytes < need) return FMM_ERR_NO_MEMORY;
+    HostSide *hs = host_side();
+    if (!hs) return FMM_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     char *w = (char *)dev_ws;
     double *dA = (double *)w;
     double *dB = (double *)(w + align256(size_t(m * k * 8)));
     double *dC = (double *)((char *)dB + align256(size_t(k * n * 8)));
     char *rest = (char *)dC + align256(size_t(m * n * 8));
+    // A on the caller's stream; B on the side stream once A is in (the two
+    // would only share the link), so that the kernels reading A alone overlap
+    // the copy of B
     cudaError_t e;
-    if ((e = cudaMemcpy2DAsync(dA, k * 8, A, lda * 8, k * 8, m, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_status(e);
-    if ((e = cudaMemcpy2DAsync(dB, n * 8, B, ldb * 8, n * 8, k, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return cuda_status(e);
+    auto fail = [&](fmm_status st) {
+        cudaStreamSynchronize(hs->side);   // no copy into the caller's buffers left in flight
+        cudaStreamSynchronize(s);
+        return st;
+    };
+    if ((e = copy_rows(dA, k, A, lda, m, k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaEventRecord(hs->a_in, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(hs->side, hs->a_in, 0)) != cudaSuccess ||
+        (e = copy_rows(dB, n, B, ldb, k, n, cudaMemcpyHostToDevice, hs->side)) != cudaSuccess ||
+        (e = cudaEventRecord(hs->b_in, hs->side)) != cudaSuccess)
+        return fail(cuda_status(e));
+    // C leaves in row bands, each copied on the side stream as soon as the
+    // last pass has written it (when the path runs in bands at all)
+    BandCopy bc{s, hs->side, hs->band, C, ldc, dC, n, 0};
+    const int bands = host_bands(m, n);
+    HostPipe pipe{hs->b_in, bands, host_gemm_bands(bands), copy_band, &bc};
     fmm_status st;
     int launches = 0;
-    if (p)
-        st = run_gemm(p, dA, k, dB, n, dC, n, m, k, n, rest, ws_bytes - (rest - w), s, &launches);
-    else
-        st = cuda_status(launch_classical(dA, k, dB, n, dC, n, m, k, n, FMM_TILE_AUTO, s, &launches));
+    if (p) {
+        st = run_gemm(p, dA, k, dB, n, dC, n, m, k, n, rest, ws_bytes - (rest - w), s, &launches, &pipe);
+    } else {
+        st = cuda_status(cudaStreamWaitEvent(s, hs->b_in, 0));
+        if (st == FMM_OK)
+            st = cuda_status(launch_classical(dA, k, dB, n, dC, n, m, k, n, FMM_TILE_AUTO, s, &launches));
+    }
     t_launches = launches;
-    if (st != FMM_OK) return st;
-    if ((e = cudaMemcpy2DAsync(C, ldc * 8, dC, n * 8, n * 8, m, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-        return cuda_status(e);
+    if (st != FMM_OK) return fail(st);
+    if (bc.rows_done == m) {
+        if ((e = cudaEventRecord(hs->side_done, hs->side)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, hs->side_done, 0)) != cudaSuccess)
+            return fail(cuda_status(e));
+    } else if (bc.rows_done != 0) {
+        return fail(FMM_ERR_CUDA);
+    } else if ((e = copy_rows(C, ldc, dC, n, m, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) {
+        return fail(cuda_status(e));
+    }
     return cuda_status(cudaStreamSynchronize(s));
 }
 

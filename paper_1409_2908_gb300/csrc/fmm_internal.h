@@ -171,9 +171,25 @@ struct ResPlan {
     int u_absmax, v_absmax;                  // max over r of sum_i |U_ir|, of sum_j |V_jr|
 };
 size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod);
+// Overlap hooks of the host entry point.  b_ready (or null): an event the
+// kernels that read B wait on, so B may still be arriving from the host while
+// the kernels that read only A run.  band_done (or null): the final W + CRT
+// pass runs in `bands` row bands, and after each band is enqueued band_done is
+// called on the host with the band's rows [r0, r1) inside each of the
+// `block_rows_count` block rows of C (each `block_rows` tall); it may enqueue
+// work on other streams (a copy of the band out of C).  gemm_bands > 1: with
+// at most one recursive level, the residue products are made in that many
+// row bands too, each combined and handed over before the next is made.
+struct HostPipe {
+    cudaEvent_t b_ready;
+    int bands, gemm_bands;
+    cudaError_t (*band_done)(void *ctx, int64_t r0, int64_t r1, int64_t block_rows, int block_rows_count);
+    void *ctx;
+};
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
-                       int accumulate, void *ws, cudaStream_t s, int *launches);
+                       int accumulate, void *ws, cudaStream_t s, int *launches,
+                       const HostPipe *pipe = nullptr);
 
 int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
                  double extra_a, double extra_b, int num_sms);

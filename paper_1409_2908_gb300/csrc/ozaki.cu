@@ -796,10 +796,12 @@ __global__ void __launch_bounds__(256) res_stream_form(const int8_t *P, int64_t 
 // qb = (a, c) of the M x N grid, modulus q: Z_qb = sum_t w_t child(r_t) mod p;
 // C'_qb from its residues, times 2^-(ea_i + eb_j), stored (or added) in C.
 // With L = 0 the one child is the product itself.  Thread: one row of the
-// child blocks, V consecutive columns.
+// child blocks, V consecutive columns.  A launch covers the child rows
+// [r0, r0 + nr) of every block (rows tall); Z points at the first of them in
+// plane 0, and the planes are zr rows apart.
 template <int V, bool REDUCE, int NMOD>
 __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t rows, int64_t cols, int64_t cld,
-                                                    int gridN, int MN, int nmod_rt, const int *w_ptr, const int *w_r,
+                                                    int64_t zr, int64_t r0, int64_t nr, int gridN, int MN, int nmod_rt, const int *w_ptr, const int *w_r,
                                                     const int *w_icoef, const int *ea, const int *eb, double *C,
                                                     int64_t ldc, int accumulate) {
     // NMOD > 0: the moduli count is a compile-time constant (loops unrolled,
@@ -816,11 +818,11 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
     __syncthreads();
     const int64_t groups = (cols + V - 1) / V;
     const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (pos >= rows * groups) return;
-    const int64_t i = pos / groups, j0 = (pos % groups) * V;
+    if (pos >= nr * groups) return;
+    const int64_t il = pos / groups, i = r0 + il, j0 = (pos % groups) * V;
     const int valid = (int)min((int64_t)V, cols - j0);
-    const int64_t plane = rows * cld;
-    const int8_t *zrow = Z + i * cld + j0;
+    const int64_t plane = zr * cld;
+    const int8_t *zrow = Z + il * cld + j0;
     for (int qb = 0; qb < MN; ++qb) {
         const int a = qb / gridN, c = qb % gridN;
         int L[V][NL];
@@ -1064,12 +1066,12 @@ cudaError_t ensure_tables(int nmod) {
 }
 
 cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, int64_t planes,
-                       int box_rows) {
+                       int box_rows, int64_t plane_rows) {
     EncodeFn enc;
     cudaError_t e = encode_fn(&enc);
     if (e != cudaSuccess) return e;
     cuuint64_t gdim[3] = {(cuuint64_t)kpad, (cuuint64_t)rows, (cuuint64_t)planes};
-    cuuint64_t gstr[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(kpad * rows * 2)};
+    cuuint64_t gstr[2] = {(cuuint64_t)kpad * 2, (cuuint64_t)(kpad * plane_rows * 2)};
     cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, gdim, gstr, box, es,
@@ -1083,17 +1085,23 @@ cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, in
 int64_t z_pitch(int64_t n) { return (n + 15) / 16 * 16; }
 
 // One persistent launch over all tiles of all planes; N = 256 tiles when the
-// planes are at least 256 wide.
+// planes are at least 256 wide.  A band: the rows [r0, r0 + m) of planes of
+// plane_m rows (S: plane_m x kpad per plane); the band's products go to Z as
+// planes of m rows (the caller points Z at the band's own region).
 cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64_t m, int64_t n,
                                 int64_t kpad, int64_t planes, int nmod, int *err, cudaStream_t s,
-                                int *launches) {
+                                int *launches, int64_t r0 = 0, int64_t plane_m = -1) {
     cudaError_t e;
     if ((e = configure_residue_gemm()) != cudaSuccess) return e;
+    if (plane_m < 0) plane_m = m;
     const bool wide = n >= 256;
     const int bn = wide ? 256 : 128;
     CUtensorMap ta, tb;
-    if ((e = make_map3d(&ta, (void *)ra, kpad, m, planes, OZ_BM)) != cudaSuccess) return e;
-    if ((e = make_map3d(&tb, (void *)rb, kpad, n, planes, bn)) != cudaSuccess) return e;
+    // kpad is a multiple of 64, so the band's first row starts 16-byte aligned
+    if ((e = make_map3d(&ta, (void *)((const char *)ra + r0 * kpad * 2), kpad, m, planes, OZ_BM, plane_m)) !=
+        cudaSuccess)
+        return e;
+    if ((e = make_map3d(&tb, (void *)rb, kpad, n, planes, bn, n)) != cudaSuccess) return e;
     const int64_t tn = (n + bn - 1) / bn, tmb = (m + OZ_BM - 1) / OZ_BM;
     const int64_t tiles = tn * tmb * planes;
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
@@ -1284,7 +1292,7 @@ static cudaError_t configure_split_form() {
 // fused into the top level of the W combination.
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
-                       int accumulate, void *ws, cudaStream_t s, int *launches) {
+                       int accumulate, void *ws, cudaStream_t s, int *launches, const HostPipe *pipe) {
     cudaError_t e = ensure_tables(nmod);
     if (e != cudaSuccess) return e;
     if ((e = configure_split_form()) != cudaSuccess) return e;
@@ -1301,46 +1309,6 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int beta = ozaki_beta(nmod, kp);
     auto check = [&]() { ++*launches; return cudaGetLastError(); };
 
-    row_exp_kernel<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, ea);
-    if ((e = check()) != cudaSuccess) return e;
-    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, 8), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
-    if ((e = check()) != cudaSuccess) return e;
-
-    // level 1 (or the GEMM operands when L = 0) straight from A and B; B is
-    // kept transposed from here on, so every T_r is formed directly in the
-    // K-major layout the residue GEMM reads
-    {
-        const int64_t ml = mp / (rp.L ? rp.M : 1), kl = kp / (rp.L ? rp.K : 1), nl = np / (rp.L ? rp.N : 1);
-        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
-        const bool last = rp.L <= 1;
-        const int64_t out_ld = last ? kpad : kl;
-        const int R1 = rp.L ? rp.R : 1;
-        const int gK = rp.L ? rp.K : 1, gN = rp.L ? rp.N : 1, nbA = rp.L ? rp.M * rp.K : 1, nbB = rp.L ? rp.K * rp.N : 1;
-        const int *up = rp.L ? rp.u_ptr : id_ptr, *uc = rp.L ? rp.u_code : id_code, *ui = rp.L ? rp.u_icoef : id_coef;
-        const int *vp = rp.L ? rp.v_ptr : id_ptr, *vc = rp.L ? rp.v_code : id_code, *vi = rp.L ? rp.v_icoef : id_coef;
-        if (fused) {
-            // limbs of |S'| < 2^(beta + ceil(log2 max sum|c|)): 3 x 14, 4 x 14 or 5 x 13 bits
-            const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
-            int bits = beta;
-            while ((1 << (bits - beta)) < cmax) ++bits;
-            const int lc = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
-#define FMM_SPLITS(F, LC)                                                                                               \
-    do {                                                                                                                \
-        e = launch_split_form_rows<F, LC>(nbA, A, lda, ea, ml, kl, gK, R1, nmod, up, uc, ui, b + w.la[0], out_ld, s);   \
-        ++*launches;                                                                                                    \
-        if (e != cudaSuccess) return e;                                                                                 \
-        e = launch_split_form_cols_t<F, LC>(nbB, B, ldb, eb, kl, nl, gN, R1, nmod, vp, vc, vi, b + w.lb[0], out_ld, s); \
-        ++*launches;                                                                                                    \
-        if (e != cudaSuccess) return e;                                                                                 \
-    } while (0)
-            if (last) {
-                if (lc == 0) FMM_SPLITS(true, 0); else if (lc == 1) FMM_SPLITS(true, 1); else FMM_SPLITS(true, 2);
-            } else {
-                if (lc == 0) FMM_SPLITS(false, 0); else if (lc == 1) FMM_SPLITS(false, 1); else FMM_SPLITS(false, 2);
-            }
-#undef FMM_SPLITS
-        }
-    }
     auto form = [&](const int8_t *par, int64_t parents, int64_t prr, int64_t pcc, int64_t rows, int64_t cols,
                     const int *uptr, const int *ucode, const int *ucoef, void *out, bool last,
                     int64_t out_ld) -> cudaError_t {
@@ -1387,22 +1355,68 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         }
         return cudaSuccess;
     };
-    if (!fused) {
-        // a base case without a fused first-level instance: level-0 residues, then level 1
-        int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
+
+    // level 1 (or the GEMM operands when L = 0) straight from A and B; B is
+    // kept transposed from here on, so every T_r is formed directly in the
+    // K-major layout the residue GEMM reads.  Everything that reads A is
+    // issued before anything that reads B, so that B may still be arriving
+    // (pipe->b_ready) while the A side runs.
+    const int64_t ml1 = mp / (rp.L ? rp.M : 1), kl1 = kp / (rp.L ? rp.K : 1), nl1 = np / (rp.L ? rp.N : 1);
+    const int64_t kpad1 = (kl1 + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const bool last1 = rp.L <= 1;
+    const int64_t out_ld1 = last1 ? kpad1 : kl1;
+    const int R1 = rp.L ? rp.R : 1;
+    const int gK = rp.L ? rp.K : 1, gN = rp.L ? rp.N : 1, nbA = rp.L ? rp.M * rp.K : 1, nbB = rp.L ? rp.K * rp.N : 1;
+    const int *up = rp.L ? rp.u_ptr : id_ptr, *uc = rp.L ? rp.u_code : id_code, *ui = rp.L ? rp.u_icoef : id_coef;
+    const int *vp = rp.L ? rp.v_ptr : id_ptr, *vc = rp.L ? rp.v_code : id_code, *vi = rp.L ? rp.v_icoef : id_coef;
+    // limbs of |S'| < 2^(beta + ceil(log2 max sum|c|)): 3 x 14, 4 x 14 or 5 x 13 bits
+    int lc = 0;
+    {
+        const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
+        int bits = beta;
+        while ((1 << (bits - beta)) < cmax) ++bits;
+        lc = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
+    }
+#define FMM_SPLIT(WHICH, F, LC)                                                                                     \
+    (WHICH ? launch_split_form_cols_t<F, LC>(nbB, B, ldb, eb, kl1, nl1, gN, R1, nmod, vp, vc, vi, b + w.lb[0],      \
+                                             out_ld1, s)                                                           \
+           : launch_split_form_rows<F, LC>(nbA, A, lda, ea, ml1, kl1, gK, R1, nmod, up, uc, ui, b + w.la[0],       \
+                                           out_ld1, s))
+    auto fused_split = [&](int which) -> cudaError_t {
+        cudaError_t se;
+        if (last1)
+            se = lc == 0 ? FMM_SPLIT(which, true, 0) : lc == 1 ? FMM_SPLIT(which, true, 1) : FMM_SPLIT(which, true, 2);
+        else
+            se = lc == 0 ? FMM_SPLIT(which, false, 0) : lc == 1 ? FMM_SPLIT(which, false, 1) : FMM_SPLIT(which, false, 2);
+        ++*launches;
+        return se;
+    };
+#undef FMM_SPLIT
+    // a base case without a fused first-level instance: level-0 residues, then level 1
+    int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
+
+    row_exp_kernel<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, ea);
+    if ((e = check()) != cudaSuccess) return e;
+    if (fused) {
+        if ((e = fused_split(0)) != cudaSuccess) return e;
+    } else {
         split_rows_i8<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, nmod, ra0, ea);
         if ((e = check()) != cudaSuccess) return e;
+        if ((e = form(ra0, 1, mp, kp, ml1, kl1, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[0], last1,
+                      out_ld1)) != cudaSuccess)
+            return e;
+    }
+    if (pipe && pipe->b_ready && (e = cudaStreamWaitEvent(s, pipe->b_ready, 0)) != cudaSuccess) return e;
+    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, 8), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
+    if ((e = check()) != cudaSuccess) return e;
+    if (fused) {
+        if ((e = fused_split(1)) != cudaSuccess) return e;
+    } else {
         split_cols_t_i8<<<dim3((unsigned)((kp + 31) / 32), (unsigned)((np + 31) / 32)), dim3(32, 8), 0, s>>>(
             B, ldb, kp, np, nmod, eb, rb0);
         if ((e = check()) != cudaSuccess) return e;
-        const int64_t ml = mp / rp.M, kl = kp / rp.K, nl = np / rp.N;
-        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
-        const bool last = rp.L == 1;
-        if ((e = form(ra0, 1, mp, kp, ml, kl, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[0], last,
-                      last ? kpad : kl)) != cudaSuccess)
-            return e;
-        if ((e = form(rb0, 1, np, kp, nl, kl, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last,
-                      last ? kpad : kl)) != cudaSuccess)
+        if ((e = form(rb0, 1, np, kp, nl1, kl1, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last1,
+                      out_ld1)) != cudaSuccess)
             return e;
     }
     // levels 2..L: S and T^T level by level
@@ -1425,8 +1439,72 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     // the leaf products, all leaves and moduli in one launch
     const int64_t mL = pm, kL = pk, nL = pn, leaves = parents;
     const int64_t kpadL = (kL + OZ_BK - 1) / OZ_BK * OZ_BK;
+    const int64_t planes = leaves * nmod;
     int8_t *Z = (int8_t *)(b + w.zres);
-    if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, leaves * nmod, nmod,
+
+    // top level of W fused with the CRT, straight into C: the child rows
+    // [r0, r0 + nr) of every block, from z (the first of them in plane 0,
+    // planes zr rows apart)
+    const int MN = rp.L ? rp.M * rp.N : 1, gM = rp.L ? rp.M : 1;   // gN: the block columns, as above
+    const int *wp = rp.L ? rp.w_ptr : id_ptr, *wr = rp.L ? rp.w_r : id_code, *wc = rp.L ? rp.w_icoef : id_coef;
+    // |limb sum| <= (sum_t |w_t|) 128 (2^16 - 1) nmod
+    const bool reduce = double(rp.L ? rp.w_absmax : 1) * 128.0 * 65535.0 * nmod >= 1073741824.0;
+    auto w_crt = [&](const int8_t *z, int64_t zr, int64_t r0, int64_t nr, int64_t cm, int64_t cn,
+                     int64_t cld) -> cudaError_t {
+        const bool v4 = cld % 4 == 0;
+        const int64_t threads = v4 ? nr * ((cn + 3) / 4) : nr * cn;
+        const unsigned blocks = (unsigned)((threads + 255) / 256);
+#define FMM_WCRT(V, RED, NM) w_crt_kernel<V, RED, NM><<<blocks, 256, 0, s>>>(z, cm, cn, cld, zr, r0, nr, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
+#define FMM_WCRT_N(V, RED)                                        \
+    switch (nmod) {                                               \
+        case 12: FMM_WCRT(V, RED, 12); break;                     \
+        case 13: FMM_WCRT(V, RED, 13); break;                     \
+        case 14: FMM_WCRT(V, RED, 14); break;                     \
+        case 15: FMM_WCRT(V, RED, 15); break;                     \
+        case 16: FMM_WCRT(V, RED, 16); break;                     \
+        default: FMM_WCRT(V, RED, 0); break;                      \
+    }
+        if (v4) {
+            if (reduce) { FMM_WCRT_N(4, true) } else { FMM_WCRT_N(4, false) }
+        } else {
+            if (reduce) { FMM_WCRT(1, true, 0); } else { FMM_WCRT(1, false, 0); }
+        }
+#undef FMM_WCRT_N
+#undef FMM_WCRT
+        cudaError_t ce = check();
+        if (ce == cudaSuccess && pipe && pipe->band_done) ce = pipe->band_done(pipe->ctx, r0, r0 + nr, cm, gM);
+        return ce;
+    };
+    // the host's copy-out bands: each pass hands its rows over as soon as
+    // they are written
+    const int bands = (pipe && pipe->band_done) ? std::max(1, pipe->bands) : 1;
+
+    // with one recursive level at most, the products themselves may be made
+    // in row bands (each band of S against all of T; the band's products form
+    // a region of their own in Z), each combined and handed over while the
+    // next band is multiplied
+    const int gb = (pipe && pipe->band_done && rp.L <= 1)
+                       ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(pipe->gemm_bands, bands), mL))
+                       : 1;
+    if (gb > 1) {
+        const int64_t cld = z_pitch(nL);
+        const int sub = std::max(1, bands / gb);
+        for (int g = 0; g < gb; ++g) {
+            const int64_t R0 = mL * g / gb, NR = mL * (g + 1) / gb - R0;
+            int8_t *Zb = Z + planes * R0 * cld;
+            if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Zb, NR, nL, kpadL, planes, nmod, err,
+                                         s, launches, R0, mL)) != cudaSuccess)
+                return e;
+            const int ns = (int)std::max<int64_t>(1, std::min<int64_t>(sub, NR));
+            for (int t = 0; t < ns; ++t) {
+                const int64_t r0 = R0 + NR * t / ns, nr = R0 + NR * (t + 1) / ns - r0;
+                if ((e = w_crt(Zb + (r0 - R0) * cld, NR, r0, nr, mL, nL, cld)) != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+
+    if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, planes, nmod,
                                  err, s, launches)) != cudaSuccess)
         return e;
     // W levels L..2 on residues, down to the level-1 products
@@ -1454,33 +1532,10 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         cld = cn;
         lp /= rp.R;
     }
-    // top level of W fused with the CRT, straight into C
-    {
-        const int gN = rp.L ? rp.N : 1, MN = rp.L ? rp.M * rp.N : 1;
-        const int *wp = rp.L ? rp.w_ptr : id_ptr, *wr = rp.L ? rp.w_r : id_code, *wc = rp.L ? rp.w_icoef : id_coef;
-        // |limb sum| <= (sum_t |w_t|) 128 (2^16 - 1) nmod
-        const bool reduce = double(rp.L ? rp.w_absmax : 1) * 128.0 * 65535.0 * nmod >= 1073741824.0;
-        const bool v4 = cld % 4 == 0;
-        const int64_t threads = v4 ? cm * ((cn + 3) / 4) : cm * cn;
-        const unsigned blocks = (unsigned)((threads + 255) / 256);
-#define FMM_WCRT(V, RED, NM) w_crt_kernel<V, RED, NM><<<blocks, 256, 0, s>>>(child, cm, cn, cld, gN, MN, nmod, wp, wr, wc, ea, eb, C, ldc, accumulate)
-#define FMM_WCRT_N(V, RED)                                        \
-    switch (nmod) {                                               \
-        case 12: FMM_WCRT(V, RED, 12); break;                     \
-        case 13: FMM_WCRT(V, RED, 13); break;                     \
-        case 14: FMM_WCRT(V, RED, 14); break;                     \
-        case 15: FMM_WCRT(V, RED, 15); break;                     \
-        case 16: FMM_WCRT(V, RED, 16); break;                     \
-        default: FMM_WCRT(V, RED, 0); break;                      \
-    }
-        if (v4) {
-            if (reduce) { FMM_WCRT_N(4, true) } else { FMM_WCRT_N(4, false) }
-        } else {
-            if (reduce) { FMM_WCRT(1, true, 0); } else { FMM_WCRT(1, false, 0); }
-        }
-#undef FMM_WCRT_N
-#undef FMM_WCRT
-        if ((e = check()) != cudaSuccess) return e;
+    const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(bands, cm));
+    for (int band = 0; band < nb; ++band) {
+        const int64_t r0 = cm * band / nb, nr = cm * (band + 1) / nb - r0;
+        if ((e = w_crt(child + r0 * cld, cm, r0, nr, cm, cn, cld)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -165,6 +165,14 @@ def test_gemm_argument_errors_before_launch():
     assert st == fmm.FMM_ERR_ARG
 
 
+def test_host_pipeline_argument_errors():
+    L = _lib.lib()
+    for bands, gemm_bands in [(-1, 0), (0, -1), (65, 0), (0, 65)]:
+        assert L.fmm_set_host_pipeline(bands, gemm_bands) == fmm.FMM_ERR_ARG
+    assert L.fmm_set_host_pipeline(64, 64) == fmm.FMM_OK
+    assert L.fmm_set_host_pipeline(0, 0) == fmm.FMM_OK
+
+
 def test_write_once_workspace_too_small_is_reported():
     L = _lib.lib()
     p = fmm.Plan("strassen_222_7", levels=1, flags=0)

@@ -189,6 +189,49 @@ def test_host_entry_point():
     assert np.array_equal(Ct.numpy(), oracle.gemm(A, B))
 
 
+@pytest.mark.parametrize("name,levels,m,k,n", [
+    ("strassen_222_7", 1, 4096, 256, 4096),   # C out in 4 row bands of 2 block rows
+    ("fmm_323_15", 1, 4080, 256, 4080),       # 3 uneven bands of 3 block rows
+    ("strassen_222_7", 0, 3000, 300, 2900),   # classical emulation: 2 bands of one block row
+    ("strassen_222_7", 1, 4097, 257, 4095),   # fringe: B awaited up front, C copied out whole
+    ("strassen_222_7", 2, 1000, 512, 900),    # small: one band
+])
+def test_host_entry_point_emulated(name, levels, m, k, n):
+    # the overlapped host path (B copied while the A side runs, C copied out
+    # in bands) gives the device entry point's result bit for bit, exact on
+    # integer inputs, with packed and with strided host buffers
+    import torch
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16")
+    A, B = synth.operands(m, k, n, 14, kind="integer")
+    Cd = fmm.gemm(p, to_dev(A), to_dev(B))
+    torch.cuda.synchronize()
+    Cd = Cd.cpu().numpy()
+    ws = torch.empty(fmm.host_workspace_size(p, m, k, n), dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(5)
+    rows, cols = rng.integers(0, m, 200), rng.integers(0, n, 200)
+    exact, _ = oracle.gemm_entries(A, B, rows, cols)
+    # pipeline depths: from the sizes, none, ragged bands, products in as
+    # many bands as C
+    try:
+        for pad, (bands, gemm_bands) in [(0, (0, 0)), (3, (0, 0)), (0, (1, 1)), (3, (5, 3)), (0, (8, 8))]:
+            fmm.set_host_pipeline(bands, gemm_bands)
+            Ah = torch.zeros((m, k + pad), dtype=torch.float64).pin_memory()
+            Bh = torch.zeros((k, n + pad), dtype=torch.float64).pin_memory()
+            Ch = torch.full((m, n + pad), 7.0, dtype=torch.float64).pin_memory()
+            Ah[:, :k] = torch.from_numpy(A)
+            Bh[:, :n] = torch.from_numpy(B)
+            for _ in range(2):
+                fmm.gemm_host(p, Ah[:, :k], Bh[:, :n], Ch[:, :n], ws)
+                C = Ch[:, :n].numpy()
+                assert np.array_equal(C, Cd)
+                assert np.array_equal(C[rows, cols], exact)
+                assert bool((Ch[:, n:] == 7.0).all())
+                Ch[:, :n] = 0.0
+    finally:
+        fmm.set_host_pipeline(0, 0)
+    fmm.check_device_error()
+
+
 @pytest.mark.parametrize("name,levels", [("strassen_222_7", 3), ("strassen_222_7", 1)])
 def test_full_size_8192_sampled(name, levels):
     # the square 8192^3 workload in the benchmark's launch configuration,
