@@ -54,7 +54,8 @@ EMUL = {"residue_space": fmm.FLAGS_DEFAULT, "per_leaf": fmm.FLAGS_DEFAULT | fmm.
 
 @pytest.mark.parametrize("mode", list(EMUL))
 @pytest.mark.parametrize("name,levels", [("strassen_222_7", 1), ("strassen_222_7", 2), ("fmm_323_15", 1),
-                                         ("fmm_423_20", 1), ("fmm_333_23", 1), ("strassen_222_7", 3)])
+                                         ("fmm_423_20", 1), ("fmm_333_23", 1), ("strassen_222_7", 3),
+                                         ("winograd_222_7", 1), ("winograd_222_7", 2)])
 def test_fast_emulated_integer_exact(name, levels, mode):
     p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", flags=EMUL[mode])
     A, B = synth.operands(261, 517, 259, 44, kind="integer")
@@ -62,11 +63,12 @@ def test_fast_emulated_integer_exact(name, levels, mode):
 
 
 @pytest.mark.parametrize("name,levels", [("strassen_222_7", 1), ("strassen_222_7", 2), ("fmm_333_23", 1),
-                                         ("fmm_323_15", 2)])
+                                         ("fmm_323_15", 2), ("winograd_222_7", 1)])
 def test_fast_residue_space_equals_classical_emulation(name, levels):
     # the recursion over Z/pZ computes the same integer A'B' as the classical
     # emulation, so on the peeled core the two agree bit for bit
-    M, K, N = {"strassen_222_7": (2, 2, 2), "fmm_333_23": (3, 3, 3), "fmm_323_15": (3, 2, 3)}[name]
+    M, K, N = {"strassen_222_7": (2, 2, 2), "fmm_333_23": (3, 3, 3), "fmm_323_15": (3, 2, 3),
+               "winograd_222_7": (2, 2, 2)}[name]
     m, k, n = M ** levels * 70, K ** levels * 150, N ** levels * 60
     A, B = synth.operands(m, k, n, 46)
     fast = run(fmm.Plan(name, levels=levels, precision="ozaki_bf16"), A, B)
