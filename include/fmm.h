@@ -8,8 +8,8 @@
  *     S_r = sum_i U_ir A_i,   T_r = sum_j V_jr B_j,          (Section 3.1)
  *     M_r = S_r T_r,          C_q = sum_r W_qr M_r,
  * and L steps are applied recursively before the classical product takes
- * over at the leaves (Section 3.3).  Dimensions that the block sizes do not
- * divide are handled by peeling (Section 3.4).
+ * over at the leaves (Section 3.4).  Dimensions that the block sizes do not
+ * divide are handled by peeling (Section 3.5).
  *
  * Conventions for every entry point
  *   - Matrices are row-major with a leading dimension (ld >= columns);
@@ -208,7 +208,7 @@ fmm_status fmm_workspace_size(fmm_plan_t plan, int64_t m, int64_t k, int64_t n,
  * row-major; 8-byte aligned.  m, k, n >= 1.  lda >= k, ldb >= n, ldc >= n.
  * The core m' x k' x n' (m' the largest multiple of M^L not above m, etc.)
  * runs the fast algorithm; the rest is added by classical products
- * (Section 3.4):  C[:m',:n'] += A[:m',k':] B[k':,:n'],  C[m':,:] = A[m':,:] B,
+ * (Section 3.5):  C[:m',:n'] += A[:m',k':] B[k':,:n'],  C[m':,:] = A[m':,:] B,
  * C[:m',n':] = A[:m',:] B[:,n'].
  * workspace: device pointer of at least fmm_workspace_size() bytes, 256-byte
  * aligned (may be NULL when that size is 0).

@@ -11,7 +11,7 @@ Contents
   tensor.py                 matmul tensor (Section 2.2.2), exact Brent check
                             (Eq. 2), L-level flattening, Props 2.1 and 2.2
   fastmm.py                 recursive fast multiply, write-once additions,
-                            top-level peeling (Sections 3.1, 3.2, 3.4)
+                            top-level peeling (Sections 3.1, 3.2, 3.5)
   norms.py                  error norms e_F and e_max
   costs.py                  flop, addition and traffic models (Sections 2.1,
                             3.2, 4.2, Table 1)

@@ -68,5 +68,5 @@ def leaf_flops(m, k, n, M, K, N, R, levels):
 
 def omega(base, R):
     """Exponent of a square <b,b,b;R> algorithm: log_b R (e.g. the composed
-    <54,54,54> of Section 6 with R = 40^3 gives 3 log_54 40)."""
+    <54,54,54> of Section 5.2 with R = 40^3 gives 3 log_54 40)."""
     return log(R) / log(base)

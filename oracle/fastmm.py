@@ -5,7 +5,7 @@ target is the classical product (classical.c).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Reading of Section 3.4 (dynamic peeling): the core m' x k' x n' with m' the
+Reading of Section 3.5 (dynamic peeling): the core m' x k' x n' with m' the
 largest multiple of M^L not above m (likewise k', n') goes through the fast
 recursion; the fringe is added with classical products:
     C[:m', :n'] += A[:m', k':] B[k':, :n']

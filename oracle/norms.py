@@ -1,4 +1,4 @@
-"""Oracle: error norms (the paper measures no accuracy, Section 7; these
+"""Oracle: error norms (the paper measures no accuracy, Section 6; these
 are the readings used throughout).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).

@@ -2,7 +2,7 @@
 base case, the number of recursive levels, the execution scheme, the leaf
 tile and the leaf precision.
 
-The paper's rule for recursion (Section 3.3) is the model prior: a recursive
+The paper's rule for recursion (Section 3.4) is the model prior: a recursive
 step only pays while its sub-products stay on the flat part of the classical
 GEMM's performance curve, and the best algorithm depends on the shape
 (Section 5: algorithms that "match the shape" win on rectangular products).

@@ -1,5 +1,5 @@
 // C ABI entry points (include/fmm.h): argument validation, peeling geometry
-// (Section 3.4) and the launch sequence of one fast product.
+// (Section 3.5) and the launch sequence of one fast product.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -589,7 +589,7 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
                 return cuda_status(e);
         }
     }
-    // fringe rows and columns (Section 3.4)
+    // fringe rows and columns (Section 3.5)
     if (g.mp < m &&
         (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
                               FMM_TILE_AUTO, s, launches)) != cudaSuccess)

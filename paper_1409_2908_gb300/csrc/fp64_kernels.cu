@@ -701,7 +701,7 @@ cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int 
     return cudaSuccess;
 }
 
-// Thin classical products (the peeling fringes of Section 3.4: at most
+// Thin classical products (the peeling fringes of Section 3.5: at most
 // M^L - 1 rows or N^L - 1 columns), where a 2-D tile would mostly compute
 // padding.  Both are deterministic: fixed k-slices reduced in a fixed order.
 

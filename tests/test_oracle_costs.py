@@ -43,7 +43,7 @@ def test_traffic_models_strassen():
 
 
 def test_omega_composed_54():
-    # Section 6: <54,54,54> composed from <3,3,6;40> and its permutations
+    # Section 5.2: <54,54,54> composed from <3,3,6;40> and its permutations
     assert costs.omega(54, 40 ** 3) == pytest.approx(3 * math.log(40) / math.log(54))
     # the paper quotes O(N^2.775); 3 log_54 40 = 2.7743.., so that figure is rounded up
     assert costs.omega(54, 40 ** 3) == pytest.approx(2.775, abs=1e-3)

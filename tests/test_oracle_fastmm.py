@@ -1,6 +1,6 @@
 """Pins of the oracle's recursive fast multiply: exact on integers for
 every shipped algorithm and depth, L = 0 is the classical product, and the
-peeled fringe is handled (Sections 3.1, 3.4)."""
+peeled fringe is handled (Sections 3.1, 3.5)."""
 import glob
 import os
 
