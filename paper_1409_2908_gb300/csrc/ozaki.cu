@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(256) res_stream_form(const int8_t *P, int64_t 
 // [r0, r0 + nr) of every block (rows tall); Z points at the first of them in
 // plane 0, and the planes are zr rows apart.
 template <int V, bool REDUCE, int NMOD>
-__global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t rows, int64_t cols, int64_t cld,
+__global__ void __launch_bounds__(256, 4) w_crt_kernel(const int8_t *Z, int64_t rows, int64_t cols, int64_t cld,
                                                     int64_t zr, int64_t r0, int64_t nr, int gridN, int MN, int nmod_rt, const int *w_ptr, const int *w_r,
                                                     const int *w_icoef, const int *ea, const int *eb, double *C,
                                                     int64_t ldc, int accumulate) {
@@ -810,10 +810,16 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
     constexpr int NL = crt_limbs(NMOD);
     __shared__ int2 swt[OZ_MAX_TERMS];   // (child r, coefficient)
     __shared__ int swp[OZ_MAX_R + 1];
+    __shared__ int swsum[OZ_MAX_R];      // sum of the coefficients of each block
     {
         const int nterms = __ldg(w_ptr + MN);
         for (int t = threadIdx.x; t < nterms; t += blockDim.x) swt[t] = make_int2(__ldg(w_r + t), __ldg(w_icoef + t));
         for (int o = threadIdx.x; o <= MN; o += blockDim.x) swp[o] = __ldg(w_ptr + o);
+        for (int o = threadIdx.x; o < MN; o += blockDim.x) {
+            int sum = 0;
+            for (int t = __ldg(w_ptr + o); t < __ldg(w_ptr + o + 1); ++t) sum += __ldg(w_icoef + t);
+            swsum[o] = sum;
+        }
     }
     __syncthreads();
     const int64_t groups = (cols + V - 1) / V;
@@ -832,13 +838,19 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
             for (int l = 0; l < NL; ++l) L[e][l] = 0;
         const int t0 = swp[qb], t1 = swp[qb + 1];
         if (NMOD > 0 && V == 4) {
-            // all moduli of a term loaded together, then combined
+            // All moduli of a term loaded together, then combined two columns
+            // to a 32-bit word: the bytes b (in [-128, 127]) are read offset
+            // as u = b + 128 and paired as u_0 + 2^16 u_1, so one multiply-add
+            // does two columns and, the map being linear, the word ends as
+            // sum w b_0 + 2^16 sum w b_1 once the offsets (128 sum w per
+            // column) are taken off up front.  Both sums lie within 128 sum|w|
+            // <= 2^15 (host-checked), so the two halves separate exactly
+            // (intermediate wrap-around modulo 2^32 cancels).
             constexpr int NQ = NMOD > 0 ? NMOD : 1;
-            int acc[NQ][4];
+            const unsigned bias = 0u - 128u * (unsigned)swsum[qb] * 65537u;
+            unsigned acc[NQ][2];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[q][e] = 0;
+            for (int q = 0; q < NQ; ++q) acc[q][0] = acc[q][1] = bias;
             for (int t = t0; t < t1; ++t) {
                 const int2 wt = swt[t];
                 const int8_t *z = zrow + (int64_t)wt.x * NQ * plane;
@@ -846,15 +858,21 @@ __global__ void __launch_bounds__(256) w_crt_kernel(const int8_t *Z, int64_t row
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) raw[q] = *reinterpret_cast<const unsigned *>(z + q * plane);
 #pragma unroll
-                for (int q = 0; q < NQ; ++q)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[q][e] += wt.y * (int)(int8_t)(raw[q] >> (8 * e));
+                for (int q = 0; q < NQ; ++q) {
+                    const unsigned u = raw[q] ^ 0x80808080u;
+                    acc[q][0] += (unsigned)wt.y * __byte_perm(u, 0u, 0x4140);
+                    acc[q][1] += (unsigned)wt.y * __byte_perm(u, 0u, 0x4342);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NQ; ++q)
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    crt_add(L[e], REDUCE ? bal_small(acc[q][e], q) : acc[q][e], q, NQ);
+                for (int h = 0; h < 2; ++h) {
+                    const int lo = (int)(short)acc[q][h];
+                    const int hi = ((int)acc[q][h] - lo) >> 16;
+                    crt_add(L[2 * h], REDUCE ? bal_small(lo, q) : lo, q, NQ);
+                    crt_add(L[2 * h + 1], REDUCE ? bal_small(hi, q) : hi, q, NQ);
+                }
         } else {
 #pragma unroll 4
             for (int q = 0; q < nmod; ++q) {
@@ -1449,6 +1467,8 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int *wp = rp.L ? rp.w_ptr : id_ptr, *wr = rp.L ? rp.w_r : id_code, *wc = rp.L ? rp.w_icoef : id_coef;
     // |limb sum| <= (sum_t |w_t|) 128 (2^16 - 1) nmod
     const bool reduce = double(rp.L ? rp.w_absmax : 1) * 128.0 * 65535.0 * nmod >= 1073741824.0;
+    // the compiled moduli counts combine two columns per word: |sum w b| <= 128 sum|w| < 2^15
+    const bool packed = (rp.L ? rp.w_absmax : 1) <= 255;
     auto w_crt = [&](const int8_t *z, int64_t zr, int64_t r0, int64_t nr, int64_t cm, int64_t cn,
                      int64_t cld) -> cudaError_t {
         const bool v4 = cld % 4 == 0;
@@ -1464,8 +1484,10 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         case 16: FMM_WCRT(V, RED, 16); break;                     \
         default: FMM_WCRT(V, RED, 0); break;                      \
     }
-        if (v4) {
+        if (v4 && packed) {
             if (reduce) { FMM_WCRT_N(4, true) } else { FMM_WCRT_N(4, false) }
+        } else if (v4) {
+            if (reduce) { FMM_WCRT(4, true, 0); } else { FMM_WCRT(4, false, 0); }
         } else {
             if (reduce) { FMM_WCRT(1, true, 0); } else { FMM_WCRT(1, false, 0); }
         }
