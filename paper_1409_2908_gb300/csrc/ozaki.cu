@@ -373,19 +373,23 @@ __global__ void split_cols_t_i8(const double *Y, int64_t ldy, int64_t rows, int6
 // Column exponents with many threads per column: blockDim.x columns x 8 row
 // groups, reduced through shared memory.
 // grid (ceil(cols/32), leaves); leaf l reads Y + l * leaf_stride.
-__global__ void col_exp_wide(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
+constexpr int COL_EXP_ROWS = 32;
+__global__ void __launch_bounds__(32 * COL_EXP_ROWS) col_exp_wide(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
                              int64_t cols, int beta, int *exps) {
-    __shared__ double part[8][32];
+    // blockDim (32, COL_EXP_ROWS): one column per lane, the rows strided over the warps
+    __shared__ double part[COL_EXP_ROWS][32];
     const int64_t leaf = blockIdx.y;
     const int64_t col = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const double *y = Y + leaf * leaf_stride;
     double mx = 0.0;
-    if (col < cols)
-        for (int64_t i = threadIdx.y; i < rows; i += 8) mx = fmax(mx, fabs(y[i * ldy + col]));
+    if (col < cols) {
+#pragma unroll 4
+        for (int64_t i = threadIdx.y; i < rows; i += COL_EXP_ROWS) mx = fmax(mx, fabs(y[i * ldy + col]));
+    }
     part[threadIdx.y][threadIdx.x] = mx;
     __syncthreads();
     if (threadIdx.y == 0 && col < cols) {
-        for (int r = 1; r < 8; ++r) mx = fmax(mx, part[r][threadIdx.x]);
+        for (int r = 1; r < COL_EXP_ROWS; ++r) mx = fmax(mx, part[r][threadIdx.x]);
         exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
     }
 }
@@ -627,8 +631,16 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
         const int64_t row = (int64_t)(b / gridK) * rows + i;
         const int s = ea[row];
         const double *x = A + row * lda + (int64_t)(b % gridK) * cols + j0;
+        if (j0 + 4 <= cols && ((uintptr_t)x & 15) == 0) {
+            const double2 v0 = reinterpret_cast<const double2 *>(x)[0], v1 = reinterpret_cast<const double2 *>(x)[1];
+            sv[(b * 4 + 0) * 256 + threadIdx.x] = scaled_trunc(v0.x, s);
+            sv[(b * 4 + 1) * 256 + threadIdx.x] = scaled_trunc(v0.y, s);
+            sv[(b * 4 + 2) * 256 + threadIdx.x] = scaled_trunc(v1.x, s);
+            sv[(b * 4 + 3) * 256 + threadIdx.x] = scaled_trunc(v1.y, s);
+        } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = (j0 + e < cols) ? scaled_trunc(x[e], s) : 0;
+            for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = (j0 + e < cols) ? scaled_trunc(x[e], s) : 0;
+        }
     }
     constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
     const int64_t plane = rows * out_ld;
@@ -918,7 +930,19 @@ __global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64
     if (row >= rows) return;
     const double *x = A + row * lda;
     double mx = 0.0;
-    for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+    if (((uintptr_t)x & 15) == 0) {
+        // 16-byte loads where the row starts 16-byte aligned
+        const double2 *x2 = reinterpret_cast<const double2 *>(x);
+        const int64_t c2 = cols / 2;
+#pragma unroll 4
+        for (int64_t j = lane; j < c2; j += 32) {
+            const double2 v = x2[j];
+            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+        }
+        if ((cols & 1) && lane == 0) mx = fmax(mx, fabs(x[cols - 1]));
+    } else {
+        for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+    }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) exps[row] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
 }
@@ -1425,7 +1449,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
             return e;
     }
     if (pipe && pipe->b_ready && (e = cudaStreamWaitEvent(s, pipe->b_ready, 0)) != cudaSuccess) return e;
-    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, 8), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
+    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, COL_EXP_ROWS), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
     if ((e = check()) != cudaSuccess) return e;
     if (fused) {
         if ((e = fused_split(1)) != cudaSuccess) return e;
@@ -1597,7 +1621,7 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
     }
     {
         if (leaves > 65535) return cudaErrorInvalidValue;
-        col_exp_wide<<<dim3((unsigned)((n + 31) / 32), (unsigned)leaves), dim3(32, 8), 0, s>>>(
+        col_exp_wide<<<dim3((unsigned)((n + 31) / 32), (unsigned)leaves), dim3(32, COL_EXP_ROWS), 0, s>>>(
             T, ldt, ts, k, n, beta, eb);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
