@@ -96,13 +96,23 @@ __device__ __forceinline__ int ilog2_abs(double x) {
     return e - 1;
 }
 
+// High word of |x| (sign cleared).  For normal x the largest of these has
+// the exponent field of max |x|, so exponent maxima run on the integer pipe
+// (FP64 max and abs would run on the FP64 pipe, 1/64 of the FP32 rate).
+// Below 2^20 (exponent field 0) every entry seen was zero or subnormal.
+__device__ __forceinline__ unsigned abs_hi(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
+constexpr unsigned OZ_NORMAL_HI = 0x00100000u;
+
 // trunc(x * 2^s) as an integer, by shifting the significand (no FP64 ops).
 __device__ __forceinline__ long long scaled_trunc(double x, int s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int be = int((b >> 52) & 0x7ff);
-    if (be == 0) return 0;   // subnormal or zero: far below 2^-beta of its row maximum
-    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = 52 - (be - 1023) - s;       // value = mant * 2^-sh
+    const unsigned long long frac = b & ((1ull << 52) - 1);
+    if (be == 0 && frac == 0) return 0;
+    // a subnormal is frac 2^-1074: exponent field 1 without the implicit bit
+    // (it matters where a whole row or column is subnormal)
+    const unsigned long long mant = be ? (frac | (1ull << 52)) : frac;
+    const int sh = 52 - ((be ? be : 1) - 1023) - s;   // value = mant * 2^-sh
     long long v;
     if (sh >= 64) v = 0;
     else if (sh >= 0) v = (long long)(mant >> sh);
@@ -203,12 +213,9 @@ __device__ __forceinline__ double round_scale(long long hi_s, unsigned long long
     if (m >> 53) { m >>= 1; ++E; }
     const unsigned long long frac = m & ((1ull << 52) - 1);
     const int be = E - e + 1023;
-    double d;
-    if (be >= 1 && be <= 2046) {
-        d = __longlong_as_double((long long)(((unsigned long long)be << 52) | frac));
-    } else {
-        d = ldexp(__longlong_as_double((long long)(((unsigned long long)(E + 1023) << 52) | frac)), -e);
-    }
+    if (be >= 1 && be <= 2046)   // sign, exponent and fraction assembled as bits (no FP64 op)
+        return __longlong_as_double((long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | frac));
+    const double d = ldexp(__longlong_as_double((long long)(((unsigned long long)(E + 1023) << 52) | frac)), -e);
     return neg ? -d : d;
 }
 
@@ -377,21 +384,43 @@ constexpr int COL_EXP_ROWS = 32;
 __global__ void __launch_bounds__(32 * COL_EXP_ROWS) col_exp_wide(const double *Y, int64_t ldy, int64_t leaf_stride, int64_t rows,
                              int64_t cols, int beta, int *exps) {
     // blockDim (32, COL_EXP_ROWS): one column per lane, the rows strided over the warps
-    __shared__ double part[COL_EXP_ROWS][32];
+    __shared__ unsigned parth[COL_EXP_ROWS][32], partl[COL_EXP_ROWS][32];
+    __shared__ double partd[COL_EXP_ROWS][32];
     const int64_t leaf = blockIdx.y;
     const int64_t col = (int64_t)blockIdx.x * 32 + threadIdx.x;
     const double *y = Y + leaf * leaf_stride;
-    double mx = 0.0;
+    unsigned mh = 0u, lo = 0u;   // max of the high words of |y|, OR of the low words
     if (col < cols) {
 #pragma unroll 4
-        for (int64_t i = threadIdx.y; i < rows; i += COL_EXP_ROWS) mx = fmax(mx, fabs(y[i * ldy + col]));
+        for (int64_t i = threadIdx.y; i < rows; i += COL_EXP_ROWS) {
+            const double v = y[i * ldy + col];
+            mh = max(mh, abs_hi(v));
+            lo |= (unsigned)__double2loint(v);
+        }
     }
-    part[threadIdx.y][threadIdx.x] = mx;
+    parth[threadIdx.y][threadIdx.x] = mh;
+    partl[threadIdx.y][threadIdx.x] = lo;
     __syncthreads();
-    if (threadIdx.y == 0 && col < cols) {
-        for (int r = 1; r < COL_EXP_ROWS; ++r) mx = fmax(mx, part[r][threadIdx.x]);
-        exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+    if (threadIdx.y == 0)
+        for (int r = 1; r < COL_EXP_ROWS; ++r) {
+            mh = max(mh, parth[r][threadIdx.x]);
+            lo |= partl[r][threadIdx.x];
+        }
+    // a column whose largest entry is subnormal: its exact maximum in FP64 (rare)
+    const bool sub = threadIdx.y == 0 && col < cols && mh < OZ_NORMAL_HI && (mh | lo) != 0u;
+    if (__syncthreads_or(sub)) {
+        double mx = 0.0;
+        if (col < cols)
+            for (int64_t i = threadIdx.y; i < rows; i += COL_EXP_ROWS) mx = fmax(mx, fabs(y[i * ldy + col]));
+        partd[threadIdx.y][threadIdx.x] = mx;
+        __syncthreads();
+        if (sub) {
+            for (int r = 1; r < COL_EXP_ROWS; ++r) mx = fmax(mx, partd[r][threadIdx.x]);
+            exps[leaf * cols + col] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+        }
     }
+    if (threadIdx.y == 0 && col < cols && !sub)
+        exps[leaf * cols + col] = (mh | lo) == 0u ? 0 : beta - 1 - (int(mh >> 20) - 1023);
 }
 
 // One recursive level in residue space: child o = s*R + r, modulus q:
@@ -929,7 +958,7 @@ __global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64
     const int lane = threadIdx.x % 32;
     if (row >= rows) return;
     const double *x = A + row * lda;
-    double mx = 0.0;
+    unsigned mh = 0u, lo = 0u;   // max of the high words of |x|, OR of the low words
     if (((uintptr_t)x & 15) == 0) {
         // 16-byte loads where the row starts 16-byte aligned
         const double2 *x2 = reinterpret_cast<const double2 *>(x);
@@ -937,14 +966,30 @@ __global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64
 #pragma unroll 4
         for (int64_t j = lane; j < c2; j += 32) {
             const double2 v = x2[j];
-            mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+            mh = max(mh, max(abs_hi(v.x), abs_hi(v.y)));
+            lo |= (unsigned)__double2loint(v.x) | (unsigned)__double2loint(v.y);
         }
-        if ((cols & 1) && lane == 0) mx = fmax(mx, fabs(x[cols - 1]));
+        if ((cols & 1) && lane == 0) {
+            mh = max(mh, abs_hi(x[cols - 1]));
+            lo |= (unsigned)__double2loint(x[cols - 1]);
+        }
     } else {
-        for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
+        for (int64_t j = lane; j < cols; j += 32) {
+            mh = max(mh, abs_hi(x[j]));
+            lo |= (unsigned)__double2loint(x[j]);
+        }
     }
+    mh = __reduce_max_sync(0xffffffffu, mh);
+    lo = __reduce_or_sync(0xffffffffu, lo);
+    if (mh >= OZ_NORMAL_HI || (mh | lo) == 0u) {
+        if (lane == 0) exps[row] = (mh | lo) == 0u ? 0 : beta - 1 - (int(mh >> 20) - 1023);
+        return;
+    }
+    // the row's largest entry is subnormal: its exact maximum in FP64 (rare)
+    double mx = 0.0;
+    for (int64_t j = lane; j < cols; j += 32) mx = fmax(mx, fabs(x[j]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) exps[row] = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
+    if (lane == 0) exps[row] = beta - 1 - ilog2_abs(mx);
 }
 
 __device__ const int g_ident_ptr[2] = {0, 1};

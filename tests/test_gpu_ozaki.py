@@ -108,3 +108,31 @@ def test_fast_emulated_loguniform(name, levels):
     A, B = synth.operands(M * 90, K * 200, N * 80, 49, kind="loguniform")
     p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=16)
     assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, 16))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 0), ("strassen_222_7", 1), ("fmm_424_26", 1)])
+def test_emulated_zero_and_subnormal_rows_and_columns(name, levels):
+    # row and column exponents on their special cases: all-zero and all
+    # negative-zero rows/columns (exponent 0), rows/columns whose largest
+    # entry is subnormal (the exact FP64 fallback), subnormal entries under a
+    # normal maximum (truncated away); magnitudes keep every result normal
+    rng = np.random.default_rng(50)
+    m, k, n = 256, 320, 192
+    A = rng.uniform(-1, 1, (m, k)) * 1e140
+    B = rng.uniform(-1, 1, (k, n)) * 1e140
+    A[3] = 0.0
+    A[5] = rng.uniform(-1, 1, k) * 1e-310
+    A[7] = rng.uniform(-1, 1, k) * 1e-310
+    A[7, 10] = 0.5e140
+    A[9] = -0.0
+    B[:, 4] = 0.0
+    B[:, 6] = rng.uniform(-1, 1, k) * 1e-310
+    B[:, 8] = rng.uniform(-1, 1, k) * 1e-310
+    B[11, 8] = -0.25e140
+    B[:, 12] = -0.0
+    assert np.all(np.abs(A[5]) < 2.3e-308) and np.any(A[5] != 0)
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=13)
+    C = run(p, A, B)
+    assert np.array_equal(C, ozaki.emulated_gemm(A, B, 13))
+    assert np.all(C[3] == 0) and np.all(C[:, 4] == 0)
+    assert np.all(np.isfinite(C))
