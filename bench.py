@@ -331,7 +331,7 @@ def main():
     ap.add_argument("--no-classical", action="store_true", help="skip the FP64 classical comparator")
     ap.add_argument("--all-schemes", action="store_true", help="try every FP64 execution scheme")
     ap.add_argument("--precisions", default="fp64,ozaki_bf16",
-                    help="comma list of leaf precisions to try: fp64, ozaki_bf16")
+                    help="comma list of leaf precisions to try: fp64, ozaki_bf16, tf32, fp32")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -532,15 +532,18 @@ def main():
                 "peak_source": "FP64 DFMA pipe: 152 SMs x 4 flop/clk x 2.07 GHz (recipe unit counts and clocks)",
                 "algorithmic_flops_per_launch": leaf_flops, "leaf_ms_avg": leaf_avg,
                 "leaf_share_of_step": leaf_avg / ms_step}
-    elif p.precision == "tf32":
+    elif p.precision in ("tf32", "fp32"):
+        # fp32: three TF32 pair products per leaf in one launch (K tripled)
+        split = 3 if p.precision == "fp32" else 1
         kpad = -(-kL // 32) * 32
-        leaf_flops = 2.0 * info["leaves"] * mL * kpad * nL
+        leaf_flops = 2.0 * info["leaves"] * mL * kpad * split * nL
         achieved = leaf_flops / leaf_avg / 1e9
         peak, src = measured_bf16_peak()
         peak, src = peak / 2.0, src + " x 1/2 (tf32 = half the bf16 rate, recipe nominal ratio)"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
-                "kernel": "tf32_gemm (tcgen05 kind::tf32, all leaves)",
+                "kernel": ("tf32_gemm (tcgen05 kind::tf32, all leaves" +
+                           (", hi/lo TF32 pairs: 3 products per leaf)" if split == 3 else ")")),
                 "peak_source": src, "algorithmic_flops_per_launch": leaf_flops,
                 "leaf_ms_avg": leaf_avg, "leaf_share_of_step": leaf_avg / ms_step}
     else:
@@ -561,7 +564,8 @@ def main():
 
     # the fastest FP64 fast plan within the target, against the FP64 classical GEMM
     fp64_cands = [r for r in results if r["plan"] != "classical" and "ozaki" not in r["plan"]
-                  and "tf32" not in r["plan"] and (r["rel_err_F"] is None or r["rel_err_F"] <= args.tol)]
+                  and "tf32" not in r["plan"] and "fp32" not in r["plan"]
+                  and (r["rel_err_F"] is None or r["rel_err_F"] <= args.tol)]
     fb = min(fp64_cands, key=lambda r: r["ms"], default=None)
     fp64_best = ({"plan": fb["plan"], "value": fb["tflops"], "rel_err_F": fb["rel_err_F"],
                   "speedup_vs_classical_fp64": (ms_c / fb["ms"]) if ms_c else None} if fb else None)
@@ -570,7 +574,8 @@ def main():
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate)"}.get(
+            "dtype": {"fp64": "f64", "tf32": "tf32 (fp32 accumulate)",
+                      "fp32": "tf32 hi/lo pairs, 3 products (fp32 accumulate)"}.get(
                 p.precision, f"bf16 residues x {p.moduli or args.moduli} (CRT-emulated f64)"),
             "data": "synthetic uniform[-1,1] (PCG64 seed 1410)",
             "config": {"workload": wl["desc"], "m": m, "k": k, "n": n, "plan": best["plan"],

@@ -65,7 +65,14 @@ typedef enum {
        10-bit significand, FP32 accumulation), widened to FP64 for the W
        combination; S/T formation and the fringe stay FP64.  Relative error
        of order 2^-11 per leaf operand. */
-    FMM_PREC_TF32 = 2
+    FMM_PREC_TF32 = 2,
+    /* FP32-accurate leaf products on the same TF32 tensor path: each leaf
+       operand x (taken in FP32) is split into x_hi = tf32(x) and x_lo =
+       tf32(x - x_hi), and one product over three K segments sums
+       S_hi T_hi + S_hi T_lo + S_lo T_hi with FP32 accumulation (three times
+       the TF32 work; the dropped S_lo T_lo is 2^-22 relative).  S/T
+       formation, the W combination and the fringe stay FP64. */
+    FMM_PREC_FP32 = 1
 } fmm_precision;
 
 /* Execution-scheme flags (fmm_plan_create / fmm_plan_load `flags`). */

@@ -21,7 +21,9 @@ FMM_ERR_TIMEOUT = -6
 FMM_PREC_FP64 = 0
 FMM_PREC_OZAKI_BF16 = 3
 FMM_PREC_TF32 = 2
-PRECISIONS = {"fp64": FMM_PREC_FP64, "ozaki_bf16": FMM_PREC_OZAKI_BF16, "tf32": FMM_PREC_TF32}
+FMM_PREC_FP32 = 1
+PRECISIONS = {"fp64": FMM_PREC_FP64, "ozaki_bf16": FMM_PREC_OZAKI_BF16, "tf32": FMM_PREC_TF32,
+              "fp32": FMM_PREC_FP32}
 FLAG_FUSED_ST = 1
 FLAG_FUSED_W = 2
 FLAG_LEVELWISE = 4

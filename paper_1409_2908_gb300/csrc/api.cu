@@ -111,6 +111,11 @@ struct WsLayout {
     std::vector<size_t> lvS, lvT, lvP;
 };
 
+// Leaf products on the TF32 tensor path: one TF32 product per leaf, or three
+// (TF32 pairs) for FP32 accuracy.
+bool tf32_family(const fmm_plan *p) { return p->prec == FMM_PREC_TF32 || p->prec == FMM_PREC_FP32; }
+int tf32_split(const fmm_plan *p) { return p->prec == FMM_PREC_FP32 ? 3 : 1; }
+
 // The whole recursion runs on residues when the base coefficients are
 // integers (the plan layer checks) and per-leaf emulation was not asked for.
 bool residue_space(const fmm_plan *p) {
@@ -150,11 +155,11 @@ ResPlan res_plan(const fmm_plan *p) {
 
 WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     WsLayout w;
-    const bool tf = p->prec == FMM_PREC_TF32;
+    const bool tf = tf32_family(p);
     const bool oz = p->prec == FMM_PREC_OZAKI_BF16 || tf;
     if (tf && p->L == 0) {
         w.oz = 0;
-        w.total = tf32_workspace(1, g.mp, g.kp, g.np);
+        w.total = tf32_workspace(1, g.mp, g.kp, g.np, tf32_split(p));
         return w;
     }
     if (!tf && oz && p->L > 0 && g.fast && residue_space(p)) {
@@ -208,7 +213,7 @@ WsLayout ws_layout(const fmm_plan *p, const Geometry &g) {
     }
     if (oz) {
         w.oz = off;
-        off = align256(off + (tf ? tf32_workspace(p->leaves, g.mL, g.kL, g.nL)
+        off = align256(off + (tf ? tf32_workspace(p->leaves, g.mL, g.kL, g.nL, tf32_split(p))
                                  : ozaki_workspace(p->leaves, p->nmod, g.mL, g.kL, g.nL)));
     }
     w.total = off;
@@ -355,15 +360,15 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     cudaError_t e;
     // the overlap hooks reach only the residue-space path without a fringe
     const bool fringe = g.mp < m || g.kp < k || g.np < n;
-    if (p->prec == FMM_PREC_TF32 || (p->L > 0 && (!residue_space(p) || fringe)))
+    if (tf32_family(p) || (p->L > 0 && (!residue_space(p) || fringe)))
         if ((e = settle_pipe(pipe, s)) != cudaSuccess) return cuda_status(e);
     // (the timing pair, when enabled, brackets the tensor-core GEMM inside)
-    const bool tf = p->prec == FMM_PREC_TF32;
+    const bool tf = tf32_family(p);
     auto leaf_products = [&](const double *S_, int64_t lds, int64_t ss, const double *T_, int64_t ldt,
                              int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
                              int64_t mm, int64_t kk, int64_t nn) {
         return tf ? tf32_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, 0,
-                                  wsb + wl.oz, s, launches)
+                                  wsb + wl.oz, s, launches, tf32_split(p))
                   : ozaki_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, p->nmod,
                                    wsb + wl.oz, s, launches);
     };
@@ -445,7 +450,7 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
                     size_t ws_bytes, cudaStream_t s, int *launches, const HostPipe *pipe = nullptr) {
     const Geometry g = geometry(p, m, k, n);
-    const bool emulated = (p->prec == FMM_PREC_OZAKI_BF16 || p->prec == FMM_PREC_TF32) && (p->L == 0 || g.fast);
+    const bool emulated = (p->prec == FMM_PREC_OZAKI_BF16 || tf32_family(p)) && (p->L == 0 || g.fast);
     if (!emulated) {
         const cudaError_t pe = settle_pipe(pipe, s);
         if (pe != cudaSuccess) return cuda_status(pe);
@@ -627,7 +632,7 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (M < 1 || K < 1 || N < 1 || R < 1 || R > 4096) return FMM_ERR_ARG;
     if (int64_t(M) * K * K * N * M * N > (int64_t(1) << 22)) return FMM_ERR_UNSUPPORTED;
     if (levels < 0 || levels > 6) return FMM_ERR_ARG;
-    if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16 && prec != FMM_PREC_TF32)
+    if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16 && prec != FMM_PREC_TF32 && prec != FMM_PREC_FP32)
         return FMM_ERR_UNSUPPORTED;
     if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE |
                           FMM_FLAG_LEAF_EMULATION))
@@ -687,7 +692,7 @@ fmm_status fmm_plan_prepare(fmm_plan_t p) {
     fmm_status st = ensure_uploaded(p);
     if (st != FMM_OK) return st;
     if (p->prec == FMM_PREC_OZAKI_BF16 && ozaki_prepare(p->nmod) != cudaSuccess) return FMM_ERR_CUDA;
-    if (p->prec == FMM_PREC_TF32 && tf32_prepare() != cudaSuccess) return FMM_ERR_CUDA;
+    if (tf32_family(p) && tf32_prepare() != cudaSuccess) return FMM_ERR_CUDA;
     if (prepare_fp64_kernels() != cudaSuccess) return FMM_ERR_CUDA;
     return FMM_OK;
 }

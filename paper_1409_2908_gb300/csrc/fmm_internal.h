@@ -154,12 +154,13 @@ cudaError_t read_device_error(int *flag, bool clear);
 cudaError_t ozaki_prepare(int nmod);          // constant tables, kernel attributes
 cudaError_t prepare_fp64_kernels();           // kernel attributes of every tile
 // tf32.cu
-size_t tf32_workspace(int64_t leaves, int64_t m, int64_t k, int64_t n);
+size_t tf32_workspace(int64_t leaves, int64_t m, int64_t k, int64_t n, int split = 1);
 cudaError_t tf32_prepare();
 cudaError_t read_tf32_error(int *flag, bool clear);
 cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
-                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches);
+                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
+                          int split = 1);
 // residue-space recursion (integer base coefficients only)
 struct ResPlan {
     int M, K, N, R, L;

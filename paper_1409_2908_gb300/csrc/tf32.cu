@@ -1,4 +1,5 @@
-// TF32 leaf products on the tensor cores (precision variant FMM_PREC_TF32):
+// TF32 leaf products on the tensor cores (precision variants FMM_PREC_TF32
+// and, with three TF32 pair products per leaf, FMM_PREC_FP32):
 // the FP64 leaf operands S_r, T_r are rounded to TF32 (10-bit significand,
 // round to nearest) in FP32 K-major layout, multiplied by tcgen05
 // (kind::tf32, FP32 accumulation in TMEM over the whole k), and the FP32
@@ -205,39 +206,76 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TB_TBUF * BN) : "memory");
 }
 
-__device__ __forceinline__ float to_tf32(double x) {
-    float f = (float)x;
+__device__ __forceinline__ float to_tf32(float f) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
     return __uint_as_float(r);
 }
 
-// X (rows x cols per plane, ld, plane stride) -> TF32 in FP32, rows padded to kpad.
+// The TF32 pair of x: hi = tf32(x) and lo = tf32(x - hi), x taken in FP32
+// (hi + lo carries 22 significant bits of it).
+__device__ __forceinline__ float2 tf32_pair(double x) {
+    const float f = (float)x;
+    const float hi = to_tf32(f);
+    return make_float2(hi, to_tf32(f - hi));
+}
+
+// X (rows x cols per plane, ld, plane stride) -> TF32 in FP32, rows padded to
+// kpad.  split 3 (FP32-accurate products): each row holds three segments of
+// kpad, hi | hi | lo, against hi | lo | hi on the T side, so one product over
+// 3 kpad sums hi hi + hi lo + lo hi (the lo lo term, 2^-22 relative, is left out).
 __global__ void tf32_rows(const double *X, int64_t ldx, int64_t xs, int64_t rows, int64_t cols,
-                          int64_t kpad, int64_t planes, float *out) {
-    const int64_t total = planes * rows * kpad;
+                          int64_t kpad, int64_t planes, int split, float *out) {
+    const int64_t kk = kpad * split;
+    const int64_t total = planes * rows * kk;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t pl = g / (rows * kpad), rem = g % (rows * kpad), i = rem / kpad, j = rem % kpad;
-        out[g] = j < cols ? to_tf32(X[pl * xs + i * ldx + j]) : 0.0f;
+        const int64_t pl = g / (rows * kk), rem = g % (rows * kk), i = rem / kk, jj = rem % kk;
+        const int64_t seg = jj / kpad, j = jj % kpad;
+        float v = 0.0f;
+        if (j < cols) {
+            const double x = X[pl * xs + i * ldx + j];
+            if (split == 1) {
+                v = to_tf32((float)x);
+            } else {
+                const float2 hl = tf32_pair(x);
+                v = seg == 2 ? hl.y : hl.x;
+            }
+        }
+        out[g] = v;
     }
 }
 
-// Y (rows x cols per plane) -> TF32 of Y^T (cols x kpad), through 32x32 tiles.
+// Y (rows x cols per plane) -> TF32 of Y^T (cols x split kpad), through 32x32
+// tiles; split 3: segments hi | lo | hi of each row of Y^T.
 __global__ void tf32_cols_t(const double *Y, int64_t ldy, int64_t ys, int64_t rows, int64_t cols,
-                            int64_t kpad, float *out) {
-    __shared__ float tile[32][33];
+                            int64_t kpad, int split, float *out) {
+    __shared__ float tile[32][33], tile_lo[32][33];
     const int64_t pl = blockIdx.z;
     const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int r = ty; r < 32; r += 8) {
         const int64_t i = i0 + r, j = j0 + tx;
-        tile[r][tx] = (i < rows && j < cols) ? to_tf32(Y[pl * ys + i * ldy + j]) : 0.0f;
+        float2 hl = make_float2(0.0f, 0.0f);
+        if (i < rows && j < cols) {
+            const double y = Y[pl * ys + i * ldy + j];
+            hl = split == 1 ? make_float2(to_tf32((float)y), 0.0f) : tf32_pair(y);
+        }
+        tile[r][tx] = hl.x;
+        tile_lo[r][tx] = hl.y;
     }
     __syncthreads();
+    const int64_t kk = kpad * split;
     for (int r = ty; r < 32; r += 8) {
         const int64_t j = j0 + r, i = i0 + tx;
-        if (j < cols && i < kpad) out[(pl * cols + j) * kpad + i] = tile[tx][r];
+        if (j < cols && i < kpad) {
+            float *o = out + (pl * cols + j) * kk + i;
+            o[0] = tile[tx][r];
+            if (split == 3) {
+                o[kpad] = tile_lo[tx][r];
+                o[2 * kpad] = tile[tx][r];
+            }
+        }
     }
 }
 
@@ -281,10 +319,10 @@ int sm_count() {
 
 }  // namespace
 
-size_t tf32_workspace(int64_t leaves, int64_t m, int64_t k, int64_t n) {
-    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K;
+size_t tf32_workspace(int64_t leaves, int64_t m, int64_t k, int64_t n, int split) {
+    const int64_t kk = (k + TB_K - 1) / TB_K * TB_K * split;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    return al(size_t(leaves) * m * kpad * 4) + al(size_t(leaves) * n * kpad * 4);
+    return al(size_t(leaves) * m * kk * 4) + al(size_t(leaves) * n * kk * 4);
 }
 
 cudaError_t tf32_prepare() {
@@ -315,46 +353,49 @@ cudaError_t read_tf32_error(int *flag, bool clear) {
     return e;
 }
 
-// Out[leaf] (m x n, ldo, leaf stride os) (+)= tf32(S[leaf]) tf32(T[leaf]).
+// Out[leaf] (m x n, ldo, leaf stride os) (+)= tf32(S[leaf]) tf32(T[leaf]);
+// split 3: the FP32-accurate sum of the three TF32 pair products.
 cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
-                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches) {
+                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
+                          int split) {
+    if (split != 1 && split != 3) return cudaErrorInvalidValue;
     cudaError_t e = tf32_prepare();
     if (e != cudaSuccess) return e;
     int *err = nullptr;
     if ((e = cudaGetSymbolAddress((void **)&err, g_tf32_error)) != cudaSuccess) return e;
-    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K;
+    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K, kk = kpad * split;
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     float *fa = (float *)ws;
-    float *fb = (float *)((char *)ws + al(size_t(leaves) * m * kpad * 4));
+    float *fb = (float *)((char *)ws + al(size_t(leaves) * m * kk * 4));
     {
-        const int64_t total = leaves * m * kpad;
+        const int64_t total = leaves * m * kk;
         const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-        tf32_rows<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, fa);
+        tf32_rows<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, split, fa);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         if (leaves > 65535) return cudaErrorInvalidValue;
         dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
-        tf32_cols_t<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, fb);
+        tf32_cols_t<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, split, fb);
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     CUtensorMap ta, tb;
     const bool wide = n >= 256;
     const int bn = wide ? 256 : 128;
-    if ((e = map3d_f32(&ta, fa, kpad, m, leaves, TB_M)) != cudaSuccess) return e;
-    if ((e = map3d_f32(&tb, fb, kpad, n, leaves, bn)) != cudaSuccess) return e;
+    if ((e = map3d_f32(&ta, fa, kk, m, leaves, TB_M)) != cudaSuccess) return e;
+    if ((e = map3d_f32(&tb, fb, kk, n, leaves, bn)) != cudaSuccess) return e;
     const int64_t tm = (m + TB_M - 1) / TB_M, tn = (n + bn - 1) / bn;
     const int64_t tiles = tm * tn * leaves;
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, sm_count());
     cudaEvent_t t0 = timing_mark(s);
     if (wide)
-        tf32_gemm<256><<<ctas, tf_threads<256>(), tf_smem<256>(), s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm),
+        tf32_gemm<256><<<ctas, tf_threads<256>(), tf_smem<256>(), s>>>(ta, tb, Out, m, n, int(kk / TB_K), int(tm),
                                                                        int(tn), tiles, ldo, os, accumulate, err);
     else
-        tf32_gemm<128><<<ctas, tf_threads<128>(), tf_smem<128>(), s>>>(ta, tb, Out, m, n, int(kpad / TB_K), int(tm),
+        tf32_gemm<128><<<ctas, tf_threads<128>(), tf_smem<128>(), s>>>(ta, tb, Out, m, n, int(kk / TB_K), int(tm),
                                                                        int(tn), tiles, ldo, os, accumulate, err);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -1,7 +1,8 @@
-"""The TF32 precision variant (tensor-core leaf products with operands rounded
-to TF32): exact on small integer inputs (they are representable in TF32 and
-every partial sum is exact in FP32), and within the TF32 rounding bound of
-the FP64 oracle on random inputs, alone and under the fast recursion."""
+"""The TF32 precision variants (tensor-core leaf products with operands
+rounded to TF32, and the FP32-accurate variant summing three TF32 pair
+products): exact on small integer inputs (they are representable in TF32 and
+every partial sum is exact in FP32), and within their rounding bounds of the
+FP64 oracle on random inputs, alone and under the fast recursion."""
 import numpy as np
 import pytest
 
@@ -45,3 +46,48 @@ def test_tf32_uniform_within_rounding_bound(name, levels):
         bound = (2.0 ** -10 + k * 2.0 ** -23) * (np.abs(A) @ np.abs(B))
         assert np.all(np.abs(C - ref) <= bound)
     assert norms.rel_frobenius(C, ref) <= 2e-3
+
+
+# FP32-accurate leaves: each operand split into a TF32 pair (hi, lo), three
+# pair products summed in one tensor-core product over a tripled k
+
+@pytest.mark.parametrize("name,levels,shape", [("strassen_222_7", 0, (200, 300, 130)),
+                                               ("strassen_222_7", 0, (1, 1, 1)),
+                                               ("strassen_222_7", 1, (257, 515, 259)),
+                                               ("winograd_222_7", 2, (300, 260, 290)),
+                                               ("fmm_323_15", 1, (301, 200, 303))])
+def test_fp32_integer_exact(name, levels, shape):
+    # small integers are their own hi part (lo = 0) and every sum is exact in FP32
+    p = fmm.Plan(name, levels=levels, precision="fp32")
+    A, B = synth.operands(*shape, 63, kind="integer")
+    assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 0), ("strassen_222_7", 1), ("strassen_222_7", 2)])
+def test_fp32_uniform_within_rounding_bound(name, levels):
+    m, k, n = 256, 1024, 192
+    A, B = synth.operands(m, k, n, 64)
+    ref = oracle.gemm(A, B)
+    C = run(fmm.Plan(name, levels=levels, precision="fp32"), A, B)
+    if levels == 0:
+        # operands to FP32 (2^-24), the pair keeps 22 bits of it (2^-22 per
+        # operand), lo x lo dropped (2^-22), FP32 accumulation over 3k terms
+        # (one unit in the last place per addition, as for TF32 above)
+        bound = (4 * 2.0 ** -22 + 3 * k * 2.0 ** -23) * (np.abs(A) @ np.abs(B))
+        assert np.all(np.abs(C - ref) <= bound)
+    # e_F is set by the tensor core's FP32 accumulation over the tripled k
+    # (1.06e-5 measured at 0 levels: between round-to-nearest and truncating
+    # summation of 3k terms), not by the operand splitting
+    e = norms.rel_frobenius(C, ref)
+    assert e <= 3e-5
+    # and an order of magnitude more accurate than one TF32 product
+    e_tf = norms.rel_frobenius(run(fmm.Plan(name, levels=levels, precision="tf32"), A, B), ref)
+    assert e * 10 < e_tf
+
+
+def test_fp32_loguniform():
+    # magnitudes over eight decades: relative accuracy per element, not per norm
+    A, B = synth.operands(128, 512, 96, 65, kind="loguniform")
+    C = run(fmm.Plan("strassen_222_7", levels=1, precision="fp32"), A, B)
+    ref = oracle.gemm(A, B)
+    assert np.all(np.abs(C - ref) <= (1e-5 + 512 * 2.0 ** -22) * (np.abs(A) @ np.abs(B)))
