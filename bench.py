@@ -474,9 +474,10 @@ def main():
         Ch = torch.empty((m, n), dtype=torch.float64).pin_memory()
         hws = torch.empty(fmm.host_workspace_size(p, m, k, n), dtype=torch.uint8, device="cuda")
         fe = (lambda: fmm.gemm_host(p, Ah, Bh, Ch, hws, stream=stream))
-        # the same warm-up as the device steps: the first calls after a long
-        # stretch of heavy load run slower while the GPU's power state settles
-        for _ in range(max(args.warmup, 1)):
+        # warm-up: the first calls after a long stretch of heavy load (the
+        # device steps) run slower for about the first ten calls, so at least
+        # ten untimed calls before the timed ones
+        for _ in range(max(args.warmup, 10)):
             fe()
         sync_all(torch, ws)
         t0 = time.perf_counter()
