@@ -6,6 +6,11 @@
 // products are widened back to FP64 for the W combination.  Expected
 // relative error ~ 2^-11 per operand; stated per result by the benchmark.
 //
+// The FP32-accurate variant splits each operand into a TF32 pair and sums
+// the three pair products in one launch over a tripled k, in chunks of 512 k
+// (x3) that the drain warps add in FP32 registers (the tensor core's own FP32
+// sums over a long k lose accuracy; see tf32_gemm<BN, true>).
+//
 // Same pipeline as the emulated-FP64 residue GEMM: persistent CTAs over
 // 128 x 256 tiles (128 x 128 for narrow products) in groups of 16 tile rows,
 // TMA (128-byte swizzle) into an mbarrier ring, one load thread, one MMA
@@ -41,8 +46,12 @@ struct TfCfg<256> { static constexpr int DW = 8, STAGES = 4; };
 template <>
 struct TfCfg<128> { static constexpr int DW = 4, STAGES = 6; };
 constexpr int TB_TBUF = 2;
-template <int BN>
-constexpr int tf_threads() { return (TfCfg<BN>::DW + 2) * 32; }
+// CH (k in chunks summed in drain-warp registers): twice the drain warps, so
+// that each holds the running sums of 64 columns
+template <int BN, bool CH>
+__host__ __device__ constexpr int tf_dw() { return TfCfg<BN>::DW * (CH ? 2 : 1); }
+template <int BN, bool CH>
+constexpr int tf_threads() { return (tf_dw<BN, CH>() + 2) * 32; }
 template <int BN>
 constexpr int tf_smem() { return TfCfg<BN>::STAGES * (TB_A + BN * TB_K * 4) + 1024 + 256; }
 
@@ -61,12 +70,13 @@ __device__ __forceinline__ void tf_tile(int64_t tile, int64_t per_plane, int til
     tm = tm0 + within % gsz;
 }
 
-template <int BN>
-__global__ void __launch_bounds__(tf_threads<BN>(), 1)
+template <int BN, bool CH>
+__global__ void __launch_bounds__(tf_threads<BN, CH>(), 1)
 tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          double *Out, int64_t m, int64_t n, int kblocks, int tiles_m, int tiles_n,
+          double *Out, int64_t m, int64_t n, int kblocks, int chunk_kb, int tiles_m, int tiles_n,
           int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err) {
-    constexpr int DW = TfCfg<BN>::DW, STAGES = TfCfg<BN>::STAGES;
+    constexpr int DW = tf_dw<BN, CH>(), STAGES = TfCfg<BN>::STAGES;
+    constexpr int CW = 4 * BN / DW;   // accumulator columns per drain warp
     constexpr int TB_B = BN * TB_K * 4, STAGE = TB_A + TB_B;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -77,6 +87,9 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     uint32_t *tmem_slot = (uint32_t *)(tempty + TB_TBUF);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t per_plane = (int64_t)tiles_m * tiles_n;
+    // k in chunks of chunk_kb blocks: each chunk is summed in TMEM and added
+    // to the drain warps' FP32 registers (round to nearest) before the next
+    const int nchunks = (kblocks + chunk_kb - 1) / chunk_kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -120,83 +133,124 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TB_M >> 4) << 24);
             bool ok = true;
-            int64_t g = 0, it = 0;
-            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
-                const int b = int(it % TB_TBUF);
-                if (it >= TB_TBUF && !mbar_wait(&tempty[b], uint32_t(((it / TB_TBUF) - 1) & 1))) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t acc = tmem + (uint32_t)(b * BN);
-                for (int kb = 0; kb < kblocks; ++kb, ++g) {
-                    const int s = int(g % STAGES);
-                    if (!mbar_wait(&full[s], uint32_t((g / STAGES) & 1))) { ok = false; break; }
+            int64_t g = 0, cg = 0;   // global k-block and chunk counters
+            for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                int kb = 0;
+                for (int c = 0; c < nchunks && ok; ++c, ++cg) {
+                    const int b = int(cg % TB_TBUF);
+                    if (cg >= TB_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / TB_TBUF) - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a0 = su32(smem + s * STAGE), b0 = a0 + TB_A;
+                    const uint32_t acc = tmem + (uint32_t)(b * BN);
+                    const int kend = min(kblocks, (c + 1) * chunk_kb);
+                    for (int first = 1; kb < kend; ++kb, ++g, first = 0) {
+                        const int s = int(g % STAGES);
+                        if (!mbar_wait(&full[s], uint32_t((g / STAGES) & 1))) { ok = false; break; }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a0 = su32(smem + s * STAGE), b0 = a0 + TB_A;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)   // K = 8 tf32 (32 bytes) per MMA
-                        mma_tf32(acc, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
-                                 (kb == 0 && kk == 0) ? 0u : 1u);
-                    mma_commit(&empty[s]);
+                        for (int kk = 0; kk < 4; ++kk)   // K = 8 tf32 (32 bytes) per MMA
+                            mma_tf32(acc, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc,
+                                     (first && kk == 0) ? 0u : 1u);
+                        mma_commit(&empty[s]);
+                    }
+                    mma_commit(&tfull[b]);
                 }
-                mma_commit(&tfull[b]);
             }
             if (!ok) atomicExch(err, 1);
         }
     } else {
         // drain warps: warp w reads TMEM lanes 32*(w%4)..+31 (rows of the tile)
-        // and the 128-column slice w/4 of the accumulator
+        // and the CW-column slice w/4 of the accumulator
         const int lg = warp % 4, ch = warp / 4;
         bool ok = true;
-        int64_t it = 0;
-        for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x, ++it) {
+        int64_t cg = 0;
+        for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
             int z, tm, tn;
             tf_tile(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
-            const int b = int(it % TB_TBUF);
-            if (!mbar_wait(&tfull[b], uint32_t((it / TB_TBUF) & 1))) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * 128);
             const int64_t row = (int64_t)tm * TB_M + lg * 32 + lane;
-            const int64_t col0 = (int64_t)tn * BN + ch * 128;
-            const int64_t cols = min((int64_t)128, n - col0);
+            const int64_t col0 = (int64_t)tn * BN + ch * CW;
+            const int64_t cols = min((int64_t)CW, n - col0);
             double *out = Out + (int64_t)z * out_stride + row * ldo + col0;
             const bool pairs = ((((uintptr_t)out) & 15) == 0);
+            // 16 accumulated columns from c0 on, widened to FP64 and stored (added)
+            auto store16 = [&](int c0, const float *v16) {
+                if (row >= m || c0 >= cols) return;
+                if (pairs && c0 + 16 <= cols) {
+                    // 16 consecutive columns as eight 16-byte stores
 #pragma unroll
-            for (int c0 = 0; c0 < 128; c0 += 16) {
-                uint32_t r[16];
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                               "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                             : "r"(base + (uint32_t)c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < m && c0 < cols) {
-                    if (pairs && c0 + 16 <= cols) {
-                        // 16 consecutive columns as eight 16-byte stores
-#pragma unroll
-                        for (int j = 0; j < 16; j += 2) {
-                            double2 v = make_double2((double)__uint_as_float(r[j]), (double)__uint_as_float(r[j + 1]));
-                            double2 *dst = reinterpret_cast<double2 *>(out + c0 + j);
-                            if (accumulate) {
-                                const double2 o = *dst;
-                                v.x += o.x;
-                                v.y += o.y;
-                            }
-                            *dst = v;
+                    for (int j = 0; j < 16; j += 2) {
+                        double2 v = make_double2((double)v16[j], (double)v16[j + 1]);
+                        double2 *dst = reinterpret_cast<double2 *>(out + c0 + j);
+                        if (accumulate) {
+                            const double2 o = *dst;
+                            v.x += o.x;
+                            v.y += o.y;
                         }
-                    } else {
+                        *dst = v;
+                    }
+                } else {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (c0 + j < cols) {
-                                const double v = (double)__uint_as_float(r[j]);
-                                out[c0 + j] = accumulate ? out[c0 + j] + v : v;
-                            }
+                    for (int j = 0; j < 16; ++j) {
+                        if (c0 + j < cols) {
+                            const double v = (double)v16[j];
+                            out[c0 + j] = accumulate ? out[c0 + j] + v : v;
                         }
                     }
                 }
+            };
+            if constexpr (!CH) {
+                // the whole k summed in TMEM: one drain per tile
+                const int b = int(cg % TB_TBUF);
+                if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1))) { ok = false; break; }
+                ++cg;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * CW);
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 16) {
+                    uint32_t r[16];
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                 : "r"(base + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    float v16[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v16[j] = __uint_as_float(r[j]);
+                    store16(c0, v16);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&tempty[b]);
+            } else {
+                // chunks of k summed in TMEM, added here in FP32 (round to nearest)
+                float acc[CW];
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[j] = 0.0f;
+                for (int c = 0; c < nchunks; ++c, ++cg) {
+                    const int b = int(cg % TB_TBUF);
+                    if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1))) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * CW);
+#pragma unroll
+                    for (int c0 = 0; c0 < CW; c0 += 16) {
+                        uint32_t r[16];
+                        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                                       "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                                     : "r"(base + (uint32_t)c0));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(r[j]);
+                    }
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&tempty[b]);
+                }
+                if (!ok) break;
+#pragma unroll
+                for (int c0 = 0; c0 < CW; c0 += 16) store16(c0, acc + c0);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&tempty[b]);
         }
         if (!ok && lane == 0) atomicExch(err, 1);
     }
@@ -331,10 +385,11 @@ cudaError_t tf32_prepare() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 64 && !configured[dev]) {
-        if ((e = cudaFuncSetAttribute(tf32_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      tf_smem<256>())) != cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(tf32_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if ((e = cudaFuncSetAttribute(tf32_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<256>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tf32_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<128>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tf32_gemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       tf_smem<128>())) != cudaSuccess)
             return e;
         configured[dev] = true;
@@ -383,20 +438,28 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     CUtensorMap ta, tb;
-    const bool wide = n >= 256;
+    // the chunked sums (FP32-accurate products) keep 64 running sums per drain
+    // thread: 128-wide tiles with 8 drain warps fit them in registers
+    const bool chunked = split == 3;
+    const bool wide = n >= 256 && !chunked;
     const int bn = wide ? 256 : 128;
     if ((e = map3d_f32(&ta, fa, kk, m, leaves, TB_M)) != cudaSuccess) return e;
     if ((e = map3d_f32(&tb, fb, kk, n, leaves, bn)) != cudaSuccess) return e;
     const int64_t tm = (m + TB_M - 1) / TB_M, tn = (n + bn - 1) / bn;
     const int64_t tiles = tm * tn * leaves;
+    // FP32-accurate products: chunks of 512 k (1536 tripled) summed on the CUDA
+    // cores; one TF32 product: the whole k in TMEM
+    const int kblocks = int(kk / TB_K), chunk_kb = chunked ? 3 * 512 / TB_K : kblocks;
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, sm_count());
     cudaEvent_t t0 = timing_mark(s);
-    if (wide)
-        tf32_gemm<256><<<ctas, tf_threads<256>(), tf_smem<256>(), s>>>(ta, tb, Out, m, n, int(kk / TB_K), int(tm),
-                                                                       int(tn), tiles, ldo, os, accumulate, err);
-    else
-        tf32_gemm<128><<<ctas, tf_threads<128>(), tf_smem<128>(), s>>>(ta, tb, Out, m, n, int(kk / TB_K), int(tm),
-                                                                       int(tn), tiles, ldo, os, accumulate, err);
+#define FMM_TF32_GEMM(BN_, CH_)                                                                                \
+    tf32_gemm<BN_, CH_><<<ctas, tf_threads<BN_, CH_>(), tf_smem<BN_>(), s>>>(ta, tb, Out, m, n, kblocks, chunk_kb, \
+                                                                          int(tm), int(tn), tiles, ldo, os,    \
+                                                                          accumulate, err)
+    if (chunked) FMM_TF32_GEMM(128, true);
+    else if (wide) FMM_TF32_GEMM(256, false);
+    else FMM_TF32_GEMM(128, false);
+#undef FMM_TF32_GEMM
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
