@@ -34,6 +34,11 @@ W_TERM_FACTOR = 0.1                  # extra CRT cost per additional W term of a
 LAUNCH_US = 4.0                      # per kernel launch (6 launches for the emulated path)
 NUM_SMS = 152
 HBM_GBS = 6700.0
+TF32_TFLOPS = {"tf32": 850.0, "fp32": 550.0}   # leaf launch, TF32 work per second (fp32: 3 products)
+# e_F against the FP64 oracle on uniform data at 16384^3, per recursion level
+# (0, 1, 2: tf32 2.6e-4, 5.6e-4, 1.2e-3; fp32 3.7e-6, 3.9e-6, 4.3e-6), used
+# with a factor 2 of slack to admit the two precisions
+TF32_ERR = {"tf32": (3e-4, 2.0), "fp32": (4e-6, 1.1)}   # (e_F at 0 levels, growth per level)
 
 
 @dataclass(frozen=True)
@@ -41,7 +46,7 @@ class Choice:
     algorithm: str            # algorithm file name (levels 0: the classical product)
     levels: int
     flags: int
-    precision: str            # "fp64" or "ozaki_bf16"
+    precision: str            # "fp64", "ozaki_bf16", "tf32" or "fp32"
     moduli: int = 15
     tile: str = "auto"
     model_ms: float = 0.0
@@ -50,7 +55,7 @@ class Choice:
     def plan(self):
         return fmm.Plan(self.algorithm, levels=self.levels, flags=self.flags,
                         precision=self.precision, tile=self.tile,
-                        moduli=self.moduli if self.precision != "fp64" else None)
+                        moduli=self.moduli if self.precision == "ozaki_bf16" else None)
 
 
 _ALGS = None
@@ -126,6 +131,8 @@ class Autotuner:
         for prec in self.precisions:
             if prec == "ozaki_bf16" and nmod is None:
                 continue
+            if prec in TF32_ERR and 2 * TF32_ERR[prec][0] > self.tol:
+                continue
             # the DFMA pipe is ~1/100 of the emulated rate: FP64 plans only
             # compete on products too small for the tensor-core path to fill
             if prec == "fp64" and emulated and min(m, k, n) >= 64:
@@ -149,6 +156,8 @@ class Autotuner:
         M, K, N, R = base
         if prec == "fp64" and L > 0 and self.tol < 1e-13 * (2.0 ** L):
             return None
+        if prec in TF32_ERR and 2 * TF32_ERR[prec][0] * TF32_ERR[prec][1] ** L > self.tol:
+            return None
         sm, sk, sn = M ** L, K ** L, N ** L
         mp, kp, np_ = (m // sm) * sm, (k // sk) * sk, (n // sn) * sn
         mL, kL, nL = mp // sm, kp // sk, np_ // sn
@@ -163,6 +172,22 @@ class Autotuner:
                 adds += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
                                   + (mp // M ** l) * (np_ // N ** l)) * 8 * 3
             t += adds / (HBM_GBS * 1e9)
+            flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
+        elif prec in TF32_ERR:
+            # leaves on the TF32 tensor path; S/T and W level by level in FP64
+            split = 3 if prec == "fp32" else 1
+            kpad = -(-kL // 32) * 32
+            tile_n = 256 if (nL >= 256 and split == 1) else 128
+            t = 2.0 * leaves * mL * kpad * split * nL / (
+                TF32_TFLOPS[prec] * 1e12 * classical_efficiency(mL, nL, 128, tile_n, leaves))
+            # FP64 operands to TF32 (8 bytes in, 4 split bytes out per element)
+            t += leaves * (mL * kL + kL * nL) * (8 + 4 * split) / (HBM_GBS * 1e9)
+            adds = 0.0
+            for l in range(1, L + 1):
+                adds += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
+                                  + (mp // M ** l) * (np_ // N ** l)) * 8 * 3
+            t += adds / (HBM_GBS * 1e9)
+            t += (3 + 3 * L) * LAUNCH_US * 1e-6
             flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
         else:
             kpad = -(-kL // 64) * 64

@@ -44,3 +44,27 @@ def test_moduli_for_tolerance():
 def test_strict_tolerance_drops_deep_fp64_plans():
     t = autotune.Autotuner(tol=1e-14, precisions=("fp64",), measure=False)
     assert all(c.levels <= 1 for c in t.candidates(4096, 4096, 4096))
+
+
+def test_tf32_and_fp32_admitted_by_tolerance():
+    precs = ("tf32", "fp32", "ozaki_bf16")
+    # a loose target admits TF32 (classical; one level doubles its error) and FP32 at any depth
+    loose = autotune.Autotuner(tol=1e-3, precisions=precs, measure=False).candidates(8192, 8192, 8192)
+    kinds = {(c.precision, c.levels) for c in loose}
+    assert ("tf32", 0) in kinds and ("tf32", 1) not in kinds
+    assert ("fp32", 0) in kinds and ("fp32", 2) in kinds
+    # TF32 does the least work per product: it leads the loose target
+    assert loose[0].precision == "tf32"
+    # an FP32-level target keeps FP32, drops TF32
+    mid = autotune.Autotuner(tol=2e-5, precisions=precs, measure=False).candidates(8192, 8192, 8192)
+    assert {c.precision for c in mid} == {"fp32", "ozaki_bf16"}
+    # an FP64-level target leaves only the emulated FP64 plans
+    strict = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False).candidates(8192, 8192, 8192)
+    assert {c.precision for c in strict} == {"ozaki_bf16"}
+
+
+def test_choice_plans_carry_moduli_only_for_emulated_fp64():
+    c = autotune.Choice("strassen_222_7", 1, 0, "tf32")
+    assert c.plan().precision == "tf32"
+    c = autotune.Choice("strassen_222_7", 0, 0, "fp32")
+    assert c.plan().precision == "fp32"
