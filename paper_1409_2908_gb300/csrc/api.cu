@@ -261,20 +261,26 @@ cudaError_t timed(cudaStream_t s, F &&f) {
 // the hooks (the caller then copies C out after the whole product).
 cudaError_t settle_pipe(const HostPipe *&pipe, cudaStream_t s) {
     if (!pipe) return cudaSuccess;
-    const cudaError_t e = pipe->b_ready ? cudaStreamWaitEvent(s, pipe->b_ready, 0) : cudaSuccess;
+    // A's bands follow B on one stream: the last of them implies all
+    const cudaEvent_t last = pipe->a_bands > 0 ? pipe->a_ready[pipe->a_bands - 1] : pipe->b_ready;
+    const cudaError_t e = last ? cudaStreamWaitEvent(s, last, 0) : cudaSuccess;
     pipe = nullptr;
     return e;
 }
 
 // Side stream and events of the host entry point, one set per thread and
 // device (created on first use).
+constexpr int kMaxABands = 8;
 struct HostSide {
     int device = -1;
     cudaStream_t side = nullptr;
-    cudaEvent_t a_in = nullptr, b_in = nullptr, band = nullptr, side_done = nullptr;
+    cudaEvent_t start = nullptr, b_in = nullptr, band = nullptr, side_done = nullptr;
+    cudaEvent_t a_in[kMaxABands] = {};
     void release() {
-        for (cudaEvent_t *ev : {&a_in, &b_in, &band, &side_done})
+        for (cudaEvent_t *ev : {&start, &b_in, &band, &side_done})
             if (*ev) cudaEventDestroy(*ev), *ev = nullptr;
+        for (cudaEvent_t &ev : a_in)
+            if (ev) cudaEventDestroy(ev), ev = nullptr;
         if (side) cudaStreamDestroy(side), side = nullptr;
         device = -1;
     }
@@ -288,8 +294,13 @@ HostSide *host_side() {
     if (t_host.device == dev) return &t_host;
     t_host.release();
     if (cudaStreamCreateWithFlags(&t_host.side, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
-    for (cudaEvent_t *ev : {&t_host.a_in, &t_host.b_in, &t_host.band, &t_host.side_done})
+    for (cudaEvent_t *ev : {&t_host.start, &t_host.b_in, &t_host.band, &t_host.side_done})
         if (cudaEventCreateWithFlags(ev, cudaEventDisableTiming) != cudaSuccess) {
+            t_host.release();
+            return nullptr;
+        }
+    for (cudaEvent_t &ev : t_host.a_in)
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
             t_host.release();
             return nullptr;
         }
@@ -923,32 +934,52 @@ fmm_status fmm_gemm_host(fmm_plan_t p, const double *A, int64_t lda, const doubl
     double *dB = (double *)(w + align256(size_t(m * k * 8)));
     double *dC = (double *)((char *)dB + align256(size_t(k * n * 8)));
     char *rest = (char *)dC + align256(size_t(m * n * 8));
-    // A on the caller's stream; B on the side stream once A is in (the two
-    // would only share the link), so that the kernels reading A alone overlap
-    // the copy of B
+    // All copies in on the side stream (one after the other: they would only
+    // share the link), once the caller's earlier work on `stream` is done
+    // with the buffers: B first, then A in bands of first-level child rows,
+    // each with an event, so that the kernels reading B run while A arrives
+    // and each band of A is formed as soon as it is in.
     cudaError_t e;
     auto fail = [&](fmm_status st) {
         cudaStreamSynchronize(hs->side);   // no copy into the caller's buffers left in flight
         cudaStreamSynchronize(s);
         return st;
     };
-    if ((e = copy_rows(dA, k, A, lda, m, k, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaEventRecord(hs->a_in, s)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(hs->side, hs->a_in, 0)) != cudaSuccess ||
+    const int gM = (p && p->L > 0) ? p->M : 1;
+    const int64_t ml1 = m / gM;   // rows of a first-level block (banding is used only without a fringe)
+    const int a_bands = (int)std::max<int64_t>(1, std::min<int64_t>({4, ml1, m * k * 8 / (64 << 20)}));
+    if ((e = cudaEventRecord(hs->start, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(hs->side, hs->start, 0)) != cudaSuccess ||
         (e = copy_rows(dB, n, B, ldb, k, n, cudaMemcpyHostToDevice, hs->side)) != cudaSuccess ||
         (e = cudaEventRecord(hs->b_in, hs->side)) != cudaSuccess)
         return fail(cuda_status(e));
+    for (int j = 0; j < a_bands; ++j) {
+        // rows [r0, r1) of every block row; the last band also takes rows
+        // past gM ml1 (none when the path bands A)
+        const int64_t r0 = ml1 * j / a_bands, r1 = ml1 * (j + 1) / a_bands;
+        for (int a = 0; a < gM; ++a) {
+            const int64_t row = a * ml1 + r0;
+            if ((e = copy_rows(dA + row * k, k, A + row * lda, lda, r1 - r0, k, cudaMemcpyHostToDevice,
+                               hs->side)) != cudaSuccess)
+                return fail(cuda_status(e));
+        }
+        if (j == a_bands - 1 && gM * ml1 < m &&
+            (e = copy_rows(dA + gM * ml1 * k, k, A + gM * ml1 * lda, lda, m - gM * ml1, k,
+                           cudaMemcpyHostToDevice, hs->side)) != cudaSuccess)
+            return fail(cuda_status(e));
+        if ((e = cudaEventRecord(hs->a_in[j], hs->side)) != cudaSuccess) return fail(cuda_status(e));
+    }
     // C leaves in row bands, each copied on the side stream as soon as the
     // last pass has written it (when the path runs in bands at all)
     BandCopy bc{s, hs->side, hs->band, C, ldc, dC, n, 0};
     const int bands = host_bands(m, n);
-    HostPipe pipe{hs->b_in, bands, host_gemm_bands(bands), copy_band, &bc};
+    HostPipe pipe{hs->b_in, a_bands, hs->a_in, bands, host_gemm_bands(bands), copy_band, &bc};
     fmm_status st;
     int launches = 0;
     if (p) {
         st = run_gemm(p, dA, k, dB, n, dC, n, m, k, n, rest, ws_bytes - (rest - w), s, &launches, &pipe);
     } else {
-        st = cuda_status(cudaStreamWaitEvent(s, hs->b_in, 0));
+        st = cuda_status(cudaStreamWaitEvent(s, hs->a_in[a_bands - 1], 0));
         if (st == FMM_OK)
             st = cuda_status(launch_classical(dA, k, dB, n, dC, n, m, k, n, FMM_TILE_AUTO, s, &launches));
     }

@@ -183,6 +183,12 @@ size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
 // row bands too, each combined and handed over before the next is made.
 struct HostPipe {
     cudaEvent_t b_ready;
+    // a_bands > 0: A arrives after B in that many bands of the first level's
+    // child rows ([ml j / a_bands, ml (j + 1) / a_bands) of every block row, ml
+    // the rows of a level-1 block, or of A itself with no level), band j
+    // complete at a_ready[j]
+    int a_bands;
+    const cudaEvent_t *a_ready;
     int bands, gemm_bands;
     cudaError_t (*band_done)(void *ctx, int64_t r0, int64_t r1, int64_t block_rows, int block_rows_count);
     void *ctx;

@@ -644,16 +644,17 @@ template <int NB, bool FINAL, int LC>
 __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t lda, const int *ea, int64_t rows,
                                                        int64_t cols, int gridK, int R, int nmod, const int *ptr,
                                                        const int *code, const int *icoef, void *out,
-                                                       int64_t out_ld) {
+                                                       int64_t out_ld, int64_t r0, int64_t nr) {
     extern __shared__ long long sv[];   // [NB][4][256]
     __shared__ int2 sterm[OZ_MAX_TERMS];
     __shared__ int sptr[OZ_MAX_R + 1];
     stage_terms(R, gridK, ptr, code, icoef, sterm, sptr);
     __syncthreads();
+    // the child rows [r0, r0 + nr) (all of them: r0 = 0, nr = rows)
     const int64_t groups = (out_ld + 3) / 4;
     const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (pos >= rows * groups) return;
-    const int64_t i = pos / groups, j0 = (pos % groups) * 4;
+    if (pos >= nr * groups) return;
+    const int64_t i = r0 + pos / groups, j0 = (pos % groups) * 4;
     const int valid = (int)min((int64_t)4, out_ld - j0);
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
@@ -953,10 +954,14 @@ __global__ void __launch_bounds__(256, 4) w_crt_kernel(const int8_t *Z, int64_t 
 
 // Row exponents s_i = beta - 1 - floor(log2 max_j |A_ij|) (0 for a zero row),
 // one warp per row.
-__global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64_t cols, int beta, int *exps) {
-    const int64_t row = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+// rows: the count of rows handled; with a band (band_rows > 0) they are the
+// rows [r0, r0 + band_rows) of each block row of block_rows rows.
+__global__ void row_exp_kernel(const double *A, int64_t lda, int64_t rows, int64_t cols, int beta, int *exps,
+                               int64_t band_rows = 0, int64_t block_rows = 0, int64_t r0 = 0) {
+    const int64_t idx = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     const int lane = threadIdx.x % 32;
-    if (row >= rows) return;
+    if (idx >= rows) return;
+    const int64_t row = band_rows > 0 ? (idx / band_rows) * block_rows + r0 + idx % band_rows : idx;
     const double *x = A + row * lda;
     unsigned mh = 0u, lo = 0u;   // max of the high words of |x|, OR of the low words
     if (((uintptr_t)x & 15) == 0) {
@@ -1314,11 +1319,14 @@ size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t n
 template <bool FINAL, int LC>
 static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, const int *ea, int64_t rows,
                                           int64_t cols, int gridK, int R, int nmod, const int *ptr, const int *code,
-                                          const int *icoef, void *out, int64_t out_ld, cudaStream_t s) {
-    const int64_t threads = rows * ((out_ld + 3) / 4);
+                                          const int *icoef, void *out, int64_t out_ld, cudaStream_t s,
+                                          int64_t r0 = 0, int64_t nr = -1) {
+    if (nr < 0) nr = rows;
+    if (nr == 0) return cudaSuccess;
+    const int64_t threads = nr * ((out_ld + 3) / 4);
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     const size_t smem = size_t(nb) * 4 * 256 * 8;
-#define FMM_SFR(NB) split_form_rows<NB, FINAL, LC><<<blocks, 256, smem, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld)
+#define FMM_SFR(NB) split_form_rows<NB, FINAL, LC><<<blocks, 256, smem, s>>>(A, lda, ea, rows, cols, gridK, R, nmod, ptr, code, icoef, out, out_ld, r0, nr)
     switch (nb) {
         case 1: FMM_SFR(1); break;
         case 4: FMM_SFR(4); break;
@@ -1468,7 +1476,9 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     (WHICH ? launch_split_form_cols_t<F, LC>(nbB, B, ldb, eb, kl1, nl1, gN, R1, nmod, vp, vc, vi, b + w.lb[0],      \
                                              out_ld1, s)                                                           \
            : launch_split_form_rows<F, LC>(nbA, A, lda, ea, ml1, kl1, gK, R1, nmod, up, uc, ui, b + w.la[0],       \
-                                           out_ld1, s))
+                                           out_ld1, s, ar0, anr))
+    // which 0: the A side, child rows [ar0, ar0 + anr); 1: the B side
+    int64_t ar0 = 0, anr = ml1;
     auto fused_split = [&](int which) -> cudaError_t {
         cudaError_t se;
         if (last1)
@@ -1482,29 +1492,52 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     // a base case without a fused first-level instance: level-0 residues, then level 1
     int8_t *ra0 = (int8_t *)(b + w.ra0), *rb0 = (int8_t *)(b + w.rb0);
 
-    row_exp_kernel<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, ea);
-    if ((e = check()) != cudaSuccess) return e;
-    if (fused) {
-        if ((e = fused_split(0)) != cudaSuccess) return e;
-    } else {
+    auto a_side = [&]() -> cudaError_t {
+        cudaError_t ae;
+        row_exp_kernel<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, ea);
+        if ((ae = check()) != cudaSuccess) return ae;
+        if (fused) return fused_split(0);
         split_rows_i8<<<(unsigned)((mp + 7) / 8), 256, 0, s>>>(A, lda, mp, kp, beta, nmod, ra0, ea);
-        if ((e = check()) != cudaSuccess) return e;
-        if ((e = form(ra0, 1, mp, kp, ml1, kl1, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[0], last1,
-                      out_ld1)) != cudaSuccess)
-            return e;
-    }
-    if (pipe && pipe->b_ready && (e = cudaStreamWaitEvent(s, pipe->b_ready, 0)) != cudaSuccess) return e;
-    col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, COL_EXP_ROWS), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
-    if ((e = check()) != cudaSuccess) return e;
-    if (fused) {
-        if ((e = fused_split(1)) != cudaSuccess) return e;
-    } else {
+        if ((ae = check()) != cudaSuccess) return ae;
+        return form(ra0, 1, mp, kp, ml1, kl1, rp.u_ptr, rp.u_code, rp.u_icoef, b + w.la[0], last1, out_ld1);
+    };
+    auto b_side = [&]() -> cudaError_t {
+        cudaError_t be;
+        if (pipe && pipe->b_ready && (be = cudaStreamWaitEvent(s, pipe->b_ready, 0)) != cudaSuccess) return be;
+        col_exp_wide<<<dim3((unsigned)((np + 31) / 32), 1), dim3(32, COL_EXP_ROWS), 0, s>>>(B, ldb, 0, kp, np, beta, eb);
+        if ((be = check()) != cudaSuccess) return be;
+        if (fused) return fused_split(1);
         split_cols_t_i8<<<dim3((unsigned)((kp + 31) / 32), (unsigned)((np + 31) / 32)), dim3(32, 8), 0, s>>>(
             B, ldb, kp, np, nmod, eb, rb0);
-        if ((e = check()) != cudaSuccess) return e;
-        if ((e = form(rb0, 1, np, kp, nl1, kl1, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last1,
-                      out_ld1)) != cudaSuccess)
-            return e;
+        if ((be = check()) != cudaSuccess) return be;
+        return form(rb0, 1, np, kp, nl1, kl1, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last1, out_ld1);
+    };
+    if (pipe && pipe->a_bands > 0) {
+        // the host copies B first, then A in bands of child rows [ml1 j / a_bands,
+        // ml1 (j + 1) / a_bands) of every block row, each with an event: the B
+        // side runs while A arrives, and each A band is formed once it is in
+        const int gM = rp.L ? rp.M : 1;
+        if ((e = b_side()) != cudaSuccess) return e;
+        if (!fused) {
+            if ((e = cudaStreamWaitEvent(s, pipe->a_ready[pipe->a_bands - 1], 0)) != cudaSuccess) return e;
+            if ((e = a_side()) != cudaSuccess) return e;
+        } else {
+            for (int j = 0; j < pipe->a_bands; ++j) {
+                if ((e = cudaStreamWaitEvent(s, pipe->a_ready[j], 0)) != cudaSuccess) return e;
+                ar0 = ml1 * j / pipe->a_bands;
+                anr = ml1 * (j + 1) / pipe->a_bands - ar0;
+                if (anr == 0) continue;
+                const int64_t rows = anr * gM;
+                row_exp_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(A, lda, rows, kp, beta, ea, anr, ml1, ar0);
+                if ((e = check()) != cudaSuccess) return e;
+                if ((e = fused_split(0)) != cudaSuccess) return e;
+            }
+            ar0 = 0;
+            anr = ml1;
+        }
+    } else {
+        if ((e = a_side()) != cudaSuccess) return e;
+        if ((e = b_side()) != cudaSuccess) return e;
     }
     // levels 2..L: S and T^T level by level
     int64_t parents = rp.L ? rp.R : 1;

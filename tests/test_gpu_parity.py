@@ -193,8 +193,11 @@ def test_host_entry_point():
     ("strassen_222_7", 1, 4096, 256, 4096),   # C out in 4 row bands of 2 block rows
     ("fmm_323_15", 1, 4080, 256, 4080),       # 3 uneven bands of 3 block rows
     ("strassen_222_7", 0, 3000, 300, 2900),   # classical emulation: 2 bands of one block row
-    ("strassen_222_7", 1, 4097, 257, 4095),   # fringe: B awaited up front, C copied out whole
+    ("strassen_222_7", 1, 4097, 257, 4095),   # fringe: all of A awaited up front, C copied out whole
     ("strassen_222_7", 2, 1000, 512, 900),    # small: one band
+    ("strassen_222_7", 1, 4096, 4096, 1024),  # A in 2 bands of 2 block rows behind B
+    ("fmm_323_15", 1, 6003, 2800, 1200),      # A in 2 uneven bands of 3 block rows
+    ("strassen_222_7", 0, 8190, 4100, 300),   # A in 4 bands, classical emulation
 ])
 def test_host_entry_point_emulated(name, levels, m, k, n):
     # the overlapped host path (B copied while the A side runs, C copied out
