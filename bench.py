@@ -493,8 +493,9 @@ def main():
         e2e = {"value": ws * flops / ems / 1e9, "unit": "TFLOP/s", "ms_per_step": ems,
                "h2d_bytes_per_step": 8 * (m * k + k * n), "d2h_bytes_per_step": 8 * m * n,
                "api": "fmm_gemm_host (pinned host A, B, C; H2D + product + D2H per step)",
-               "pipeline": ("B copied in while the kernels reading only A run; residue products in row "
-                            "bands, each combined and copied out while the next band is multiplied"),
+               "pipeline": ("B copied in first and A after it in row bands: the B side is formed while A "
+                            "arrives and each A band as soon as it is in; residue products in row bands, "
+                            "each combined and copied out while the next band is multiplied"),
                "link_gbs": {"h2d": Ah.numel() * 8 / h2d_ms / 1e6, "d2h": Ah.numel() * 8 / d2h_ms / 1e6},
                "serialised_ms": (8 * (m * k + k * n) / (Ah.numel() * 8 / h2d_ms) + 8 * m * n / (Ah.numel() * 8 / d2h_ms)
                                  + ms_step)}
