@@ -86,3 +86,20 @@ def test_error_within_truncation_bound(n):
     rowsum_a = np.abs(A).sum(axis=1, keepdims=True)
     bound = ra * colsum_b + rowsum_a * rb + 64 * ra * rb + 4 * 2.0 ** -53 * (np.abs(A) @ np.abs(B))
     assert np.all(np.abs(C - Cl) <= bound)
+
+
+def test_subnormal_rows_and_columns_scale_exactly():
+    # a row (and a column) of small multiples of the least subnormal 2^-1074:
+    # its exponent comes from frexp, and the scaled integers are exact, so the
+    # emulation reproduces the exact product (every value here is a small
+    # integer times a power of two, exact in FP64)
+    rng = np.random.default_rng(4)
+    tiny = 2.0 ** -1074
+    A = rng.integers(-4, 5, (6, 30)).astype(np.float64)
+    B = rng.integers(-4, 5, (30, 5)).astype(np.float64)
+    A[2] = rng.integers(-9, 10, 30) * tiny
+    B[:, 3] = rng.integers(-9, 10, 30) * 2.0 ** 900
+    assert np.all(np.abs(A[2]) < 2.0 ** -1022) and np.any(A[2] != 0)
+    C = ozaki.emulated_gemm(A, B, 12)
+    assert np.array_equal(C, A @ B)
+    assert np.any(C[2] != 0)
