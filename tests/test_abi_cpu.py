@@ -180,3 +180,25 @@ def test_write_once_workspace_too_small_is_reported():
     a = ctypes.addressof(buf)
     st = L.fmm_gemm(p.handle, a, 2, a + 64, 2, a + 128, 2, 2, 2, 2, None, 0, None)
     assert st == fmm.FMM_ERR_NO_MEMORY
+
+
+def test_emulated_and_tf32_workspace_layouts():
+    # the documented layouts, region by region (256-byte aligned)
+    al = lambda x: (x + 255) // 256 * 256
+    n = 8192
+    # Strassen 1 level, 12 moduli: exponents, 7 x 12 bf16 planes per operand
+    # (4096 x 4096, k padded to 64), 7 x 12 int8 product planes (rows padded to 16)
+    p = fmm.Plan("strassen_222_7", levels=1, precision="ozaki_bf16", moduli=12)
+    want = al(n * 4) * 2 + 2 * al(7 * 12 * 4096 * 4096 * 2) + al(7 * 12 * 4096 * 4096)
+    assert p.workspace_size(n, n, n) == want == 7046496256
+    # the host entry point adds device copies of A, B and C in front
+    assert fmm.host_workspace_size(p, n, n, n) == 3 * al(n * n * 8) + want
+    # no level: the classical emulated product, 12 planes per operand
+    p0 = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=12)
+    assert p0.workspace_size(n, n, n) == al(n * 4) * 2 + 2 * al(12 * n * n * 2) + al(12 * n * n)
+    # TF32 operands in FP32 with k padded to 32; the FP32-accurate variant triples k
+    kpad = 1024
+    assert fmm.Plan("strassen_222_7", levels=0, precision="tf32").workspace_size(1000, 1000, 1000) == \
+        2 * al(1000 * kpad * 4)
+    assert fmm.Plan("strassen_222_7", levels=0, precision="fp32").workspace_size(1000, 1000, 1000) == \
+        2 * al(1000 * 3 * kpad * 4)
