@@ -63,3 +63,41 @@ def test_error_norms():
     A = np.full((1, 2), 2.0)
     B = np.full((2, 2), 0.5)
     assert norms.rel_max(C + 1.0, C, A, B) == pytest.approx(1.0 / 2.0)
+
+
+def test_long_double_accumulator_keeps_what_fp64_loses():
+    # 2^53 + 1 + 1 - 2^53 = 2 exactly; an FP64 accumulator rounds 2^53 + 1 back
+    # to 2^53 (ties to even) and returns 0.  The wide variant must return 2: a
+    # double accumulator in oracle_gemm_ld fails here.
+    big = 2.0 ** 53
+    A = np.array([[big, 1.0, 1.0, -big]])
+    B = np.ones((4, 1))
+    assert oracle.gemm(A, B)[0, 0] == 0.0          # the FP64 loop loses the ones
+    assert oracle.gemm(A, B, precision="ld")[0, 0] == 2.0
+    _, eld = oracle.gemm_entries(A, B, [0], [0])
+    assert eld[0] == 2.0
+
+
+def test_long_double_products_are_formed_wide():
+    # (1 + 2^-30)^2 = 1 + 2^-29 + 2^-60: the 2^-60 term needs 61 significant
+    # bits, so a product rounded to FP64 before the wide sum loses it and the
+    # entry comes out 0 instead of 2^-60.
+    a = 1.0 + 2.0 ** -30
+    A = np.array([[a, -(1.0 + 2.0 ** -29)]])
+    B = np.array([[a], [1.0]])
+    assert oracle.gemm(A, B)[0, 0] == 0.0
+    assert oracle.gemm(A, B, precision="ld")[0, 0] == 2.0 ** -60
+    _, eld = oracle.gemm_entries(A, B, [0], [0])
+    assert eld[0] == 2.0 ** -60
+
+
+def test_gamma_closed_form():
+    # gamma_n = n u / (1 - n u) with u = 2^-53 (unit roundoff of round to
+    # nearest in FP64) equals n / (2^53 - n) exactly; gamma_1 = u / (1 - u).
+    from fractions import Fraction
+    for n in (1, 2, 3, 1000, 16384, 2 ** 20):
+        want = Fraction(n, 2 ** 53 - n)
+        assert abs(Fraction(norms.gamma(n)) - want) <= want * Fraction(1, 2 ** 52)
+    assert norms.gamma(1) == pytest.approx(2.0 ** -53, rel=1e-15)
+    # a unit roundoff of 2^-52 (machine epsilon) would double every bound
+    assert norms.gamma(1000) < 1000 * 2.0 ** -52 * 0.75
