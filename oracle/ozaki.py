@@ -11,7 +11,8 @@ Definition (our reading, fixed here):
   * beta = the largest width (at most 62) with k 2^(2 beta + 1) < P, P the
     product of the moduli: then |A'B'| < P/2 is guaranteed;
   * row exponents s_i = beta - 1 - floor(log2 max_j |A_ij|) (0 for a zero row),
-    A'_ij = trunc(A_ij 2^s_i); column exponents t_j and B'_ij likewise;
+    A'_ij = round(A_ij 2^s_i), to the nearest integer with ties away from
+    zero, so |A'_ij| <= 2^beta; column exponents t_j and B'_ij likewise;
   * Z = A' B' exactly (integers); residues Z mod p for each modulus p are what
     the tensor cores compute, from balanced residues A' mod p and B' mod p;
   * C_ij = Z_ij 2^(-s_i - t_j).
@@ -48,8 +49,20 @@ def balanced(x, p):
     return r - p if r >= (p + 1) // 2 else r
 
 
+def round_half_away(y):
+    """Nearest integer to each entry of y, ties away from zero.  Exact: for
+    |y| >= 1 the fraction |y| - floor(|y|) is computed without rounding, and
+    below 1 the answer is 0 or 1 by comparison with 1/2."""
+    a = np.abs(y)
+    f = np.floor(a)
+    r = f + (a - f >= 0.5)
+    return np.where(y < 0, -r, r)
+
+
 def scale_rows(A, beta):
-    """(A' as int64, exponents s) with A'_ij = trunc(A_ij 2^s_i)."""
+    """(A' as int64, exponents s) with A'_ij = round(A_ij 2^s_i), ties away
+    from zero (2^s_i is a power of two, so A_ij 2^s_i itself is exact wherever
+    it is at least 2^-1022; anything smaller rounds to 0 either way)."""
     A = np.asarray(A, np.float64)
     s = np.zeros(A.shape[0], np.int64)
     out = np.zeros(A.shape, np.int64)
@@ -59,7 +72,7 @@ def scale_rows(A, beta):
             continue
         e = math.frexp(mx)[1] - 1          # floor(log2 mx)
         s[i] = beta - 1 - e
-        out[i] = np.trunc(np.ldexp(A[i], int(s[i]))).astype(np.int64)
+        out[i] = round_half_away(np.ldexp(A[i], int(s[i]))).astype(np.int64)
     return out, s
 
 
@@ -106,3 +119,26 @@ def emulated_gemm(A, B, n_moduli):
         for j in range(Z.shape[1]):
             C[i, j] = math.ldexp(float(Z[i, j]), -int(s[i]) - int(t[j]))
     return C
+
+
+def emulated_entries(A, B, rows, cols, n_moduli):
+    """Entries (rows[t], cols[t]) of emulated_gemm(A, B, n_moduli), each from
+    its own row of A and column of B: the row exponent depends only on the
+    row and the column exponent only on the column, so this is the same
+    definition evaluated one entry at a time (for sampling full-size
+    products)."""
+    k = A.shape[1]
+    beta = beta_bits(n_moduli, k)
+    rows = np.asarray(rows)
+    cols = np.asarray(cols)
+    ur, ri = np.unique(rows, return_inverse=True)
+    uc, ci = np.unique(cols, return_inverse=True)
+    Ai, s = scale_rows(np.asarray(A)[ur], beta)
+    Bi, t = scale_cols(np.asarray(B)[:, uc], beta)
+    arows = [list(map(int, Ai[i])) for i in range(len(ur))]
+    bcols = [list(map(int, Bi[:, j])) for j in range(len(uc))]
+    out = np.empty(len(rows))
+    for e, (i, j) in enumerate(zip(ri, ci)):
+        z = sum(a * b for a, b in zip(arows[i], bcols[j]))
+        out[e] = math.ldexp(float(z), -int(s[i]) - int(t[j]))
+    return out

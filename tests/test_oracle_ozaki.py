@@ -63,25 +63,61 @@ def test_residue_product_matches_exact_product():
 
 
 def test_scaling_is_exact_for_short_integers():
-    # integer inputs whose rows fit in beta bits are not truncated, so the
-    # emulation reproduces the exact product
+    # integer inputs whose rows fit in beta bits scale to integers exactly (no
+    # rounding), so the emulation reproduces the exact product
     rng = np.random.default_rng(2)
     A = rng.integers(-4, 5, (9, 40)).astype(np.float64)
     B = rng.integers(-4, 5, (40, 11)).astype(np.float64)
     assert np.array_equal(ozaki.emulated_gemm(A, B, 12), A @ B)
 
 
+def test_round_half_away_against_exact_rationals():
+    # brute force against exact rational rounding (floor(|y| + 1/2), sign
+    # restored) on ties, near-ties and values over many binades
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    ties = [0.5, -0.5, 1.5, -1.5, 2.5, -2.5, 2.0 ** 51 + 0.5, -(2.0 ** 40 + 0.5), 0.0, -0.0]
+    near = [0.49999999999999994, -0.49999999999999994, 2.5 - 2 ** -51, 1.0 - 2 ** -53]
+    rand = list(rng.uniform(-1, 1, 200) * 2.0 ** rng.integers(-3, 60, 200))
+    ys = np.array(ties + near + rand)
+    got = ozaki.round_half_away(ys)
+    for y, g in zip(ys, got):
+        a = Fraction(abs(float(y)))
+        want = (a + Fraction(1, 2)).__floor__()
+        assert g == (-want if y < 0 else want), y
+    assert list(ozaki.round_half_away(np.array([0.5, 2.5, -2.5]))) == [1.0, 3.0, -3.0]
+
+
+def test_scaled_entries_round_to_nearest():
+    # |A_ij 2^s_i - A'_ij| <= 1/2 (truncation would leave errors up to 1), and
+    # |A'_ij| <= 2^beta, with the row maximum mapped into [2^(beta-1), 2^beta]
+    rng = np.random.default_rng(8)
+    A = rng.uniform(-1, 1, (20, 50)) * 2.0 ** rng.integers(-30, 30, (20, 1))
+    beta = 20
+    Ai, s = ozaki.scale_rows(A, beta)
+    exact = np.ldexp(A, s[:, None])      # exact: powers of two, no underflow here
+    assert np.all(np.abs(exact - Ai) <= 0.5)
+    assert np.max(np.abs(exact - Ai)) > 0.45   # the bound is reached, not slack
+    assert np.all(np.abs(Ai) <= 2 ** beta)
+    mx = np.abs(Ai).max(axis=1)
+    assert np.all((mx >= 2 ** (beta - 1)) & (mx <= 2 ** beta))
+    # a row maximum just below 2^(e+1) rounds up to exactly 2^beta
+    Ai2, _ = ozaki.scale_rows(np.array([[2.0 - 2.0 ** -40, 0.25]]), beta)
+    assert Ai2[0, 0] == 2 ** beta
+
+
 @pytest.mark.parametrize("n", [8, 12, 15])
-def test_error_within_truncation_bound(n):
+def test_error_within_rounding_bound(n):
     rng = np.random.default_rng(3)
     A = rng.uniform(-1, 1, (12, 64))
     B = rng.uniform(-1, 1, (64, 10))
     C = ozaki.emulated_gemm(A, B, n)
     Cl = oracle.gemm(A, B, precision="ld")
     beta = ozaki.beta_bits(n, 64)
-    # |dA_ij| <= 2^(1-beta) max_j |A_ij| (likewise B): first-order bound
-    ra = np.abs(A).max(axis=1, keepdims=True) * 2.0 ** (1 - beta)
-    rb = np.abs(B).max(axis=0, keepdims=True) * 2.0 ** (1 - beta)
+    # |dA_ij| <= 2^-beta max_j |A_ij| (likewise B): rounding to nearest moves
+    # each scaled entry by at most 1/2, and 2^-s_i <= 2^(1-beta) max_j |A_ij|
+    ra = np.abs(A).max(axis=1, keepdims=True) * 2.0 ** (-beta)
+    rb = np.abs(B).max(axis=0, keepdims=True) * 2.0 ** (-beta)
     colsum_b = np.abs(B).sum(axis=0, keepdims=True)
     rowsum_a = np.abs(A).sum(axis=1, keepdims=True)
     bound = ra * colsum_b + rowsum_a * rb + 64 * ra * rb + 4 * 2.0 ** -53 * (np.abs(A) @ np.abs(B))
@@ -103,3 +139,14 @@ def test_subnormal_rows_and_columns_scale_exactly():
     C = ozaki.emulated_gemm(A, B, 12)
     assert np.array_equal(C, A @ B)
     assert np.any(C[2] != 0)
+
+
+@pytest.mark.parametrize("kind,n", [("uniform", 12), ("uniform", 14), ("loguniform", 13)])
+def test_emulated_entries_match_full_emulation(kind, n):
+    from paper_1409_2908_gb300 import synth
+    A, B = synth.operands(37, 90, 29, 9, kind=kind)
+    C = ozaki.emulated_gemm(A, B, n)
+    rng = np.random.default_rng(10)
+    rows = rng.integers(0, 37, 60)
+    cols = rng.integers(0, 29, 60)
+    assert np.array_equal(ozaki.emulated_entries(A, B, rows, cols, n), C[rows, cols])
