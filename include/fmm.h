@@ -52,14 +52,21 @@ typedef enum {
 
 typedef enum {
     FMM_PREC_FP64 = 0,       /* FP64 leaves (DFMA), FP64 combinations */
-    /* Leaf products emulated to FP64 accuracy on the tensor cores: each leaf
-       operand is scaled per row (S) / column (T) to beta-bit integers, the
-       integer product is computed exactly modulo N pairwise coprime moduli
-       <= 256 with bfloat16 residues and FP32 accumulation (tcgen05), and
-       rebuilt by the Chinese remainder theorem in FP64.  S/T formation, the W
-       combination and the fringe stay FP64.  Error: truncation of the
-       scaled operands to beta bits, beta = floor((log2 prod p - 1 -
-       log2 k_L)/2) (about 51 bits for N = 15, k_L = 16384). */
+    /* Leaf products emulated to FP64 accuracy on the tensor cores: the
+       operands are scaled per row (A or S) / column (B or T) by powers of two
+       and truncated to beta-bit integers, the integer product is computed
+       exactly modulo N pairwise coprime moduli <= 256 with bfloat16 residues
+       and FP32 accumulation (tcgen05), and rebuilt by the Chinese remainder
+       theorem, rounded once to FP64.  beta is the largest width <= 62 with
+       k 2^(2 beta + 1) < P, P the product of the moduli (an exact integer
+       search; about 51 bits for N = 15, k = 16384).
+       With integer base coefficients (every shipped algorithm) the whole
+       recursion runs on residues of the once-scaled A and B: S/T formation
+       and the W combination are exact modular arithmetic on the residues, and
+       only the scaling and the final CRT rounding touch FP64 values.  With
+       other coefficients, or with FMM_FLAG_LEAF_EMULATION, each leaf product
+       is emulated on its own and S/T formation and the W combination run in
+       FP64.  The fringe (Section 3.5) is a classical FP64 product. */
     FMM_PREC_OZAKI_BF16 = 3,
     /* Leaf products on the tensor cores in TF32 (operands rounded to a
        10-bit significand, FP32 accumulation), widened to FP64 for the W
@@ -98,6 +105,18 @@ enum {
        of the once-scaled A and B (the default when every base coefficient
        is an integer: the bilinear algorithm is then exact modulo p). */
     FMM_FLAG_LEAF_EMULATION = 1u << 3,
+    /* Addition schemes of the level-by-level passes (Section 3.2), for the
+       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 and TF32
+       plans): by default each child S_r, T_r or C block is written once from
+       all its terms ("write-once").  STREAMING reads each parent element
+       once and writes it into every child that uses it; PAIRWISE forms each
+       child by one pass per term (child = c x, then child += c x).  All three
+       do the same additions in the same order and give the same bits.  At
+       most one of the two flags; base cases with more than 512 terms in a
+       factor matrix, R > 128 or more than 64 blocks fall back to write-once
+       for STREAMING. */
+    FMM_FLAG_STREAMING = 1u << 4,
+    FMM_FLAG_PAIRWISE = 1u << 5,
     FMM_FLAGS_DEFAULT = FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W
 };
 
@@ -126,7 +145,8 @@ typedef enum {
  * levels: 0..6 (0 = classical product).  M, K, N: 1..16; R: 1..1024.
  * out: receives the plan; unchanged on error.
  * Errors: FMM_ERR_ARG (null pointer, sizes out of range, levels out of range,
- * unknown flags), FMM_ERR_INVALID_ALGORITHM (Brent check failed),
+ * unknown flags, STREAMING with PAIRWISE), FMM_ERR_INVALID_ALGORITHM (Brent
+ * check failed),
  * FMM_ERR_UNSUPPORTED (R^L or the unrolled term lists too large, or a
  * coefficient that is not finite), FMM_ERR_NO_MEMORY, FMM_ERR_CUDA.
  */
@@ -161,6 +181,27 @@ fmm_status fmm_plan_set_moduli(fmm_plan_t plan, int n_moduli);
    reports an error. */
 fmm_status fmm_check_device_error(void);
 
+/* Time limit, in nanoseconds of the GPU's global timer, of every bounded
+   device-side wait in the tensor-core kernels (the emulated-FP64 residue
+   GEMM and the TF32 GEMM) launched after this call; default 2e9 (2 s).  A
+   kernel whose wait runs out stops issuing work, waits (with the same limit)
+   for the copies and MMAs it already issued, frees its tensor memory and
+   returns; fmm_check_device_error then reports FMM_ERR_TIMEOUT and the
+   product's result is undefined.  Process-wide.
+   Errors: FMM_ERR_ARG for 0. */
+fmm_status fmm_set_wait_limit(uint64_t ns);
+
+/* Self-test of that timeout path: launches one CTA of the chosen kernel
+   (0 = residue GEMM, 1 = TF32 GEMM) on small private buffers with its load
+   and MMA threads told to issue nothing, so its first wait for a finished
+   accumulator runs out after `ns` nanoseconds with no copy or MMA
+   outstanding.  Synchronises `stream`, then reads and clears the device
+   error flag: FMM_ERR_TIMEOUT is the expected answer (the wait ran out and
+   the kernel returned), FMM_OK would mean it did not.  The CUDA context stays
+   usable.  Errors: FMM_ERR_ARG (kernel not 0 or 1, ns = 0), FMM_ERR_CUDA,
+   FMM_ERR_NO_MEMORY. */
+fmm_status fmm_selftest_wait_timeout(int kernel, uint64_t ns, void *stream);
+
 /* Copy the plan to the current device and set up everything its kernels
    need (constant tables, kernel attributes) now, instead of on the first
    fmm_gemm call; afterwards fmm_gemm with this plan performs no allocation or
@@ -169,8 +210,12 @@ fmm_status fmm_check_device_error(void);
 fmm_status fmm_plan_prepare(fmm_plan_t plan);
 
 /* Choose the leaf GEMM tile shape used by later fmm_gemm calls with this
-   plan (default FMM_TILE_AUTO).  Not thread-safe against concurrent
-   fmm_gemm calls on the same plan. */
+   plan (default FMM_TILE_AUTO).  FP64 plans: the FP64 leaf kernel's CTA tile.
+   Tensor-core plans (emulated FP64, TF32, FP32): FMM_TILE_128x128 narrows the
+   tensor-core GEMM's tiles from 128 x 256 to 128 x 128 (two TMEM accumulators
+   of 128 columns, more CTAs for narrow or few leaves); any other value keeps
+   128 x 256 wherever the leaves are at least 256 wide.  Not thread-safe
+   against concurrent fmm_gemm calls on the same plan. */
 fmm_status fmm_plan_set_tile(fmm_plan_t plan, fmm_tile tile);
 
 /* Description of a plan (fmm_plan_info). */
@@ -292,38 +337,45 @@ fmm_status fmm_gemm_host(fmm_plan_t plan, const double *A, int64_t lda,
 
 /*
  * fmm_gemm_noalloc - C = A B like fmm_gemm, for callers that cannot allocate
- * device memory when they need a product (no counterpart in the paper).
+ * device memory when they need a product.  The paper has no counterpart.
  *
- * Who needs it: code that runs while a CUDA graph is being captured, hosts
- * whose device memory is reserved up front by another allocator, and paths
- * that cannot afford the implicit device synchronisation of cudaMalloc.  The
- * call allocates nothing and takes no workspace: it runs the plan's stored-
- * product scheme (leaf products M_r kept, then C formed in a fixed order,
- * bitwise reproducible) with S_r/T_r formed in the leaf kernel, and keeps the
- * unrolled plan lists and the leaf products in one file-scope device array of
- * FMM_NOALLOC_SCRATCH_BYTES that every GPU loading this library holds until
- * the process exits.  The plan's own scheme flags are ignored.
+ * Who needs it: programs whose device memory is all reserved up front by
+ * another allocator (a framework's caching allocator, or a pool sized at
+ * start-up), where a cudaMalloc at call time fails or competes with that
+ * pool, and code that may not call into the CUDA allocator on its hot path
+ * at all.  The call allocates no device or host memory, takes no workspace
+ * and copies nothing from the host.  It runs the stored-product scheme (leaf
+ * products M_r kept, then C formed in a fixed order, bitwise reproducible)
+ * with S_r/T_r formed in the leaf kernel; the plan's own scheme flags are
+ * ignored.  Its only scratch, the leaf products, is one file-scope device
+ * array of FMM_NOALLOC_SCRATCH_BYTES (32 MiB) that every GPU loading this
+ * library holds until the process exits.
  *
- * Limit: the lists plus R^L * (m'/M^L) * (n'/N^L) * 8 bytes of products must
- * fit in FMM_NOALLOC_SCRATCH_BYTES; larger problems return
- * FMM_ERR_UNSUPPORTED before anything is enqueued.  Products that take the
- * classical path (no fast core) need no scratch.
+ * Precondition: the plan's lists are already on the current device
+ * (fmm_plan_prepare, or any earlier fmm_gemm with this plan, made with this
+ * device current); otherwise FMM_ERR_ARG, since uploading them would
+ * allocate.  The first call on a device looks up the scratch array's device
+ * address with that device current.
  *
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
- * call reuses the same array (its contents are whatever the last call left;
- * each call rewrites all of it that it reads), so calls whose GPU work
+ * Limit: R^L * (m'/M^L) * (n'/N^L) * 8 bytes of leaf products must fit in
+ * FMM_NOALLOC_SCRATCH_BYTES; larger problems return FMM_ERR_UNSUPPORTED
+ * before anything is enqueued.  Products that take the classical path (no
+ * fast core) need no scratch.
+ *
+ * Every call uses the same array, which keeps whatever the last call left
+ * (each call writes all of it that it reads), so calls whose GPU work
  * overlaps - on different streams or host threads - race and must be
- * serialised by the caller.  The lists are copied from host memory on
- * `stream` each call.  Pointer, size and error rules are those of fmm_gemm.
+ * serialised by the caller.  fmm_last_launch_count reports this call's
+ * launches.  Pointer, size and error rules are those of fmm_gemm.
  */
 #define FMM_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 fmm_status fmm_gemm_noalloc(fmm_plan_t plan, const double *A, int64_t lda,
                             const double *B, int64_t ldb, double *C, int64_t ldc,
                             int64_t m, int64_t k, int64_t n, void *stream);
 
-/* Number of CUDA kernel launches the last fmm_gemm / fmm_classical_gemm
-   call on this host thread enqueued (for launch accounting). */
+/* Number of CUDA kernel launches the last fmm_gemm, fmm_gemm_batched,
+   fmm_gemm_noalloc, fmm_gemm_host or fmm_classical_gemm call on this host
+   thread enqueued (for launch accounting). */
 int fmm_last_launch_count(void);
 
 /*

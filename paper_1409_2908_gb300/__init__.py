@@ -28,6 +28,8 @@ FLAG_FUSED_ST = 1
 FLAG_FUSED_W = 2
 FLAG_LEVELWISE = 4
 FLAG_LEAF_EMULATION = 8
+FLAG_STREAMING = 16
+FLAG_PAIRWISE = 32
 FLAGS_DEFAULT = FLAG_FUSED_ST | FLAG_FUSED_W
 
 TILES = {"auto": 0, "128x128": 1, "96x96": 2, "64x64": 3, "32x32": 4, "128x64": 5, "64x128": 6}
@@ -300,6 +302,17 @@ def last_launch_count():
 def check_device_error():
     """Raise FmmError(FMM_ERR_TIMEOUT) if a bounded device wait gave up."""
     _check(_lib.lib().fmm_check_device_error(), "device")
+
+
+def set_wait_limit(ns):
+    """Time limit (ns) of the tensor-core kernels' bounded waits (fmm_set_wait_limit)."""
+    _check(_lib.lib().fmm_set_wait_limit(int(ns)), "set_wait_limit")
+
+
+def selftest_wait_timeout(kernel, ns, stream=None):
+    """Status of fmm_selftest_wait_timeout: FMM_ERR_TIMEOUT when the dry
+    kernel's wait ran out as it should (kernel 0: residue GEMM, 1: TF32)."""
+    return _lib.lib().fmm_selftest_wait_timeout(int(kernel), int(ns), _stream_handle(stream))
 
 
 def timing_enable(on=True):

@@ -73,6 +73,10 @@ def _declare(L):
     L.fmm_timing_enable.restype = st
     L.fmm_timing_leaf_ms.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.fmm_timing_leaf_ms.restype = st
+    L.fmm_set_wait_limit.argtypes = [ctypes.c_uint64]
+    L.fmm_set_wait_limit.restype = st
+    L.fmm_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_uint64, c_p]
+    L.fmm_selftest_wait_timeout.restype = st
     L.fmm_status_string.argtypes = [ctypes.c_int]
     L.fmm_status_string.restype = ctypes.c_char_p
 

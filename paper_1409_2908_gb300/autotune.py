@@ -41,6 +41,65 @@ TF32_TFLOPS = {"tf32": 850.0, "fp32": 550.0}   # leaf launch, TF32 work per seco
 TF32_ERR = {"tf32": (3e-4, 2.0), "fp32": (4e-6, 1.1)}   # (e_F at 0 levels, growth per level)
 
 
+def _transpose_case(M, K, N, U, V, W):
+    """<M,K,N;R> -> <N,K,M;R> from C^T = B^T A^T (Section 2.3, Prop. 2.1):
+    the new A is B^T (block (c,b) = B_bc^T), the new B is A^T and the new C
+    is C^T, and each product (S_r T_r)^T = T_r^T S_r^T keeps its index r."""
+    import numpy as np
+    R = U.shape[1]
+    U2, V2, W2 = np.zeros((N * K, R)), np.zeros((K * M, R)), np.zeros((N * M, R))
+    for b in range(K):
+        for c in range(N):
+            U2[c * K + b] = V[b * N + c]
+    for a in range(M):
+        for b in range(K):
+            V2[b * M + a] = U[a * K + b]
+        for c in range(N):
+            W2[c * M + a] = W[a * N + c]
+    return N, K, M, U2, V2, W2
+
+
+def _cycle_case(M, K, N, U, V, W):
+    """<M,K,N;R> -> <K,N,M;R> by the cyclic symmetry of the matmul tensor
+    (Section 2.3, Prop. 2.2): sum_r U_(a,b)r V_(b,c)r W_(a,c)r is unchanged
+    when the roles rotate, so [[V, W', U']] with W' indexed (c,a) and U'
+    indexed (b,a) is an exact <K,N,M> algorithm."""
+    import numpy as np
+    R = U.shape[1]
+    V2, W2 = np.zeros((N * M, R)), np.zeros((K * M, R))
+    for a in range(M):
+        for c in range(N):
+            V2[c * M + a] = W[a * N + c]
+        for b in range(K):
+            W2[b * M + a] = U[a * K + b]
+    return K, N, M, V.copy(), V2, W2
+
+
+PERMS = ("", "c", "cc", "t", "tc", "tcc")   # identity, cycles, transpose then cycles
+
+
+def permuted_factors(name, perm):
+    """(M, K, N, U, V, W) of a shipped base case under a permutation of its
+    dimensions: "c" cycles <M,K,N> to <K,N,M>, "t" transposes it to <N,K,M>;
+    the six strings of PERMS give every ordering of (M, K, N).  Every result
+    is checked exactly by fmm_plan_create when a plan is built from it."""
+    from . import algorithm_factors
+    f = algorithm_factors(name)
+    for op in perm:
+        f = _transpose_case(*f) if op == "t" else _cycle_case(*f)
+    return f
+
+
+_FACTORS = {}
+
+
+def _factors(name, perm):
+    key = (name, perm)
+    if key not in _FACTORS:
+        _FACTORS[key] = permuted_factors(name, perm)
+    return _FACTORS[key]
+
+
 @dataclass(frozen=True)
 class Choice:
     algorithm: str            # algorithm file name (levels 0: the classical product)
@@ -48,14 +107,25 @@ class Choice:
     flags: int
     precision: str            # "fp64", "ozaki_bf16", "tf32" or "fp32"
     moduli: int = 15
-    tile: str = "auto"
+    tile: str = "auto"        # leaf tile (FP64 leaf GEMM tiles; 128x128 narrows the tensor-core tiles)
     model_ms: float = 0.0
     measured_ms: float = -1.0
+    perm: str = ""            # permutation of the base case (PERMS)
+    measured_err: float = -1.0   # e_F of the chosen moduli against a 16-moduli product (emulated)
+
+    @property
+    def label(self):
+        p = f"[{self.perm}]" if self.perm else ""
+        m = f" x{self.moduli}" if self.precision == "ozaki_bf16" else ""
+        return f"{self.algorithm}{p} L{self.levels} {self.precision}{m} tile {self.tile}"
 
     def plan(self):
+        mod = self.moduli if self.precision == "ozaki_bf16" else None
+        if self.perm and self.levels > 0:
+            return fmm.Plan(levels=self.levels, flags=self.flags, precision=self.precision, tile=self.tile,
+                            factors=_factors(self.algorithm, self.perm), moduli=mod)
         return fmm.Plan(self.algorithm, levels=self.levels, flags=self.flags,
-                        precision=self.precision, tile=self.tile,
-                        moduli=self.moduli if self.precision == "ozaki_bf16" else None)
+                        precision=self.precision, tile=self.tile, moduli=mod)
 
 
 _ALGS = None
@@ -76,10 +146,40 @@ def algorithms():
     return out
 
 
+def cases():
+    """Every base case with its permutations: (name, perm) -> (M, K, N, R),
+    one entry per distinct (M, K, N) of each shipped algorithm."""
+    out = {}
+    for name, (M, K, N, R) in algorithms().items():
+        seen = set()
+        for perm in PERMS:
+            dims = (M, K, N)
+            for op in perm:
+                a, b, c = dims
+                dims = (c, b, a) if op == "t" else (b, c, a)
+            if dims in seen:
+                continue
+            seen.add(dims)
+            out[(name, perm)] = dims + (R,)
+    return out
+
+
+def beta_for(n, k):
+    """Width of the scaled integers with n moduli (the library's rule)."""
+    P = 1
+    for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
+        P *= p
+    beta = 62
+    while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
+        beta -= 1
+    return beta
+
+
 def moduli_for(tol, k):
-    """Fewest moduli whose truncation error 2^(1-beta) (with a factor 4 of
-    slack; measured e_F on uniform data is about 0.9 x 2^(1-beta)) meets the
-    relative tolerance."""
+    """Fewest moduli whose rounding error 2^-beta (with a factor 2 of slack;
+    the e_F measured on uniform data is about 0.9 x 2^-beta once the scaled
+    operands are rounded to nearest) meets the relative tolerance: the prior
+    that measured trials then correct."""
     for n in range(6, 17):
         P = 1
         for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
@@ -87,7 +187,7 @@ def moduli_for(tol, k):
         beta = 62
         while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
             beta -= 1
-        if 4 * 2.0 ** (1 - beta) <= tol:
+        if 2 * 2.0 ** (-beta) <= tol:
             return n
     return None
 
@@ -105,15 +205,26 @@ def classical_efficiency(m, n, tile=128, tile_n=None, planes=1):
     return max(fill * waves, 0.02)
 
 
+# relative speed of each FP64 leaf tile per flop (the 128 x 128 tile runs at
+# 97 % of the DFMA ceiling; smaller tiles pay more shared-memory traffic)
+FP64_TILES = {"128x128": (128, 128, 1.0), "128x64": (128, 64, 0.95), "64x128": (64, 128, 0.95),
+              "96x96": (96, 96, 0.93), "64x64": (64, 64, 0.85), "32x32": (32, 32, 0.6)}
+# tensor-core tiles: 128 x 256 ("auto" where the leaves are at least 256 wide)
+# or 128 x 128 ("128x128"), relative speed per flop
+TC_TILES = {"auto": 1.0, "128x128": 0.92}
+FUSED_BLOCKS = (1, 4, 6, 8, 9)   # block grids with a fused first-level split in the library
+
+
 class Autotuner:
     def __init__(self, tol=1e-11, precisions=("fp64", "ozaki_bf16"), max_levels=3,
-                 trials=3, cache_file=None, measure=True):
+                 trials=3, cache_file=None, measure=True, permutations=True):
         self.tol = tol
         self.precisions = tuple(precisions)
         self.max_levels = max_levels
         self.trials = trials
         self.cache_file = cache_file
         self.measure = measure
+        self.permutations = permutations
         self._cache = {}
         self._plans = {}
         if cache_file and os.path.exists(cache_file):
@@ -123,22 +234,20 @@ class Autotuner:
 
     # ----------------------------------------------------------- model
     def candidates(self, m, k, n):
-        """Every admissible candidate with its model time (ms), best first."""
+        """Every admissible candidate with its model time (ms), best first:
+        each shipped base case and (with permutations) each ordering of its
+        dimensions (Section 2.3), at 0..max_levels levels, every listed leaf
+        precision, with the leaf tile the model prefers."""
         out = []
-        algs = algorithms()
         nmod = moduli_for(self.tol, k) if "ozaki_bf16" in self.precisions else None
-        emulated = "ozaki_bf16" in self.precisions and nmod is not None
+        allc = cases() if self.permutations else {(nm, ""): b for nm, b in algorithms().items()}
         for prec in self.precisions:
             if prec == "ozaki_bf16" and nmod is None:
                 continue
             if prec in TF32_ERR and 2 * TF32_ERR[prec][0] > self.tol:
                 continue
-            # the DFMA pipe is ~1/100 of the emulated rate: FP64 plans only
-            # compete on products too small for the tensor-core path to fill
-            if prec == "fp64" and emulated and min(m, k, n) >= 64:
-                continue
-            out.append(self._model(m, k, n, "strassen_222_7", (2, 2, 2, 7), 0, prec, nmod))
-            for name, base in algs.items():
+            out.append(self._model(m, k, n, "strassen_222_7", "", (2, 2, 2, 7), 0, prec, nmod))
+            for (name, perm), base in allc.items():
                 M, K, N, R = base
                 for L in range(1, self.max_levels + 1):
                     mL, kL, nL = m // M ** L, k // K ** L, n // N ** L
@@ -146,13 +255,13 @@ class Autotuner:
                         break
                     if prec == "ozaki_bf16" and R ** L * nmod > 65535:
                         break
-                    out.append(self._model(m, k, n, name, base, L, prec, nmod))
+                    out.append(self._model(m, k, n, name, perm, base, L, prec, nmod))
         # FP64 error grows with depth; drop plans that cannot meet the target
         out = [c for c in out if c is not None]
         out.sort(key=lambda c: c.model_ms)
         return out
 
-    def _model(self, m, k, n, name, base, L, prec, nmod):
+    def _model(self, m, k, n, name, perm, base, L, prec, nmod):
         M, K, N, R = base
         if prec == "fp64" and L > 0 and self.tol < 1e-13 * (2.0 ** L):
             return None
@@ -163,9 +272,15 @@ class Autotuner:
         mL, kL, nL = mp // sm, kp // sk, np_ // sn
         leaves = R ** L
         fringe = 2.0 * (m * n * k - mp * np_ * kp)
+        tile = "auto"
         if prec == "fp64":
             leaf_flops = 2.0 * leaves * mL * kL * nL
-            t = leaf_flops / (FP64_TFLOPS * 1e12 * classical_efficiency(mL, nL))
+            best = None
+            for tname, (bm, bn, speed) in FP64_TILES.items():
+                tt = leaf_flops / (FP64_TFLOPS * 1e12 * speed * classical_efficiency(mL, nL, bm, bn, leaves))
+                if best is None or tt < best[0]:
+                    best = (tt, tname)
+            t, tile = best
             # level-by-level additions: bytes moved per level
             adds = 0.0
             for l in range(1, L + 1):
@@ -177,9 +292,14 @@ class Autotuner:
             # leaves on the TF32 tensor path; S/T and W level by level in FP64
             split = 3 if prec == "fp32" else 1
             kpad = -(-kL // 32) * 32
-            tile_n = 256 if (nL >= 256 and split == 1) else 128
-            t = 2.0 * leaves * mL * kpad * split * nL / (
-                TF32_TFLOPS[prec] * 1e12 * classical_efficiency(mL, nL, 128, tile_n, leaves))
+            best = None
+            for tname, speed in TC_TILES.items():
+                tile_n = 256 if (nL >= 256 and split == 1 and tname == "auto") else 128
+                tt = 2.0 * leaves * mL * kpad * split * nL / (
+                    TF32_TFLOPS[prec] * 1e12 * speed * classical_efficiency(mL, nL, 128, tile_n, leaves))
+                if best is None or tt < best[0]:
+                    best = (tt, tname)
+            t, tile = best
             # FP64 operands to TF32 (8 bytes in, 4 split bytes out per element)
             t += leaves * (mL * kL + kL * nL) * (8 + 4 * split) / (HBM_GBS * 1e9)
             adds = 0.0
@@ -191,8 +311,14 @@ class Autotuner:
             flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
         else:
             kpad = -(-kL // 64) * 64
-            t = 2.0 * leaves * nmod * mL * kpad * nL / (
-                TC_TFLOPS * 1e12 * classical_efficiency(mL, nL, 128, 256 if nL >= 256 else 128, leaves * nmod))
+            best = None
+            for tname, speed in TC_TILES.items():
+                tile_n = 256 if (nL >= 256 and tname == "auto") else 128
+                tt = 2.0 * leaves * nmod * mL * kpad * nL / (
+                    TC_TFLOPS * 1e12 * speed * classical_efficiency(mL, nL, 128, tile_n, leaves * nmod))
+                if best is None or tt < best[0]:
+                    best = (tt, tname)
+            t, tile = best
             # exponents, then the fused first level: FP64 in, R/(MK) residue
             # planes out per operand element (bfloat16 when it is the last level)
             grow_a = R / (M * K) if L else 1.0
@@ -200,37 +326,56 @@ class Autotuner:
             width = 2 if L <= 1 else 1
             t += (mp * kp + kp * np_) * 8 * 2 / (HBM_GBS * 1e9)
             t += (mp * kp * (8 + grow_a * nmod * width) + kp * np_ * (8 + grow_b * nmod * width)) / (SPLIT_GBS * 1e9)
+            if L and (M * K not in FUSED_BLOCKS or K * N not in FUSED_BLOCKS):
+                # no fused first level for this block grid: a residue pass first
+                t += (mp * kp + kp * np_) * (8 + 2 * nmod) / (LEVEL_GBS * 1e9)
             for l in range(2, L + 1):
                 w = 2 if l == L else 1
                 ml, kl, nl = mp // M ** l, kp // K ** l, np_ // N ** l
                 t += R ** l * (ml * kl + kl * nl) * nmod * (2 + w) / (LEVEL_GBS * 1e9)
                 t += R ** (l - 1) * M * N * ml * nl * nmod * 3 / (LEVEL_GBS * 1e9)
-            terms = (self._w_terms(name) / (M * N)) if L else 1.0
+            terms = (self._w_terms(name, perm) / (M * N)) if L else 1.0
             t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12 * (1.0 + W_TERM_FACTOR * (terms - 1.0))
             t += (6 + 3 * max(L - 1, 0)) * LAUNCH_US * 1e-6
             flags = fmm.FLAGS_DEFAULT
         t += fringe / (FP64_TFLOPS * 1e12)
-        return Choice(name, L, flags, prec, nmod or 15, "auto", 1e3 * t)
+        return Choice(name, L, flags, prec, nmod or 15, tile, 1e3 * t, perm=perm if L else "")
 
-    def _w_terms(self, name):
-        """Nonzeros of the base case's W (terms of the top-level W combination)."""
+    def _w_terms(self, name, perm=""):
+        """Nonzeros of the (permuted) base case's W (terms of the top-level W
+        combination)."""
         if not hasattr(self, "_wnnz"):
             self._wnnz = {}
-        if name not in self._wnnz:
-            from . import algorithm_factors
-            self._wnnz[name] = int((algorithm_factors(name)[5] != 0).sum())
-        return self._wnnz[name]
+        if (name, perm) not in self._wnnz:
+            self._wnnz[(name, perm)] = int((_factors(name, perm)[5] != 0).sum())
+        return self._wnnz[(name, perm)]
 
     # ----------------------------------------------------------- choice
     def choose(self, m, k, n):
+        """The choice for (m, k, n).  Without measurement: the model's best.
+        With measurement: the model's best few, each checked for accuracy
+        against a 16-moduli emulated classical product on random uniform
+        operands of the shape (the emulated candidates' moduli count moved up
+        or down until its measured e_F meets the target with the fewest
+        moduli), then timed (median of three calls); the fastest kept."""
         key = f"{m}x{k}x{n}:{self.tol:g}:{','.join(self.precisions)}"
         if key in self._cache:
             return self._cache[key]
         cands = self.candidates(m, k, n)
         best = cands[0]
-        if self.measure and self.trials > 1:
-            timed = [self._time(c, m, k, n) for c in cands[:self.trials]]
-            best = min(timed, key=lambda c: c.measured_ms)
+        if self.measure and self.trials > 0:
+            import torch
+            A = torch.rand((m, k), dtype=torch.float64, device="cuda") * 2 - 1
+            B = torch.rand((k, n), dtype=torch.float64, device="cuda") * 2 - 1
+            ref = self._run(Choice("strassen_222_7", 0, fmm.FLAGS_DEFAULT, "ozaki_bf16", 16), A, B)
+            timed = []
+            for c in cands[:self.trials]:
+                c2 = self._fit_accuracy(c, A, B, ref)
+                if c2 is not None:
+                    timed.append(self._time(c2, A, B))
+            if timed:
+                best = min(timed, key=lambda c: c.measured_ms)
+            del A, B, ref
         self._cache[key] = best
         if self.cache_file:
             with open(self.cache_file, "w") as fh:
@@ -239,25 +384,68 @@ class Autotuner:
 
     def plan(self, m, k, n):
         c = self.choose(m, k, n)
-        key = (c.algorithm, c.levels, c.flags, c.precision, c.moduli, c.tile)
+        key = (c.algorithm, c.perm, c.levels, c.flags, c.precision, c.moduli, c.tile)
         if key not in self._plans:
             self._plans[key] = c.plan()
         return self._plans[key]
 
-    def _time(self, c, m, k, n):
+    @staticmethod
+    def _run(c, A, B, plan=None):
         import torch
-        p = c.plan()
-        A = torch.rand((m, k), dtype=torch.float64, device="cuda") * 2 - 1
-        B = torch.rand((k, n), dtype=torch.float64, device="cuda") * 2 - 1
+        p = plan or c.plan()
+        m, k = A.shape
+        n = B.shape[1]
         C = torch.empty((m, n), dtype=torch.float64, device="cuda")
         wsz = p.workspace_size(m, k, n)
         ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
         fmm.gemm(p, A, B, C=C, workspace=ws)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
+        return C
+
+    @staticmethod
+    def _err(C, ref):
+        import torch
+        return float(torch.linalg.norm(C - ref) / torch.linalg.norm(ref))
+
+    def _fit_accuracy(self, c, A, B, ref):
+        """The candidate with its measured e_F, or None if it misses the
+        target; emulated candidates get the fewest moduli (<= 16) that meet it."""
+        if c.precision != "ozaki_bf16":
+            e = self._err(self._run(c, A, B), ref)
+            return Choice(**{**asdict(c), "measured_err": e}) if e <= self.tol else None
+        nm = c.moduli
+        e = self._err(self._run(Choice(**{**asdict(c), "moduli": nm}), A, B), ref)
+        while e > self.tol and nm < 16:
+            nm += 1
+            e = self._err(self._run(Choice(**{**asdict(c), "moduli": nm}), A, B), ref)
+        if e > self.tol:
+            return None
+        while nm > 3:
+            e2 = self._err(self._run(Choice(**{**asdict(c), "moduli": nm - 1}), A, B), ref)
+            if e2 > self.tol:
+                break
+            nm, e = nm - 1, e2
+        return Choice(**{**asdict(c), "moduli": nm, "measured_err": e})
+
+    def _time(self, c, A, B, reps=3):
+        """Median of `reps` timed calls after one untimed call."""
+        import statistics
+        import torch
+        p = c.plan()
+        m, k = A.shape
+        n = B.shape[1]
+        C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+        wsz = p.workspace_size(m, k, n)
+        ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
         fmm.gemm(p, A, B, C=C, workspace=ws)
-        e1.record()
-        e1.synchronize()
-        return Choice(**{**asdict(c), "measured_ms": e0.elapsed_time(e1)})
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fmm.gemm(p, A, B, C=C, workspace=ws)
+            e1.record()
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return Choice(**{**asdict(c), "measured_ms": statistics.median(times)})

@@ -50,6 +50,7 @@ cudaEvent_t timing_mark(cudaStream_t s) {
 void timing_unmark() {
     if (t_timing.used > 0) --t_timing.used;
 }
+void set_last_launch_count(int n) { t_launches = n; }
 }  // namespace fmm
 
 namespace {
@@ -136,6 +137,7 @@ ResPlan res_plan(const fmm_plan *p) {
     rp.v_ptr = p->dev.lv_ptr; rp.v_code = p->dev.lv_code; rp.v_icoef = p->dev.lv_icoef;
     rp.vt_code = p->dev.lvt_code;
     rp.w_ptr = p->dev.lw_ptr; rp.w_r = p->dev.lw_r; rp.w_icoef = p->dev.lw_icoef;
+    rp.tile = p->tile;
     rp.w_absmax = 0;
     for (int q = 0; q < p->M * p->N; ++q) {
         double sum = 0;
@@ -243,7 +245,10 @@ fmm_status ensure_uploaded(fmm_plan *p) {
     } catch (const std::bad_alloc &) {
         st = FMM_ERR_NO_MEMORY;
     }
-    if (st == FMM_OK) p->uploaded = true;
+    if (st == FMM_OK) {
+        p->uploaded = true;
+        cudaGetDevice(&p->upload_device);
+    }
     return st;
 }
 
@@ -362,6 +367,82 @@ cudaError_t copy_band(void *ctx, int64_t r0, int64_t r1, int64_t block_rows, int
     return cudaSuccess;
 }
 
+// One recursive level of S (side 0, from parents with an M x K block grid)
+// or T (side 1, K x N) in the plan's addition scheme (Section 3.2):
+// write-once, streaming or pairwise.
+cudaError_t form_level(const fmm_plan *p, int side, const double *par, int64_t pld, int64_t pst,
+                       int64_t parents, int64_t rows, int64_t cols, double *out, cudaStream_t s, int *launches) {
+    const int gR = side ? p->K : p->M, gC = side ? p->N : p->K;
+    const int *ptr = side ? p->dev.lv_ptr : p->dev.lu_ptr, *code = side ? p->dev.lv_code : p->dev.lu_code;
+    const double *coef = side ? p->dev.lv_coef : p->dev.lu_coef;
+    const std::vector<double> &F = side ? p->V : p->U;
+    size_t nnz = 0;
+    for (double x : F) nnz += x != 0.0;
+    if ((p->flags & FMM_FLAG_STREAMING) && nnz <= 512 && p->R <= 128 && gR * gC <= 64)
+        return launch_level_stream(par, pld, pst, parents, rows, cols, gR, gC, p->R, ptr, code, coef, out, s,
+                                   launches);
+    if (p->flags & FMM_FLAG_PAIRWISE) {
+        const int64_t per = rows * cols;
+        for (int r = 0; r < p->R; ++r) {
+            bool first = true;
+            for (int i = 0; i < gR * gC; ++i) {
+                const double c = F[size_t(i) * p->R + r];
+                if (c == 0.0) continue;
+                const double *X = par + (int64_t)(i / gC) * rows * pld + (int64_t)(i % gC) * cols;
+                cudaError_t e = launch_block_axpy(X, pld, pst, out + r * per, cols, p->R * per, parents, rows,
+                                                  cols, c, first ? 1 : 0, s, launches);
+                if (e != cudaSuccess) return e;
+                first = false;
+            }
+            if (first) {   // no terms: the child is zero (0 x, inputs are finite)
+                cudaError_t e = launch_block_axpy(par, pld, pst, out + r * per, cols, p->R * per, parents, rows,
+                                                  cols, 0.0, 1, s, launches);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+    return launch_level_form(par, pld, pst, parents, rows, cols, p->R, ptr, code, coef, out, s, launches);
+}
+
+// One recursive level of the W combination in the plan's addition scheme:
+// the MN blocks of each parent (ld pld, parents pst apart) from its R child
+// products (packed rows x cols, consecutive).
+cudaError_t w_level(const fmm_plan *p, const double *child, int64_t rows, int64_t cols, double *parent,
+                    int64_t pld, int64_t pst, int64_t parents, int accumulate, cudaStream_t s, int *launches) {
+    const int MN = p->M * p->N;
+    size_t nnz = 0;
+    for (double x : p->W) nnz += x != 0.0;
+    if ((p->flags & FMM_FLAG_STREAMING) && nnz <= 512 && p->R <= 128 && MN <= 128)
+        return launch_level_w_stream(child, rows, cols, p->R, p->N, MN, parent, pld, pst, parents, p->dev.lw_ptr,
+                                     p->dev.lw_r, p->dev.lw_coef, accumulate, s, launches);
+    if (p->flags & FMM_FLAG_PAIRWISE) {
+        const int64_t per = rows * cols;
+        for (int q = 0; q < MN; ++q) {
+            double *Y = parent + (int64_t)(q / p->N) * rows * pld + (int64_t)(q % p->N) * cols;
+            bool first = !accumulate;
+            bool any = false;
+            for (int r = 0; r < p->R; ++r) {
+                const double w = p->W[size_t(q) * p->R + r];
+                if (w == 0.0) continue;
+                cudaError_t e = launch_block_axpy(child + r * per, cols, p->R * per, Y, pld, pst, parents, rows,
+                                                  cols, w, first ? 1 : 0, s, launches);
+                if (e != cudaSuccess) return e;
+                first = false;
+                any = true;
+            }
+            if (!any && !accumulate) {
+                cudaError_t e = launch_block_axpy(child, cols, p->R * per, Y, pld, pst, parents, rows, cols, 0.0, 1,
+                                                  s, launches);
+                if (e != cudaSuccess) return e;
+            }
+        }
+        return cudaSuccess;
+    }
+    return launch_level_w(child, rows, cols, p->R, p->N, MN, parent, pld, pst, parents, p->dev.lw_ptr, p->dev.lw_r,
+                          p->dev.lw_coef, accumulate, s, launches);
+}
+
 // Emulated-FP64 leaves: FP64 level-by-level S/T, tensor-core residue
 // products, FP64 level-by-level W; classical FP64 fringe.
 fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, const double *A,
@@ -379,9 +460,9 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
                              int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
                              int64_t mm, int64_t kk, int64_t nn) {
         return tf ? tf32_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, 0,
-                                  wsb + wl.oz, s, launches, tf32_split(p))
+                                  wsb + wl.oz, s, launches, tf32_split(p), p->tile)
                   : ozaki_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, p->nmod,
-                                   wsb + wl.oz, s, launches);
+                                   wsb + wl.oz, s, launches, p->tile);
     };
     if (p->L == 0)
         return cuda_status(tf ? leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n)
@@ -411,11 +492,9 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
         const int64_t ml = g.mp / ipow(p->M, l), kl = g.kp / ipow(p->K, l), nl = g.np / ipow(p->N, l);
         double *oa = (double *)(wsb + wl.lvS[l - 1]);
         double *ob = (double *)(wsb + wl.lvT[l - 1]);
-        if ((e = launch_level_form(pa, pld_a, pst_a, parents, ml, kl, p->R, p->dev.lu_ptr,
-                                   p->dev.lu_code, p->dev.lu_coef, oa, s, launches)) != cudaSuccess)
+        if ((e = form_level(p, 0, pa, pld_a, pst_a, parents, ml, kl, oa, s, launches)) != cudaSuccess)
             return cuda_status(e);
-        if ((e = launch_level_form(pb, pld_b, pst_b, parents, kl, nl, p->R, p->dev.lv_ptr,
-                                   p->dev.lv_code, p->dev.lv_coef, ob, s, launches)) != cudaSuccess)
+        if ((e = form_level(p, 1, pb, pld_b, pst_b, parents, kl, nl, ob, s, launches)) != cudaSuccess)
             return cuda_status(e);
         pa = oa; pld_a = kl; pst_a = ml * kl;
         pb = ob; pld_b = nl; pst_b = kl * nl;
@@ -437,9 +516,8 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
         double *parent = l == 1 ? C : (double *)(wsb + wl.lvP[l - 2]);
         const int64_t pld = l == 1 ? ldc : nl * p->N;
         const int64_t pst = l == 1 ? 0 : (ml * p->M) * (nl * p->N);
-        if ((e = launch_level_w(child, ml, nl, p->R, p->N, p->M * p->N, parent, pld, pst, lparents,
-                                p->dev.lw_ptr, p->dev.lw_r, p->dev.lw_coef, (l == 1 && kfringe) ? 1 : 0,
-                                s, launches)) != cudaSuccess)
+        if ((e = w_level(p, child, ml, nl, parent, pld, pst, lparents, (l == 1 && kfringe) ? 1 : 0, s,
+                         launches)) != cudaSuccess)
             return cuda_status(e);
         lparents /= p->R;
     }
@@ -503,11 +581,9 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
             const int64_t ml = g.mp / ipow(p->M, l), kl = g.kp / ipow(p->K, l), nl = g.np / ipow(p->N, l);
             double *oa = (double *)(wsb + wl.lvS[l - 1]);
             double *ob = (double *)(wsb + wl.lvT[l - 1]);
-            if ((e = launch_level_form(pa, pld_a, pst_a, parents, ml, kl, p->R, p->dev.lu_ptr,
-                                       p->dev.lu_code, p->dev.lu_coef, oa, s, launches)) != cudaSuccess)
+            if ((e = form_level(p, 0, pa, pld_a, pst_a, parents, ml, kl, oa, s, launches)) != cudaSuccess)
                 return cuda_status(e);
-            if ((e = launch_level_form(pb, pld_b, pst_b, parents, kl, nl, p->R, p->dev.lv_ptr,
-                                       p->dev.lv_code, p->dev.lv_coef, ob, s, launches)) != cudaSuccess)
+            if ((e = form_level(p, 1, pb, pld_b, pst_b, parents, kl, nl, ob, s, launches)) != cudaSuccess)
                 return cuda_status(e);
             pa = oa; pld_a = kl; pst_a = ml * kl;
             pb = ob; pld_b = nl; pst_b = kl * nl;
@@ -591,9 +667,8 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
                 double *parent = l == 1 ? C : (double *)(wsb + wl.lvP[l - 2]);
                 const int64_t pld = l == 1 ? ldc : nl * p->N;
                 const int64_t pst = l == 1 ? 0 : (ml * p->M) * (nl * p->N);
-                if ((e = launch_level_w(child, ml, nl, p->R, p->N, p->M * p->N, parent, pld, pst,
-                                        parents, p->dev.lw_ptr, p->dev.lw_r, p->dev.lw_coef,
-                                        (l == 1 && kfringe) ? 1 : 0, s, launches)) != cudaSuccess)
+                if ((e = w_level(p, child, ml, nl, parent, pld, pst, parents, (l == 1 && kfringe) ? 1 : 0, s,
+                                 launches)) != cudaSuccess)
                     return cuda_status(e);
                 parents /= p->R;
             }
@@ -646,8 +721,9 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16 && prec != FMM_PREC_TF32 && prec != FMM_PREC_FP32)
         return FMM_ERR_UNSUPPORTED;
     if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE |
-                          FMM_FLAG_LEAF_EMULATION))
+                          FMM_FLAG_LEAF_EMULATION | FMM_FLAG_STREAMING | FMM_FLAG_PAIRWISE))
         return FMM_ERR_ARG;
+    if ((flags & FMM_FLAG_STREAMING) && (flags & FMM_FLAG_PAIRWISE)) return FMM_ERR_ARG;
     bool representable = true;
     if (!brent_exact(M, K, N, R, U, V, W, &representable))
         return representable ? FMM_ERR_INVALID_ALGORITHM : FMM_ERR_UNSUPPORTED;
@@ -719,6 +795,23 @@ fmm_status fmm_check_device_error(void) {
     if (read_device_error(&flag, true) != cudaSuccess) return FMM_ERR_CUDA;
     if (read_tf32_error(&flag2, true) != cudaSuccess) return FMM_ERR_CUDA;
     return (flag || flag2) ? FMM_ERR_TIMEOUT : FMM_OK;
+}
+
+fmm_status fmm_set_wait_limit(uint64_t ns) {
+    if (ns == 0) return FMM_ERR_ARG;
+    set_wait_limit_ns(ns);
+    return FMM_OK;
+}
+
+fmm_status fmm_selftest_wait_timeout(int kernel, uint64_t ns, void *stream) {
+    if ((kernel != 0 && kernel != 1) || ns == 0) return FMM_ERR_ARG;
+    const cudaError_t e = kernel == 0 ? residue_gemm_timeout_probe(ns, (cudaStream_t)stream)
+                                      : tf32_gemm_timeout_probe(ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? FMM_ERR_NO_MEMORY : FMM_ERR_CUDA;
+    }
+    return fmm_check_device_error();
 }
 
 fmm_status fmm_plan_info(fmm_plan_t p, fmm_plan_info_t *info) {

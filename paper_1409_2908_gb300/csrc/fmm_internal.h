@@ -77,6 +77,7 @@ struct fmm_plan {
     fmm::DevicePlan dev;                     // uploaded on first use
     std::mutex upload_mu;
     bool uploaded = false;
+    int upload_device = -1;                  // device holding `dev` once uploaded
     fmm_precision prec = FMM_PREC_FP64;
     int nmod = 15;                           // moduli of the emulated-FP64 variant
     bool integer_coefs = false;              // every base coefficient an integer in [-127, 127]
@@ -135,9 +136,22 @@ cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int 
                            int MN, double *parent, int64_t parent_ld, int64_t parent_stride,
                            int64_t parents, const int *w_ptr, const int *w_r, const double *w_coef,
                            int accumulate, cudaStream_t s, int *launches);
+cudaError_t launch_level_stream(const double *parent, int64_t parent_ld, int64_t parent_stride,
+                                int64_t parents, int64_t rows, int64_t cols, int gridR, int gridC, int R,
+                                const int *ptr, const int *code, const double *coef, double *out,
+                                cudaStream_t s, int *launches);
+cudaError_t launch_level_w_stream(const double *child, int64_t rows, int64_t cols, int R, int gridN, int MN,
+                                  double *parent, int64_t parent_ld, int64_t parent_stride, int64_t parents,
+                                  const int *w_ptr, const int *w_r, const double *w_coef, int accumulate,
+                                  cudaStream_t s, int *launches);
+cudaError_t launch_block_axpy(const double *X, int64_t xld, int64_t xstride, double *Y, int64_t yld,
+                              int64_t ystride, int64_t parents, int64_t rows, int64_t cols, double c,
+                              int first, cudaStream_t s, int *launches);
 cudaError_t launch_classical(const double *A, int64_t lda, const double *B, int64_t ldb,
                              double *C, int64_t ldc, int64_t m, int64_t k, int64_t n,
                              int tile, cudaStream_t s, int *launches);
+// api.cu: launch count reported by fmm_last_launch_count (this host thread)
+void set_last_launch_count(int n);
 // api.cu: CUDA event pairs around the dominant launch (fmm_timing_enable)
 cudaEvent_t timing_mark(cudaStream_t s);
 void timing_unmark();
@@ -149,8 +163,14 @@ size_t ozaki_workspace(int64_t leaves, int nmod, int64_t m, int64_t k, int64_t n
 cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                            int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
                            int64_t m, int64_t k, int64_t n, int nmod, void *ws, cudaStream_t s,
-                           int *launches);
+                           int *launches, int tile = FMM_TILE_AUTO);
 cudaError_t read_device_error(int *flag, bool clear);
+// time limit of the tensor-core kernels' bounded waits (fmm_set_wait_limit)
+unsigned long long wait_limit_ns();
+void set_wait_limit_ns(unsigned long long ns);
+// kernels of the timeout tests: a wait that nothing completes runs out
+cudaError_t residue_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
+cudaError_t tf32_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
 cudaError_t ozaki_prepare(int nmod);          // constant tables, kernel attributes
 cudaError_t prepare_fp64_kernels();           // kernel attributes of every tile
 // tf32.cu
@@ -160,7 +180,7 @@ cudaError_t read_tf32_error(int *flag, bool clear);
 cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
                           int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
-                          int split = 1);
+                          int split = 1, int tile = FMM_TILE_AUTO);
 // residue-space recursion (integer base coefficients only)
 struct ResPlan {
     int M, K, N, R, L;
@@ -170,6 +190,7 @@ struct ResPlan {
     const int *w_ptr, *w_r, *w_icoef;
     int w_absmax;                            // max over C blocks of sum_r |W_qr|
     int u_absmax, v_absmax;                  // max over r of sum_i |U_ir|, of sum_j |V_jr|
+    int tile;                                // the plan's fmm_tile (128x128: narrow GEMM tiles)
 };
 size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod);
 // Overlap hooks of the host entry point.  b_ready (or null): an event the

@@ -61,15 +61,24 @@ __device__ __forceinline__ const double *term_base(int code, const double *X, in
     return slot + (int64_t)(-code - 1) * slot_stride;
 }
 
+// Coefficient tests on the integer pipe: on this GPU the FP64 pipe retires
+// 1/64 of the FP32 rate, and an FP64 compare per term and element costs as
+// much as the addition itself.
+__device__ __forceinline__ bool is_one(double c) { return __double_as_longlong(c) == 0x3FF0000000000000ll; }
+__device__ __forceinline__ bool is_minus_one(double c) {
+    return __double_as_longlong(c) == (long long)0xBFF0000000000000ull;
+}
+__device__ __forceinline__ bool is_zero(double c) { return (__double_as_longlong(c) << 1) == 0; }
+
 // Add coef * x into v; coefficients +-1 need no multiply.
 __device__ __forceinline__ double chain_step(double v, double c, double x) {
-    if (c == 1.0) return v + x;
-    if (c == -1.0) return v - x;
+    if (is_one(c)) return v + x;
+    if (is_minus_one(c)) return v - x;
     return fma(c, x, v);
 }
 
 __device__ __forceinline__ double chain_first(double c, double x) {
-    if (c == 1.0) return x;
+    if (is_one(c)) return x;
     return c * x;
 }
 
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
     for (int t = c0; t < c1; ++t) {
         const int code = p.c_code[t];
         const double w = p.c_coef[t];
-        if (w == 0.0) continue;
+        if (is_zero(w)) continue;
         double *Cb = opC + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
@@ -209,7 +218,7 @@ __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
             for (int j = 0; j < TN; ++j) {
                 const int64_t gc = col0 + tx + 16 * j;
                 if (gc >= p.nL) continue;
-                const double v = (w == 1.0) ? acc[i][j] : (w == -1.0 ? -acc[i][j] : w * acc[i][j]);
+                const double v = is_one(w) ? acc[i][j] : (is_minus_one(w) ? -acc[i][j] : w * acc[i][j]);
                 if (p.epi == EPI_ATOMIC)
                     atomicAdd(Cb + gr * p.ldc + gc, v);
                 else
@@ -384,7 +393,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
     for (int t = c0; t < c1; ++t) {
         const int code = p.c_code[t];
         const double w = p.c_coef[t];
-        if (w == 0.0) continue;
+        if (is_zero(w)) continue;
         double *Cb = opC + (int64_t)(code >> 16) * p.mL * p.ldc + (int64_t)(code & 0xffff) * p.nL;
 #pragma unroll
         for (int i = 0; i < TM; ++i) {
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) leaf_gemm_ws(const KParams p) {
             for (int j = 0; j < TN; ++j) {
                 const int64_t gc = col0 + tx + 16 * j;
                 if (gc >= p.nL) continue;
-                const double v = (w == 1.0) ? acc[i][j] : (w == -1.0 ? -acc[i][j] : w * acc[i][j]);
+                const double v = is_one(w) ? acc[i][j] : (is_minus_one(w) ? -acc[i][j] : w * acc[i][j]);
                 if (p.epi == EPI_ATOMIC)
                     atomicAdd(Cb + gr * p.ldc + gc, v);
                 else
@@ -440,7 +449,7 @@ __global__ void w_pass_kernel(double *C, int64_t ldc, int64_t mL, int64_t nL, in
             double v = accumulate ? Cb[i * ldc + j] : 0.0;
             for (int t = t0; t < t1; ++t) {
                 const double w = cq_coef[t];
-                if (w == 0.0) continue;
+                if (is_zero(w)) continue;
                 const double x = __ldg(wsM + (int64_t)cq_leaf[t] * mL * nL + i * nL + j);
                 v = chain_step(v, w, x);
             }
@@ -499,6 +508,105 @@ __global__ void level_w_kernel(const double *child, int64_t rows, int64_t cols, 
             }
             Pout[i * pld + j] = v;
         }
+    }
+}
+
+// Streaming additions (Section 3.2), one recursive level of S (or T): a
+// thread reads its element of all NB blocks of its parent once and writes
+// that element of every child, child r = sum_t c_t block(t) in list order
+// (the same operations in the same order as level_form_kernel, so the same
+// bits).  parent s: (gridR rows) x (gridC cols) blocks of rows x cols, ld
+// pld, parents pstride apart; children out[s*R + r] packed rows x cols.
+// Dynamic shared memory: NB x 256 doubles.
+__global__ void __launch_bounds__(256) level_stream_kernel(const double *parent, int64_t pld, int64_t pstride,
+                                                           int64_t rows, int64_t cols, int gridC, int NB,
+                                                           int R, int64_t parents, const int *ptr,
+                                                           const int *code, const double *coef,
+                                                           double *out) {
+    extern __shared__ double sx[];
+    __shared__ int sb[512];
+    __shared__ double sc[512];
+    __shared__ int sp[129];
+    const int nt = ptr[R];
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int cd = code[t];
+        sb[t] = (cd >> 16) * gridC + (cd & 0xffff);
+        sc[t] = coef[t];
+    }
+    for (int t = threadIdx.x; t <= R; t += blockDim.x) sp[t] = ptr[t];
+    __syncthreads();
+    const int64_t per = rows * cols;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= parents * per) return;
+    const int64_t sidx = pos / per, rem = pos % per, i = rem / cols, j = rem % cols;
+    const double *P = parent + sidx * pstride;
+    for (int b = 0; b < NB; ++b)
+        sx[b * 256 + threadIdx.x] = __ldg(P + ((int64_t)(b / gridC) * rows + i) * pld + (int64_t)(b % gridC) * cols + j);
+    double *O = out + sidx * R * per + rem;
+    for (int r = 0; r < R; ++r) {
+        const int t0 = sp[r], t1 = sp[r + 1];
+        double v = 0.0;
+        for (int t = t0; t < t1; ++t) {
+            const double x = sx[sb[t] * 256 + threadIdx.x];
+            v = (t == t0) ? chain_first(sc[t], x) : chain_step(v, sc[t], x);
+        }
+        O[(int64_t)r * per] = v;
+    }
+}
+
+// Streaming W combination, one level: a thread reads its element of all R
+// child products of parent s once and writes that element of each of the
+// MN blocks of s, block q = (old value if accumulate) + sum_t W_t child(r_t)
+// in list order (as level_w_kernel).  Dynamic shared memory: R x 128 doubles.
+__global__ void __launch_bounds__(128) level_w_stream_kernel(const double *child, int64_t rows, int64_t cols,
+                                                             int R, int gridN, int MN, double *parent,
+                                                             int64_t pld, int64_t pstride, int64_t parents,
+                                                             const int *w_ptr, const int *w_r,
+                                                             const double *w_coef, int accumulate) {
+    extern __shared__ double sx[];
+    __shared__ int sr[512];
+    __shared__ double sc[512];
+    __shared__ int sp[129];
+    const int nt = w_ptr[MN];
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        sr[t] = w_r[t];
+        sc[t] = w_coef[t];
+    }
+    for (int t = threadIdx.x; t <= MN; t += blockDim.x) sp[t] = w_ptr[t];
+    __syncthreads();
+    const int64_t per = rows * cols;
+    const int64_t pos = (int64_t)blockIdx.x * 128 + threadIdx.x;
+    if (pos >= parents * per) return;
+    const int64_t sidx = pos / per, rem = pos % per, i = rem / cols, j = rem % cols;
+    const double *X = child + sidx * R * per + rem;
+    for (int r = 0; r < R; ++r) sx[r * 128 + threadIdx.x] = __ldg(X + (int64_t)r * per);
+    double *Pb = parent + sidx * pstride + i * pld + j;
+    for (int q = 0; q < MN; ++q) {
+        double *dst = Pb + (int64_t)(q / gridN) * rows * pld + (int64_t)(q % gridN) * cols;
+        double v = accumulate ? *dst : 0.0;
+        bool first = !accumulate;
+        for (int t = sp[q]; t < sp[q + 1]; ++t) {
+            const double x = sx[sr[t] * 128 + threadIdx.x];
+            v = first ? chain_first(sc[t], x) : chain_step(v, sc[t], x);
+            first = false;
+        }
+        *dst = v;
+    }
+}
+
+// Pairwise additions (Section 3.2): one pass per term, Y_s = c X_s (first)
+// or Y_s + c X_s, for every parent s; X_s and Y_s are rows x cols blocks with
+// their own leading dimensions and parent strides.
+__global__ void __launch_bounds__(256) block_axpy_kernel(const double *X, int64_t xld, int64_t xstride, double *Y,
+                                                         int64_t yld, int64_t ystride, int64_t parents,
+                                                         int64_t rows, int64_t cols, double c, int first) {
+    const int64_t per = rows * cols;
+    for (int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x; pos < parents * per;
+         pos += (int64_t)gridDim.x * 256) {
+        const int64_t sidx = pos / per, rem = pos % per, i = rem / cols, j = rem % cols;
+        const double x = __ldg(X + sidx * xstride + i * xld + j);
+        double *y = Y + sidx * ystride + i * yld + j;
+        *y = first ? chain_first(c, x) : chain_step(*y, c, x);
     }
 }
 
@@ -699,6 +807,62 @@ cudaError_t launch_level_w(const double *child, int64_t rows, int64_t cols, int 
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_level_stream(const double *parent, int64_t parent_ld, int64_t parent_stride,
+                                int64_t parents, int64_t rows, int64_t cols, int gridR, int gridC, int R,
+                                const int *ptr, const int *code, const double *coef, double *out,
+                                cudaStream_t s, int *launches) {
+    const int NB = gridR * gridC;
+    if (NB > 64 || R > 128) return cudaErrorInvalidValue;
+    const size_t smem = size_t(NB) * 256 * 8;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(level_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             64 * 256 * 8);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t total = parents * rows * cols;
+    level_stream_kernel<<<(unsigned)((total + 255) / 256), 256, smem, s>>>(
+        parent, parent_ld, parent_stride, rows, cols, gridC, NB, R, parents, ptr, code, coef, out);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level_w_stream(const double *child, int64_t rows, int64_t cols, int R, int gridN, int MN,
+                                  double *parent, int64_t parent_ld, int64_t parent_stride, int64_t parents,
+                                  const int *w_ptr, const int *w_r, const double *w_coef, int accumulate,
+                                  cudaStream_t s, int *launches) {
+    if (R > 128 || MN > 128) return cudaErrorInvalidValue;
+    const size_t smem = size_t(R) * 128 * 8;
+    static bool configured[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !configured[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(level_w_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             128 * 128 * 8);
+        if (e != cudaSuccess) return e;
+        configured[dev] = true;
+    }
+    const int64_t total = parents * rows * cols;
+    level_w_stream_kernel<<<(unsigned)((total + 127) / 128), 128, smem, s>>>(
+        child, rows, cols, R, gridN, MN, parent, parent_ld, parent_stride, parents, w_ptr, w_r, w_coef,
+        accumulate);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_axpy(const double *X, int64_t xld, int64_t xstride, double *Y, int64_t yld,
+                              int64_t ystride, int64_t parents, int64_t rows, int64_t cols, double c,
+                              int first, cudaStream_t s, int *launches) {
+    const int64_t total = parents * rows * cols;
+    const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    block_axpy_kernel<<<blocks, 256, 0, s>>>(X, xld, xstride, Y, yld, ystride, parents, rows, cols, c, first);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 // Thin classical products (the peeling fringes of Section 3.5: at most

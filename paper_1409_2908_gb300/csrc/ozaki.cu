@@ -1,26 +1,32 @@
-// Emulated-FP64 leaf products on the tensor cores (precision variant
-// FMM_PREC_OZAKI_BF16).  For each leaf product S T (FP64):
+// Emulated-FP64 products on the tensor cores (precision variant
+// FMM_PREC_OZAKI_BF16).  For a product S T (FP64):
 //
-//   1. split   scale row i of S by 2^s_i and column j of T by 2^t_j so the
-//              entries truncate to integers of beta bits, and write their
-//              balanced residues modulo each of N pairwise coprime moduli
-//              p <= 256 as bfloat16 (|r| <= 128: exact), K-major;
+//   1. split   scale row i of S by 2^s_i and column j of T by 2^t_j and round
+//              the entries to integers of at most beta bits (ties away from
+//              zero), then write their balanced residues modulo each of N
+//              pairwise coprime moduli p <= 256 as bfloat16 (|r| <= 128:
+//              exact), K-major;
 //   2. gemm    Z_p = S'_p T'_p mod p on tcgen05 (kind::f16, FP32 accumulator in
 //              TMEM).  Products are < 2^14, so a k-chunk of 512 sums exactly in
-//              FP32; each chunk is drained into int32 registers through four
+//              FP32; each chunk is drained into int32 registers through
 //              rotating TMEM buffers while the next chunk is multiplied;
-//   3. crt     mixed-radix (Garner) digits of Z from its N residues, evaluated
-//              in FP64 by Horner's rule and scaled by 2^-(s_i + t_j).
+//   3. crt     Z from its N residues as a weighted sum of 16-bit limbs
+//              (X = sum_q r_q c_q mod P), brought to [-P/2, P/2), rounded once
+//              to FP64 from its integer bits and scaled by 2^-(s_i + t_j).
 //
-// Operand tiles reach shared memory by TMA (128-byte swizzle) through a
-// 4-stage mbarrier ring; one thread issues the MMAs, one thread the loads,
-// four warps drain TMEM.  Every mbarrier wait is bounded: on timeout the CTA
+// With integer base coefficients the recursion itself runs on the residues
+// (ozaki_fast below): the scaling and the first level share one pass, the
+// levels are modular combinations, and the top W level shares the CRT pass.
+// Operand tiles reach shared memory by TMA (128-byte swizzle) through an
+// mbarrier ring; one thread issues the MMAs, one thread the loads, four or
+// eight warps drain TMEM.  Every mbarrier wait is bounded: on timeout the CTA
 // records an error, stops issuing work and frees its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -36,6 +42,11 @@ const int kOzakiModuli[20] = {256, 255, 253, 251, 247, 241, 239, 233, 229, 227,
                               223, 217, 211, 199, 197, 193, 191, 181, 179, 173};
 
 __device__ int g_device_error = 0;   // set when a bounded wait gives up
+
+// Time limit of every bounded device wait in the tensor-core kernels.
+static std::atomic<unsigned long long> g_wait_ns{2000000000ull};
+unsigned long long wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
+void set_wait_limit_ns(unsigned long long ns) { g_wait_ns.store(ns, std::memory_order_relaxed); }
 
 namespace {
 
@@ -103,8 +114,10 @@ __device__ __forceinline__ int ilog2_abs(double x) {
 __device__ __forceinline__ unsigned abs_hi(double x) { return (unsigned)__double2hiint(x) & 0x7fffffffu; }
 constexpr unsigned OZ_NORMAL_HI = 0x00100000u;
 
-// trunc(x * 2^s) as an integer, by shifting the significand (no FP64 ops).
-__device__ __forceinline__ long long scaled_trunc(double x, int s) {
+// x * 2^s rounded to the nearest integer (ties away from zero), by shifting
+// the significand (no FP64 ops).  With s = beta - 1 - floor(log2 max|x|) the
+// result is at most 2^beta in magnitude.
+__device__ __forceinline__ long long scaled_round(double x, int s) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int be = int((b >> 52) & 0x7ff);
     const unsigned long long frac = b & ((1ull << 52) - 1);
@@ -114,9 +127,9 @@ __device__ __forceinline__ long long scaled_trunc(double x, int s) {
     const unsigned long long mant = be ? (frac | (1ull << 52)) : frac;
     const int sh = 52 - ((be ? be : 1) - 1023) - s;   // value = mant * 2^-sh
     long long v;
-    if (sh >= 64) v = 0;
-    else if (sh >= 0) v = (long long)(mant >> sh);
-    else v = (long long)(mant << (-sh));       // beta > 53 (short k): still < 2^beta <= 2^62
+    if (sh >= 54) v = 0;                       // mant < 2^53: value < 1/2
+    else if (sh >= 1) v = (long long)((mant + (1ull << (sh - 1))) >> sh);
+    else v = (long long)(mant << (-sh));       // an integer already (beta > 53 with short k)
     return (b >> 63) ? -v : v;
 }
 
@@ -147,7 +160,7 @@ __global__ void split_rows_kernel(const double *X, int64_t ldx, int64_t leaf_str
     const int s = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
     if (lane == 0) exps[leaf * rows + row] = s;
     for (int64_t j = lane; j < kpad; j += 32) {
-        const long long v = j < cols ? scaled_trunc(x[j], s) : 0;
+        const long long v = j < cols ? scaled_round(x[j], s) : 0;
         for (int q = 0; q < nmod; ++q)
             out[((leaf * nmod + q) * rows + row) * kpad + j] = __float2bfloat16_rn(residue_bf16(v, q));
     }
@@ -166,7 +179,7 @@ __global__ void split_cols_kernel(const double *Y, int64_t ldy, int64_t leaf_str
     for (int r = ty; r < 32; r += 8) {
         const int64_t i = i0 + r, j = j0 + tx;
         long long v = 0;
-        if (i < rows && j < cols) v = scaled_trunc(y[i * ldy + j], exps[leaf * cols + j]);
+        if (i < rows && j < cols) v = scaled_round(y[i * ldy + j], exps[leaf * cols + j]);
         tile[r][tx] = v;
     }
     __syncthreads();
@@ -350,7 +363,7 @@ __global__ void split_rows_i8(const double *X, int64_t ldx, int64_t rows, int64_
     const int s = (mx == 0.0) ? 0 : beta - 1 - ilog2_abs(mx);
     if (lane == 0) exps[row] = s;
     for (int64_t j = lane; j < cols; j += 32) {
-        const long long v = scaled_trunc(x[j], s);
+        const long long v = scaled_round(x[j], s);
         for (int q = 0; q < nmod; ++q)
             out[((int64_t)q * rows + row) * cols + j] = (int8_t)residue_bf16(v, q);
     }
@@ -366,7 +379,7 @@ __global__ void split_cols_t_i8(const double *Y, int64_t ldy, int64_t rows, int6
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int r = ty; r < 32; r += 8) {
         const int64_t i = i0 + r, j = j0 + tx;
-        tile[r][tx] = (i < rows && j < cols) ? scaled_trunc(Y[i * ldy + j], exps[j]) : 0;
+        tile[r][tx] = (i < rows && j < cols) ? scaled_round(Y[i * ldy + j], exps[j]) : 0;
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
@@ -631,7 +644,7 @@ __device__ __forceinline__ void stage_terms(int R, int gridC, const int *ptr, co
 }
 
 // S side: A (peeled core, ld lda) as a grid of M x K blocks of rows x cols;
-// A' = trunc(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
+// A' = round(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
 // consecutive columns of out_ld (columns >= cols are the zero padding of the
 // GEMM operand).  256 threads; dynamic shared memory NB x 4 x 256 int64.
 // Limb layouts of the combined integers: LC 0 = 3 x 14 bits, 1 = 4 x 14, 2 = 5 x 13.
@@ -663,13 +676,13 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
         const double *x = A + row * lda + (int64_t)(b % gridK) * cols + j0;
         if (j0 + 4 <= cols && ((uintptr_t)x & 15) == 0) {
             const double2 v0 = reinterpret_cast<const double2 *>(x)[0], v1 = reinterpret_cast<const double2 *>(x)[1];
-            sv[(b * 4 + 0) * 256 + threadIdx.x] = scaled_trunc(v0.x, s);
-            sv[(b * 4 + 1) * 256 + threadIdx.x] = scaled_trunc(v0.y, s);
-            sv[(b * 4 + 2) * 256 + threadIdx.x] = scaled_trunc(v1.x, s);
-            sv[(b * 4 + 3) * 256 + threadIdx.x] = scaled_trunc(v1.y, s);
+            sv[(b * 4 + 0) * 256 + threadIdx.x] = scaled_round(v0.x, s);
+            sv[(b * 4 + 1) * 256 + threadIdx.x] = scaled_round(v0.y, s);
+            sv[(b * 4 + 2) * 256 + threadIdx.x] = scaled_round(v1.x, s);
+            sv[(b * 4 + 3) * 256 + threadIdx.x] = scaled_round(v1.y, s);
         } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = (j0 + e < cols) ? scaled_trunc(x[e], s) : 0;
+            for (int e = 0; e < 4; ++e) sv[(b * 4 + e) * 256 + threadIdx.x] = (j0 + e < cols) ? scaled_round(x[e], s) : 0;
         }
     }
     constexpr int ES = FINAL ? 2 : 1;   // bytes per output entry
@@ -681,7 +694,7 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
 }
 
 // T side, transposed: B (peeled core, ld ldb) as a grid of K x N blocks of
-// krows x ncols; B' = trunc(B_ij 2^eb_j).  Output rows are columns of B
+// krows x ncols; B' = round(B_ij 2^eb_j).  Output rows are columns of B
 // (T^T, K-major for the GEMM).  CTA: 32 k x 32 n positions of the child
 // blocks through shared memory (dynamic: NB x 32 x 33 int64, then reused as
 // [NB][4][256]); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
@@ -705,7 +718,7 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
         for (int r = ty; r < 32; r += 8) {
             const int64_t k = k0 + r;
             sv[(b * 32 + r) * 33 + tx] =
-                (k < krows && n < ncols) ? scaled_trunc(B[(bk * krows + k) * ldb + bn * ncols + n], s) : 0;
+                (k < krows && n < ncols) ? scaled_round(B[(bk * krows + k) * ldb + bn * ncols + n], s) : 0;
         }
     }
     __syncthreads();
@@ -1182,11 +1195,11 @@ int64_t z_pitch(int64_t n) { return (n + 15) / 16 * 16; }
 // planes of m rows (the caller points Z at the band's own region).
 cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64_t m, int64_t n,
                                 int64_t kpad, int64_t planes, int nmod, int *err, cudaStream_t s,
-                                int *launches, int64_t r0 = 0, int64_t plane_m = -1) {
+                                int *launches, int64_t r0 = 0, int64_t plane_m = -1, bool narrow = false) {
     cudaError_t e;
     if ((e = configure_residue_gemm()) != cudaSuccess) return e;
     if (plane_m < 0) plane_m = m;
-    const bool wide = n >= 256;
+    const bool wide = n >= 256 && !narrow;
     const int bn = wide ? 256 : 128;
     CUtensorMap ta, tb;
     // kpad is a multiple of 64, so the band's first row starts 16-byte aligned
@@ -1199,12 +1212,13 @@ cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
     cudaEvent_t t0 = timing_mark(s);
     const int64_t ldz = z_pitch(n);
+    const unsigned long long wns = wait_limit_ns();
     if (wide)
         residue_gemm<256><<<ctas, oz_threads<256>(), oz_smem<256>(), s>>>(
-            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err, wns, 0);
     else
         residue_gemm<128><<<ctas, oz_threads<128>(), oz_smem<128>(), s>>>(
-            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err);
+            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err, wns, 0);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
@@ -1222,6 +1236,31 @@ cudaError_t read_device_error(int *flag, bool clear) {
         e = cudaMemcpyToSymbol(g_device_error, &zero, sizeof(int));
     }
     return e;
+}
+
+// The timeout path of the residue GEMM: one CTA over a 128 x 256 tile whose
+// load and MMA threads issue nothing (dry), so the drain warps' first wait
+// runs out after limit_ns with no copy or MMA outstanding; the CTA then sets
+// the error flag and exits.  Small private buffers back the tensor maps.
+cudaError_t residue_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = configure_residue_gemm()) != cudaSuccess) return e;
+    int *err = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&err, g_device_error)) != cudaSuccess) return e;
+    void *buf = nullptr;
+    const size_t a_bytes = 128 * 64 * 2, b_bytes = 256 * 64 * 2, z_bytes = 128 * 256;
+    if ((e = cudaMalloc(&buf, a_bytes + b_bytes + z_bytes)) != cudaSuccess) return e;
+    char *c = (char *)buf;
+    CUtensorMap ta, tb;
+    if ((e = make_map3d(&ta, c, 64, 128, 1, OZ_BM, 128)) == cudaSuccess &&
+        (e = make_map3d(&tb, c + a_bytes, 64, 256, 1, 256, 256)) == cudaSuccess) {
+        residue_gemm<256><<<1, oz_threads<256>(), oz_smem<256>(), s>>>(
+            ta, tb, (int8_t *)(c + a_bytes + b_bytes), 128, 256, 256, 1, 1, 1, 1, 1, err, limit_ns, 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    const cudaError_t f = cudaFree(buf);
+    return e != cudaSuccess ? e : f;
 }
 
 // Largest beta <= 62 with k 2^(2 beta + 1) < P (P = product of the moduli,
@@ -1468,8 +1507,9 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     int lc = 0;
     {
         const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
-        int bits = beta;
-        while ((1 << (bits - beta)) < cmax) ++bits;
+        // |A'| <= 2^beta (rounded), so |S'| <= cmax 2^beta < 2^(beta + floor(log2 cmax) + 1)
+        int bits = beta + 1;
+        while ((2 << (bits - beta - 1)) <= cmax) ++bits;
         lc = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
     }
 #define FMM_SPLIT(WHICH, F, LC)                                                                                     \
@@ -1617,7 +1657,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
             const int64_t R0 = mL * g / gb, NR = mL * (g + 1) / gb - R0;
             int8_t *Zb = Z + planes * R0 * cld;
             if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Zb, NR, nL, kpadL, planes, nmod, err,
-                                         s, launches, R0, mL)) != cudaSuccess)
+                                         s, launches, R0, mL, rp.tile == FMM_TILE_128x128)) != cudaSuccess)
                 return e;
             const int ns = (int)std::max<int64_t>(1, std::min<int64_t>(sub, NR));
             for (int t = 0; t < ns; ++t) {
@@ -1629,7 +1669,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     }
 
     if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, planes, nmod,
-                                 err, s, launches)) != cudaSuccess)
+                                 err, s, launches, 0, -1, rp.tile == FMM_TILE_128x128)) != cudaSuccess)
         return e;
     // W levels L..2 on residues, down to the level-1 products
     int64_t cm = mL, cn = nL, cld = z_pitch(nL);
@@ -1670,7 +1710,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
 cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                            int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves,
                            int64_t m, int64_t k, int64_t n, int nmod, void *ws,
-                           cudaStream_t s, int *launches) {
+                           cudaStream_t s, int *launches, int tile) {
     int *err = nullptr;
     cudaError_t e0 = cudaGetSymbolAddress((void **)&err, g_device_error);
     if (e0 != cudaSuccess) return e0;
@@ -1708,8 +1748,8 @@ cudaError_t ozaki_products(const double *S, int64_t lds, int64_t ss, const doubl
         ++*launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = launch_residue_gemm(ra, rb, Z, m, n, kpad, leaves * nmod, nmod, err, s, launches)) !=
-        cudaSuccess)
+    if ((e = launch_residue_gemm(ra, rb, Z, m, n, kpad, leaves * nmod, nmod, err, s, launches, 0, -1,
+                                 tile == FMM_TILE_128x128)) != cudaSuccess)
         return e;
     {
         const int64_t total = leaves * m * n;

@@ -10,7 +10,12 @@
 // Persistent: CTA c handles tiles c, c + gridDim.x, ...; the load, MMA and
 // drain roles walk the same tile sequence, so stage and TMEM-buffer phases
 // continue across tiles and the tensor core never waits for a tile's final
-// reduction (four TMEM buffers of slack).
+// reduction.  Every wait gives up after wait_ns nanoseconds (err set); before
+// the CTA exits, the load thread waits for the copies it issued to land and
+// the MMA thread for its MMAs to complete, so nothing asynchronous of the CTA
+// outlives it (unless those waits run out too).  dry != 0 (tests of the
+// timeout path only): the load and MMA threads issue nothing, so the drain
+// warps' first wait runs out with no copy or MMA outstanding.
 // Tile t of the persistent sequence -> (plane z, tile row tm, tile column tn).
 // Within a plane, tiles go in groups of OZ_GROUP tile rows, column by column,
 // so the CTAs of one wave share a few A row panels and B column panels in L2
@@ -47,7 +52,7 @@ template <int BN>
 __global__ void __launch_bounds__(oz_threads<BN>(), 1)
 residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
              int8_t *Z, int64_t m, int64_t n, int64_t ldz, int kblocks, int nmod, int tiles_m, int tiles_n,
-             int64_t tiles_total, int *err) {
+             int64_t tiles_total, int *err, unsigned long long wait_ns, int dry) {
     constexpr int OZ_TBUF = OzCfg<BN>::TBUF, OZ_STAGES = OzCfg<BN>::STAGES;
     constexpr int DW = OzCfg<BN>::DRAIN_WARPS;
     constexpr int OZ_BN = BN, OZ_B_BYTES = BN * OZ_BK * 2, OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
@@ -57,13 +62,15 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint64_t *empty = full + OZ_STAGES;
     uint64_t *tfull = empty + OZ_STAGES;
     uint64_t *tempty = tfull + OZ_TBUF;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + OZ_TBUF);
+    uint64_t *mdone = tempty + OZ_TBUF;   // the MMA thread's last commit
+    uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int nchunks = (kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int b = 0; b < OZ_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], DW * 32); }
+        mbar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -78,7 +85,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     const int64_t per_plane = (int64_t)tiles_m * tiles_n;
 
     if (warp == DW) {
-        if (lane == 0) {
+        if (lane == 0 && !dry) {
             int64_t g = 0;   // global k-block counter: stage and phase
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
@@ -86,7 +93,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 tile_coords(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = int(g % OZ_STAGES);
-                    if (g >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((g / OZ_STAGES) - 1) & 1))) {
+                    if (g >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((g / OZ_STAGES) - 1) & 1), wait_ns)) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
@@ -97,9 +104,14 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     tma_load_3d(sb, &tmB, kb * OZ_BK, tn * OZ_BN, z, &full[s]);
                 }
             }
+            // no bulk copy of this CTA may still be in flight when it exits:
+            // wait for the last (at most OZ_STAGES) k-blocks issued to land
+            // (normally consumed long ago; after a timeout elsewhere, bounded)
+            for (int64_t j = g > OZ_STAGES ? g - OZ_STAGES : 0; j < g; ++j)
+                if (!mbar_wait(&full[j % OZ_STAGES], uint32_t((j / OZ_STAGES) & 1), wait_ns)) atomicExch(err, 1);
         }
     } else if (warp == DW + 1) {
-        if (lane == 0) {
+        if (lane == 0 && !dry) {
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                    ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
             bool ok = true;
@@ -108,7 +120,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 int kb = 0;
                 for (int c = 0; c < nchunks && ok; ++c, ++cg) {
                     const int b = int(cg % OZ_TBUF);
-                    if (cg >= OZ_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / OZ_TBUF) - 1) & 1))) {
+                    if (cg >= OZ_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / OZ_TBUF) - 1) & 1), wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -117,7 +129,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     const int kend = min(kblocks, (c + 1) * OZ_CHUNK_KB);
                     for (int first = 1; kb < kend; ++kb, ++g, first = 0) {
                         const int s = int(g % OZ_STAGES);
-                        if (!mbar_wait(&full[s], uint32_t((g / OZ_STAGES) & 1))) { ok = false; break; }
+                        if (!mbar_wait(&full[s], uint32_t((g / OZ_STAGES) & 1), wait_ns)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t a0 = su32(smem + s * OZ_STAGE_BYTES), b0 = a0 + OZ_A_BYTES;
 #pragma unroll
@@ -129,6 +141,9 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     mma_commit(&tfull[b]);
                 }
             }
+            // every MMA issued here completes before TMEM is freed
+            mma_commit(mdone);
+            if (!mbar_wait(mdone, 0u, wait_ns)) ok = false;
             if (!ok) atomicExch(err, 1);
         }
     } else {
@@ -147,7 +162,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             for (int j = 0; j < 128; ++j) acc[j] = 0;
             for (int c = 0; c < nchunks; ++c, ++cg) {
                 const int b = int(cg % OZ_TBUF);
-                if (!mbar_wait(&tfull[b], uint32_t((cg / OZ_TBUF) & 1))) { ok = false; break; }
+                if (!mbar_wait(&tfull[b], uint32_t((cg / OZ_TBUF) & 1), wait_ns)) { ok = false; break; }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * OZ_BN + ch * 128);
 #pragma unroll

@@ -1,5 +1,5 @@
 // Device helpers shared by the tcgen05 kernels (ozaki.cu, tf32.cu): mbarrier
-// waits with an iteration limit, 3-D TMA loads, shared-memory matrix
+// waits with a time limit, 3-D TMA loads, shared-memory matrix
 // descriptors for K-major 128-byte-swizzled tiles, and the MMA / commit
 // wrappers.  Inline PTX for sm_103a.
 #pragma once
@@ -12,8 +12,6 @@
 namespace fmm {
 namespace tc {
 
-constexpr long long WAIT_LIMIT = 1ll << 26;
-
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t cnt) {
@@ -25,13 +23,30 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity) {
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Wait for the phase of `b` with parity `parity` to complete, for at most
+// limit_ns nanoseconds of the global timer (checked every 8 polls; each poll
+// may itself suspend the thread for a short, hardware-defined time; 2^34
+// polls end the wait too, should the timer not advance).  Returns false when
+// the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, unsigned long long limit_ns) {
     const uint32_t a = su32(b);
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
-        if (ok) return true;
+    if (mbar_try(a, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long i = 1; i < (1ll << 34); ++i) {
+        if (mbar_try(a, parity)) return true;
+        if ((i & 7) == 0 && global_ns() - t0 > limit_ns) return false;
     }
     return false;
 }

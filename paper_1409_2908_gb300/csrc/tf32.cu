@@ -74,7 +74,8 @@ template <int BN, bool CH>
 __global__ void __launch_bounds__(tf_threads<BN, CH>(), 1)
 tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           double *Out, int64_t m, int64_t n, int kblocks, int chunk_kb, int tiles_m, int tiles_n,
-          int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err) {
+          int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err,
+          unsigned long long wait_ns, int dry) {
     constexpr int DW = tf_dw<BN, CH>(), STAGES = TfCfg<BN>::STAGES;
     constexpr int CW = 4 * BN / DW;   // accumulator columns per drain warp
     constexpr int TB_B = BN * TB_K * 4, STAGE = TB_A + TB_B;
@@ -84,7 +85,8 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     uint64_t *empty = full + STAGES;
     uint64_t *tfull = empty + STAGES;
     uint64_t *tempty = tfull + TB_TBUF;
-    uint32_t *tmem_slot = (uint32_t *)(tempty + TB_TBUF);
+    uint64_t *mdone = tempty + TB_TBUF;   // the MMA thread's last commit
+    uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int64_t per_plane = (int64_t)tiles_m * tiles_n;
     // k in chunks of chunk_kb blocks: each chunk is summed in TMEM and added
@@ -94,6 +96,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int b = 0; b < TB_TBUF; ++b) { mbar_init(&tfull[b], 1); mbar_init(&tempty[b], DW * 32); }
+        mbar_init(mdone, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -107,7 +110,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const uint32_t tmem = *tmem_slot;
 
     if (warp == DW) {
-        if (lane == 0) {
+        if (lane == 0 && !dry) {
             int64_t g = 0;
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
@@ -115,7 +118,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 tf_tile(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
                 for (int kb = 0; kb < kblocks; ++kb, ++g) {
                     const int s = int(g % STAGES);
-                    if (g >= STAGES && !mbar_wait(&empty[s], uint32_t(((g / STAGES) - 1) & 1))) {
+                    if (g >= STAGES && !mbar_wait(&empty[s], uint32_t(((g / STAGES) - 1) & 1), wait_ns)) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
@@ -126,9 +129,12 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     tma_load_3d(sb, &tmB, kb * TB_K, tn * BN, z, &full[s]);
                 }
             }
+            // no bulk copy of this CTA may still be in flight when it exits
+            for (int64_t j = g > STAGES ? g - STAGES : 0; j < g; ++j)
+                if (!mbar_wait(&full[j % STAGES], uint32_t((j / STAGES) & 1), wait_ns)) atomicExch(err, 1);
         }
     } else if (warp == DW + 1) {
-        if (lane == 0) {
+        if (lane == 0 && !dry) {
             // FP32 accumulator, TF32 A and B, both K-major
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                                    ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TB_M >> 4) << 24);
@@ -138,7 +144,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 int kb = 0;
                 for (int c = 0; c < nchunks && ok; ++c, ++cg) {
                     const int b = int(cg % TB_TBUF);
-                    if (cg >= TB_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / TB_TBUF) - 1) & 1))) {
+                    if (cg >= TB_TBUF && !mbar_wait(&tempty[b], uint32_t(((cg / TB_TBUF) - 1) & 1), wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -147,7 +153,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     const int kend = min(kblocks, (c + 1) * chunk_kb);
                     for (int first = 1; kb < kend; ++kb, ++g, first = 0) {
                         const int s = int(g % STAGES);
-                        if (!mbar_wait(&full[s], uint32_t((g / STAGES) & 1))) { ok = false; break; }
+                        if (!mbar_wait(&full[s], uint32_t((g / STAGES) & 1), wait_ns)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t a0 = su32(smem + s * STAGE), b0 = a0 + TB_A;
 #pragma unroll
@@ -159,6 +165,9 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     mma_commit(&tfull[b]);
                 }
             }
+            // every MMA issued here completes before TMEM is freed
+            mma_commit(mdone);
+            if (!mbar_wait(mdone, 0u, wait_ns)) ok = false;
             if (!ok) atomicExch(err, 1);
         }
     } else {
@@ -204,7 +213,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             if constexpr (!CH) {
                 // the whole k summed in TMEM: one drain per tile
                 const int b = int(cg % TB_TBUF);
-                if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1))) { ok = false; break; }
+                if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1), wait_ns)) { ok = false; break; }
                 ++cg;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * CW);
@@ -230,7 +239,7 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 for (int j = 0; j < CW; ++j) acc[j] = 0.0f;
                 for (int c = 0; c < nchunks; ++c, ++cg) {
                     const int b = int(cg % TB_TBUF);
-                    if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1))) { ok = false; break; }
+                    if (!mbar_wait(&tfull[b], uint32_t((cg / TB_TBUF) & 1), wait_ns)) { ok = false; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t base = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(b * BN + ch * CW);
 #pragma unroll
@@ -413,7 +422,7 @@ cudaError_t read_tf32_error(int *flag, bool clear) {
 cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
                           int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
-                          int split) {
+                          int split, int tile) {
     if (split != 1 && split != 3) return cudaErrorInvalidValue;
     cudaError_t e = tf32_prepare();
     if (e != cudaSuccess) return e;
@@ -441,7 +450,7 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
     // the chunked sums (FP32-accurate products) keep 64 running sums per drain
     // thread: 128-wide tiles with 8 drain warps fit them in registers
     const bool chunked = split == 3;
-    const bool wide = n >= 256 && !chunked;
+    const bool wide = n >= 256 && !chunked && tile != FMM_TILE_128x128;
     const int bn = wide ? 256 : 128;
     if ((e = map3d_f32(&ta, fa, kk, m, leaves, TB_M)) != cudaSuccess) return e;
     if ((e = map3d_f32(&tb, fb, kk, n, leaves, bn)) != cudaSuccess) return e;
@@ -455,7 +464,7 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
 #define FMM_TF32_GEMM(BN_, CH_)                                                                                \
     tf32_gemm<BN_, CH_><<<ctas, tf_threads<BN_, CH_>(), tf_smem<BN_>(), s>>>(ta, tb, Out, m, n, kblocks, chunk_kb, \
                                                                           int(tm), int(tn), tiles, ldo, os,    \
-                                                                          accumulate, err)
+                                                                          accumulate, err, wait_limit_ns(), 0)
     if (chunked) FMM_TF32_GEMM(128, true);
     else if (wide) FMM_TF32_GEMM(256, false);
     else FMM_TF32_GEMM(128, false);
@@ -464,6 +473,29 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
     return cudaSuccess;
+}
+
+// The timeout path of the TF32 GEMM (see residue_gemm_timeout_probe): one
+// dry CTA, the drain warps' first wait runs out with nothing outstanding.
+cudaError_t tf32_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s) {
+    cudaError_t e = tf32_prepare();
+    if (e != cudaSuccess) return e;
+    int *err = nullptr;
+    if ((e = cudaGetSymbolAddress((void **)&err, g_tf32_error)) != cudaSuccess) return e;
+    void *buf = nullptr;
+    const size_t a_bytes = 128 * 32 * 4, b_bytes = 256 * 32 * 4, o_bytes = 128 * 256 * 8;
+    if ((e = cudaMalloc(&buf, a_bytes + b_bytes + o_bytes)) != cudaSuccess) return e;
+    char *c = (char *)buf;
+    CUtensorMap ta, tb;
+    if ((e = map3d_f32(&ta, (float *)c, 32, 128, 1, TB_M)) == cudaSuccess &&
+        (e = map3d_f32(&tb, (float *)(c + a_bytes), 32, 256, 1, 256)) == cudaSuccess) {
+        tf32_gemm<256, false><<<1, tf_threads<256, false>(), tf_smem<256>(), s>>>(
+            ta, tb, (double *)(c + a_bytes + b_bytes), 128, 256, 1, 1, 1, 1, 1, 256, 0, 0, err, limit_ns, 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    const cudaError_t f = cudaFree(buf);
+    return e != cudaSuccess ? e : f;
 }
 
 }  // namespace fmm

@@ -202,3 +202,12 @@ def test_emulated_and_tf32_workspace_layouts():
         2 * al(1000 * kpad * 4)
     assert fmm.Plan("strassen_222_7", levels=0, precision="fp32").workspace_size(1000, 1000, 1000) == \
         2 * al(1000 * 3 * kpad * 4)
+
+
+def test_wait_limit_argument_errors():
+    # checked on the host, no GPU involved
+    L = _lib.lib()
+    assert L.fmm_set_wait_limit(0) == fmm.FMM_ERR_ARG
+    assert L.fmm_set_wait_limit(2_000_000_000) == fmm.FMM_OK
+    assert L.fmm_selftest_wait_timeout(2, 1000, None) == fmm.FMM_ERR_ARG
+    assert L.fmm_selftest_wait_timeout(0, 0, None) == fmm.FMM_ERR_ARG

@@ -15,9 +15,13 @@ def test_candidates_cover_algorithms_levels_precisions():
     cands = t.candidates(8192, 8192, 8192)
     assert any(c.precision == "ozaki_bf16" and c.levels >= 1 for c in cands)
     assert any(c.precision == "ozaki_bf16" and c.levels == 0 for c in cands)
-    # with the emulated variant available, FP64 plans only compete on tiny products
-    assert all(c.precision == "ozaki_bf16" for c in cands)
+    # with the emulated variant available it leads; the native FP64 plans stay
+    # in the ranking (an FP64-only tuner reaches them)
+    assert cands[0].precision == "ozaki_bf16"
+    assert any(c.precision == "fp64" and c.levels >= 1 for c in cands)
     assert any(c.precision == "fp64" for c in t.candidates(40, 3000, 40))
+    best = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False).choose(8192, 8192, 8192)
+    assert best.precision == "fp64" and best.levels >= 1
 
 
 def test_recursion_stops_when_leaves_get_small():
@@ -68,3 +72,39 @@ def test_choice_plans_carry_moduli_only_for_emulated_fp64():
     assert c.plan().precision == "tf32"
     c = autotune.Choice("strassen_222_7", 0, 0, "fp32")
     assert c.plan().precision == "fp32"
+
+
+def test_permuted_base_cases_are_exact():
+    # every ordering of every shipped base case (Section 2.3's permutations)
+    # passes the oracle's exact Brent check and the library's plan check
+    import numpy as np
+    from fractions import Fraction
+    import paper_1409_2908_gb300 as fmm
+    from oracle import tensor
+    for name in autotune.algorithms():
+        M0, K0, N0 = autotune.algorithms()[name][:3]
+        shapes = set()
+        for perm in autotune.PERMS:
+            M, K, N, U, V, W = autotune.permuted_factors(name, perm)
+            shapes.add((M, K, N))
+            F = [[[Fraction(float(x)) for x in row] for row in X] for X in (U, V, W)]
+            assert tensor.brent_violations(M, K, N, *F) == [], (name, perm)
+            fmm.Plan(levels=1, factors=(M, K, N, U, V, W))
+        assert shapes == {(M0, K0, N0), (K0, N0, M0), (N0, M0, K0), (N0, K0, M0), (K0, M0, N0), (M0, N0, K0)}
+
+
+def test_permutations_reach_shape_matched_cases():
+    # tall-skinny m >> k = n: orderings of <4,2,3> with the 4 on m are candidates
+    t = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False)
+    cands = t.candidates(16384, 2048, 2048)
+    dims = {autotune.cases()[(c.algorithm, c.perm)][:3] for c in cands if c.levels >= 1}
+    assert (4, 3, 2) in dims and (4, 2, 3) in dims
+    assert any(c.perm for c in cands)
+
+
+def test_fp64_tile_follows_leaf_size():
+    t = autotune.Autotuner(tol=1e-11, precisions=("fp64",), measure=False, permutations=False)
+    big = [c for c in t.candidates(8192, 8192, 8192) if c.levels == 1 and c.algorithm == "strassen_222_7"][0]
+    assert big.tile == "128x128"
+    small = [c for c in t.candidates(192, 4096, 192) if c.levels == 1 and c.algorithm == "strassen_222_7"][0]
+    assert small.tile in ("96x96", "64x64", "32x32")

@@ -136,3 +136,23 @@ def test_emulated_zero_and_subnormal_rows_and_columns(name, levels):
     assert np.array_equal(C, ozaki.emulated_gemm(A, B, 13))
     assert np.all(C[3] == 0) and np.all(C[:, 4] == 0)
     assert np.all(np.isfinite(C))
+
+
+@pytest.mark.parametrize("name,levels", [("strassen_222_7", 0), ("strassen_222_7", 1), ("fmm_424_26", 1)])
+def test_emulated_rounding_ties(name, levels):
+    # entries whose scaled values are exact half-integers (ties): the scaling
+    # rounds them away from zero, as the oracle's emulation does
+    rng = np.random.default_rng(51)
+    M, K, N = {"strassen_222_7": (2, 2, 2), "fmm_424_26": (4, 2, 4)}[name]
+    m, k, n = (M ** levels) * 64, (K ** levels) * 128, (N ** levels) * 48
+    nmod = 12
+    beta = ozaki.beta_bits(nmod, k)
+    ulp = 2.0 ** -(beta - 1)        # rows and columns with maximum in [1, 2)
+    A = (rng.integers(-5000, 5000, (m, k)) + 0.5) * ulp
+    B = (rng.integers(-5000, 5000, (k, n)) + 0.5) * ulp
+    A[:, 0] = 1.5
+    B[0, :] = -1.25
+    A[1::3] += rng.uniform(-1, 1, (len(range(1, m, 3)), k)) * 1e-9
+    assert np.all(np.abs(A).max(axis=1) < 2) and np.all(np.abs(B).max(axis=0) < 2)
+    p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=nmod)
+    assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, nmod))

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle import norms
+from oracle import norms, ozaki
 import paper_1409_2908_gb300 as fmm
 from paper_1409_2908_gb300 import synth
 from tests.gpu_util import classical_bound, to_dev
@@ -312,6 +312,10 @@ def test_full_size_workloads_sampled(name, levels, precision, moduli, shape):
     e64, eld = oracle.gemm_entries(A, B, rows, cols)
     got = C[ri, ci].cpu().numpy()
     assert np.linalg.norm(got - eld) / np.linalg.norm(eld) <= TOL_F
+    if precision == "ozaki_bf16":
+        # the same scaled integers, their exact product and one rounding as
+        # the oracle's emulation, entry by entry
+        assert np.array_equal(got, ozaki.emulated_entries(A, B, rows, cols, moduli))
     Ai, Bi = np.rint(4 * A), np.rint(4 * B)
     Ad.copy_(torch.from_numpy(Ai))
     Bd.copy_(torch.from_numpy(Bi))
@@ -319,3 +323,95 @@ def test_full_size_workloads_sampled(name, levels, precision, moduli, shape):
     torch.cuda.synchronize()
     ei64, _ = oracle.gemm_entries(Ai, Bi, rows, cols)
     assert np.array_equal(C[ri, ci].cpu().numpy(), ei64)
+
+
+def fast_abs_entries(name, A, B, rows, cols):
+    """For a one-level plan: sum_r |W_qr| (|S_r| |T_r|)_ij at the sampled
+    entries, |S_r| = sum_i |U_ir| |A_i| and |T_r| = sum_j |V_jr| |B_j| (block
+    (i, j) of C in block q).  Leaf products with relative error e per term
+    give C within e times this, entry by entry (the FP64 additions add
+    rounding errors far below the bounds used)."""
+    M, K, N, U, V, W = fmm.algorithm_factors(name)
+    m, k = A.shape
+    n = B.shape[1]
+    mb, kb, nb = m // M, k // K, n // N
+    out = np.zeros(len(rows))
+    for t, (i, j) in enumerate(zip(rows, cols)):
+        a, ii = divmod(int(i), mb)
+        c, jj = divmod(int(j), nb)
+        q = a * N + c
+        for r in np.nonzero(W[q])[0]:
+            srow = np.zeros(kb)
+            for blk in np.nonzero(U[:, r])[0]:
+                ba, bb = divmod(int(blk), K)
+                srow += abs(U[blk, r]) * np.abs(A[ba * mb + ii, bb * kb:(bb + 1) * kb])
+            tcol = np.zeros(kb)
+            for blk in np.nonzero(V[:, r])[0]:
+                bb, bc = divmod(int(blk), N)
+                tcol += abs(V[blk, r]) * np.abs(B[bb * kb:(bb + 1) * kb, bc * nb + jj])
+            out[t] += abs(W[q, r]) * float(srow @ tcol)
+    return out
+
+
+FULL_SIZE_PRECISION = [
+    # (algorithm, levels, precision, moduli, (m, k, n), data): the precision
+    # variants at the sizes the paper's largest square runs and the rank-k
+    # workload use
+    ("strassen_222_7", 1, "ozaki_bf16", 14, (16384, 16384, 16384), "uniform"),
+    ("strassen_222_7", 1, "ozaki_bf16", 13, (16384, 16384, 16384), "loguniform"),
+    ("fmm_424_26", 1, "ozaki_bf16", 14, (16384, 2048, 16384), "uniform"),
+    ("strassen_222_7", 0, "tf32", None, (16384, 16384, 16384), "uniform"),
+    ("strassen_222_7", 1, "tf32", None, (16384, 16384, 16384), "uniform"),
+    ("strassen_222_7", 1, "fp32", None, (16384, 16384, 16384), "uniform"),
+]
+
+
+@pytest.mark.parametrize("name,levels,precision,moduli,shape,data", FULL_SIZE_PRECISION)
+def test_full_size_precision_variants_sampled(name, levels, precision, moduli, shape, data):
+    # emulated FP64: bit-identical to the oracle's emulation at every sampled
+    # entry.  TF32 / FP32-accurate leaves: every sampled entry within its
+    # rounding bound of the oracle's long-double value (k = 16384, the regime
+    # where whole-k FP32 sums in the tensor core lose accuracy), and e_F within
+    # the variant's stated error.
+    import torch
+    m, k, n = shape
+    p = fmm.Plan(name, levels=levels, precision=precision, moduli=moduli)
+    A, B = synth.operands(m, k, n, 1411, kind=data)
+    Ad, Bd = to_dev(A), to_dev(B)
+    C = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    wsz = p.workspace_size(m, k, n)
+    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda") if wsz else None
+    fmm.gemm(p, Ad, Bd, C=C, workspace=ws)
+    torch.cuda.synchronize()
+    fmm.check_device_error()
+    del ws
+    rows, cols = synth.sample_indices(m, n, 256, 79)
+    got = C[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
+    del Ad, Bd, C
+    _, eld = oracle.gemm_entries(A, B, rows, cols)
+    if precision == "ozaki_bf16":
+        assert np.array_equal(got, ozaki.emulated_entries(A, B, rows, cols, moduli))
+        # e_F: about 2^-beta on uniform data (beta = 47 for 14 moduli at
+        # k = 16384); log-uniform rows lose the digits of their small entries
+        # relative to the row maximum, so there the target is the plan's 1e-11
+        assert np.linalg.norm(got - eld) / np.linalg.norm(eld) <= (2e-14 if data == "uniform" else TOL_F)
+        return
+    kL = k // 2 ** levels
+    if levels == 0:
+        _, absab = oracle.gemm_entries(np.abs(A), np.abs(B), rows, cols)
+    else:
+        absab = fast_abs_entries(name, A, B, rows, cols)
+    if precision == "tf32":
+        # operands rounded to FP32 then TF32 (2^-11 + 2^-24 each), FP32 sums
+        # over the whole k in the tensor core (one unit in the last place per
+        # addition at worst)
+        factor = 2.0 ** -10 + 2.0 ** -20 + kL * 2.0 ** -23
+        e_max = 1e-3
+    else:
+        # TF32 pairs keep 22 bits of each FP32 operand, lo x lo dropped; sums of
+        # 512 k (x3 terms) in the tensor core, chunk sums added with round to
+        # nearest on the CUDA cores
+        factor = 4 * 2.0 ** -22 + 1.01 * 1536 * 2.0 ** -23 + (kL / 512 + 4) * 2.0 ** -24
+        e_max = 1e-5
+    assert np.all(np.abs(got - eld) <= factor * absab + 2.0 ** -40 * absab)
+    assert np.linalg.norm(got - eld) / np.linalg.norm(eld) <= e_max
