@@ -70,17 +70,13 @@ __device__ __forceinline__ bool is_minus_one(double c) {
 }
 __device__ __forceinline__ bool is_zero(double c) { return (__double_as_longlong(c) << 1) == 0; }
 
-// Add coef * x into v; coefficients +-1 need no multiply.
-__device__ __forceinline__ double chain_step(double v, double c, double x) {
-    if (is_one(c)) return v + x;
-    if (is_minus_one(c)) return v - x;
-    return fma(c, x, v);
-}
+// Add coef * x into v with one FP64 operation whatever the coefficient: for
+// c = +-1, fma(c, x, v) rounds v +- x once, the same bits as the addition,
+// and avoids a data-dependent choice between several FP64 results.
+__device__ __forceinline__ double chain_step(double v, double c, double x) { return fma(c, x, v); }
 
-__device__ __forceinline__ double chain_first(double c, double x) {
-    if (is_one(c)) return x;
-    return c * x;
-}
+// The first term of a chain: c x (exact for c = +-1, and for powers of two).
+__device__ __forceinline__ double chain_first(double c, double x) { return c * x; }
 
 template <int TM, int TN>
 __global__ void __launch_bounds__(THREADS, 1) leaf_gemm(const KParams p) {
