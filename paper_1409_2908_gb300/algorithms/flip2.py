@@ -3,7 +3,9 @@ followed by a Hensel lift of the found scheme to exact small rationals.
 
 Section 2.3 frames the search as finding a rank-R decomposition of the matmul
 tensor and recovering discrete coefficients.  Here the discrete structure
-comes first: a random walk over schemes modulo 2 (a flip rewrites two terms
+comes first, by the flip-graph method of Kauers and Moosbauer ("Flip graphs
+for matrix multiplication", 2022; plus transitions from their follow-up work),
+implemented here from its published description: a random walk over schemes modulo 2 (a flip rewrites two terms
 sharing a factor, x(y1)(z1) + x(y2)(z2) = x(y1+y2)(z1) + x(y2)(z1+z2) mod 2;
 a reduction merges two terms sharing two factors; terms with a zero factor
 vanish) from the classical scheme until the rank is R.  The scheme is then

@@ -1,5 +1,8 @@
 /* Fast random walk over matmul schemes modulo 2 (the discrete half of the
- * offline search for base cases <M,K,N;R>, Section 2.3).
+ * offline search for base cases <M,K,N;R>, Section 2.3): the flip-graph
+ * method of Kauers and Moosbauer ("Flip graphs for matrix multiplication",
+ * 2022), with the plus transitions of their later work, written here from
+ * the published description.
  *
  * A scheme is a list of rank-one terms u (x) v (x) w whose sum is the matmul
  * tensor of <M,K,N> over GF(2); each factor is a bitmask over the MK, KN or
