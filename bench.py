@@ -59,14 +59,14 @@ WORKLOADS = {
 # FP64 ceiling of the DFMA pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# DRAM traffic of the residue GEMM from one ncu capture (summary in
-# profiles/residue_gemm_strassen_L1_square4096_x12.md): dram bytes read +
+# DRAM traffic of the residue GEMM from one ncu capture (Strassen one level,
+# 14 moduli, 4096^3; its summary is kept under profiles/): dram bytes read +
 # written over the algorithmic bytes (operand planes read once, int8 product
 # planes written once) of that launch.  Valid only for the kernel source it
 # was taken on (sha256 of csrc/residue_gemm.cuh); otherwise traffic is null.
-RGEMM_TRAFFIC = {"sha256": "443b452527908945b6caead93af9da3694ca6fec12395097f835037166797b89",
-                 "dram_bytes": 1.409377e9 + 0.337443584e9,
-                 "algorithmic_bytes": 84 * (4096 * 2048 * 2 + 2048 * 2048)}
+RGEMM_TRAFFIC = {"sha256": "c5721642aa2e6ebba74b9a71aa6b0877c7395608d04da649dbe9276dcbb427b8",
+                 "dram_bytes": 1.647126e9 + 0.3954368e9,
+                 "algorithmic_bytes": 98 * (2048 * 2048 * 2 * 2 + 2048 * 2048)}
 
 
 def rgemm_traffic(planes, m, n, kpad):
@@ -82,7 +82,13 @@ def rgemm_traffic(planes, m, n, kpad):
     return alg * RGEMM_TRAFFIC["dram_bytes"] / RGEMM_TRAFFIC["algorithmic_bytes"]
 
 
-def scheme_desc(flags, fmm):
+def scheme_desc(flags, fmm, precision="fp64", levels=1):
+    if precision == "ozaki_bf16":
+        s = ("S' formed inside the tensor-core GEMM from int8 residues of A' (tensor-memory A operand), "
+             "T' as fp16 operand planes" if flags & fmm.FLAG_TC_FUSED_S else
+             "S' and T' as bf16 operand planes in HBM")
+        return ("residue space: exponents, then scaling, residues and the first level in one pass per operand; "
+                + s + "; W level 1 fused with the CRT" + ("; later levels on int8 residues" if levels > 1 else ""))
     lw = "level by level" if flags & fmm.FLAG_LEVELWISE else "from unrolled chains"
     st = ("S/T fused into operand staging" if flags & fmm.FLAG_FUSED_ST
           else f"S/T written once to workspace ({lw})")
@@ -166,13 +172,18 @@ def roofline(p, info, m, k, n, leaf_avg, ms_step, region_s, clocks, args):
     kpad = -(-kL // 64) * 64
     leaf_flops = 2.0 * info["leaves"] * nmod * mL * kpad * nL
     achieved = leaf_flops / leaf_avg / 1e9
-    traffic = rgemm_traffic(info["leaves"] * nmod, mL, nL, kpad)
+    fused_s = bool(p.flags & fmm.FLAG_TC_FUSED_S) and Lv <= 1
+    traffic = None if fused_s else rgemm_traffic(info["leaves"] * nmod, mL, nL, kpad)
     other = measured_bf16_peak("sustained" if kind == "burst" else "burst")[0]
+    kname = (f"residue_gemm_fa (tcgen05 kind::f16, S' formed in tensor memory from int8 residues of A', "
+             f"fp16 T' planes, x {nmod} moduli, all leaves)" if fused_s else
+             f"residue_gemm (tcgen05 kind::f16, bf16 residues x {nmod} moduli, all leaves)")
     return dict({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                  "frac": achieved / peak, "traffic": traffic,
                  "traffic_note": ("ncu dram bytes read+written per launch, scaled from the 4096^3 capture by the "
-                                  "algorithmic operand and product bytes" if traffic else None),
-                 "kernel": f"residue_gemm (tcgen05 kind::f16, bf16 residues x {nmod} moduli, all leaves)",
+                                  "algorithmic operand and product bytes" if traffic else
+                                  "no ncu counters for this kernel as built" if fused_s else None),
+                 "kernel": kname,
                  "peak_source": src, "peak_kind": kind,
                  "peak_kind_rule": "burst for a timed region under 1 s with no power cap seen, else sustained",
                  ("frac_of_sustained" if kind == "burst" else "frac_of_burst"): achieved / other,
@@ -263,6 +274,13 @@ def time_e2e(torch, fmm, p, A, B, m, k, n, ms_step, args, ws, stream):
     ems = time_steps(torch, fe, args.steps, stream)
     wall = (time.perf_counter() - t0) * 1e3
     ems = max_over_ranks(torch, ws, max(ems, wall)) / args.steps
+    # the same calls one by one (context: occasional calls take several times
+    # longer on this machine, for the device-only product too)
+    per = []
+    for _ in range(args.steps):
+        t1 = time.perf_counter()
+        fe()
+        per.append((time.perf_counter() - t1) * 1e3)
     # the host link on its own (context: the copies bound the end-to-end time)
     scratch = hws[:Ah.numel() * 8].view(torch.float64).view(Ah.shape)
     scratch.copy_(Ah, non_blocking=True)
@@ -276,6 +294,8 @@ def time_e2e(torch, fmm, p, A, B, m, k, n, ms_step, args, ws, stream):
                         "arrives and each A band as soon as it is in; residue products in row bands, "
                         "each combined and copied out while the next band is multiplied"),
            "link_gbs": {"h2d": Ah.numel() * 8 / h2d_ms / 1e6, "d2h": Ah.numel() * 8 / d2h_ms / 1e6},
+           "per_call_ms": {"median": statistics.median(per), "max": max(per), "min": min(per),
+                           "what": "the same calls timed one by one on the host clock after the timed steps"},
            "serialised_ms": (8 * (m * k + k * n) / (Ah.numel() * 8 / h2d_ms) + 8 * m * n / (Ah.numel() * 8 / d2h_ms)
                              + ms_step)}
     del hws, scratch
@@ -447,34 +467,49 @@ def run_serving(args):
     pool = torch.rand(2 * 8192 * 8192, dtype=torch.float64, device="cuda", generator=gen) * 2 - 1
     shapes = serve.request_shapes(count, seed=1409, shape_pool=args.shape_pool)
     mean_flops = float(np.mean([2.0 * m * k * n for m, k, n in shapes]))
-    # classical capacity on this request mix: a closed-loop run (every request
-    # present at the start) after a short warm-up run
-    def closed_loop(max_levels, n_req):
-        tuner = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False, max_levels=max_levels)
-        reqs = serve.poisson_requests(n_req, 1e12, seed=1409, pool=pool, shape_pool=args.shape_pool)
-        return serve.Server(tuner, memory_budget_bytes=64 << 30, slots=4, use_graphs=True,
-                            keep_results=False).run(reqs)
-    closed_loop(0, min(count, 300))
-    cap_run = closed_loop(0, count)
-    torch.cuda.synchronize()
-    torch.cuda.empty_cache()
-    cap = cap_run["effective_tflops"] * 1e12
-    rate = 0.8 * cap / mean_flops
-    out = {}
     import gc
-    for label, max_levels in (("classical", 0), ("autotuned", 3)):
+
+    def server(max_levels, group=True):
         tuner = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False, max_levels=max_levels)
-        srv = serve.Server(tuner, memory_budget_bytes=64 << 30, slots=4, use_graphs=True, keep_results=False)
-        # an untimed pass over the first requests prepares this server's plans,
-        # workspaces and graphs, then the timed open-loop pass
-        srv.run(serve.poisson_requests(min(count, 300), 1e12, seed=1409, pool=pool, shape_pool=args.shape_pool))
+        return serve.Server(tuner, memory_budget_bytes=64 << 30, slots=4, use_graphs=True, keep_results=False,
+                            group_shapes=group and not args.no_group)
+
+    def warm(srv):
+        # an untimed pass over requests from a DISJOINT seed prepares the
+        # server's plans and workspaces without capturing the timed shapes
+        srv.run(serve.poisson_requests(min(count, 300), 1e12, seed=2409, pool=pool, shape_pool=args.shape_pool))
         srv.stats = serve.Stats()
-        reqs = serve.poisson_requests(count, rate, seed=1409, pool=pool, shape_pool=args.shape_pool)
-        out[label] = srv.run(reqs)
-        del srv, tuner, reqs
+
+    def settle():
         gc.collect()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()   # the next pass starts from the same allocator state
+
+    # closed-loop capacity of each server on this mix (every request present
+    # at the start), each after its own warm-up
+    caps = {}
+    for label, max_levels, group in (("classical", 0, True), ("autotuned", 3, True),
+                                     ("classical_ungrouped", 0, False)):
+        if group is False and args.no_group:
+            continue
+        srv = server(max_levels, group)
+        warm(srv)
+        caps[label] = srv.run(serve.poisson_requests(count, 1e12, seed=1409, pool=pool,
+                                                     shape_pool=args.shape_pool))
+        del srv
+        settle()
+    cap = caps["classical"]["effective_tflops"] * 1e12
+    rate = 0.8 * cap / mean_flops
+    out = {}
+    for label, max_levels in (("classical", 0), ("autotuned", 3)):
+        srv = server(max_levels)
+        warm(srv)
+        reqs = serve.poisson_requests(count, rate, seed=1409, pool=pool, shape_pool=args.shape_pool)
+        out[label] = srv.run(reqs)
+        out[label]["utilisation"] = rate * mean_flops / (caps[label]["effective_tflops"] * 1e12)
+        del srv, reqs
+        settle()
+    cap_run = caps["classical"]
     line = {"metric": METRIC + " (serving)", "value": out["autotuned"]["effective_tflops"], "unit": "TFLOP/s",
             "n_gpus": ws, "steps": count, "warmup": 0, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64 or CRT-emulated f64 per autotuned plan",
@@ -485,7 +520,11 @@ def run_serving(args):
                                    f"{cap/1e12:.1f} TFLOP/s closed-loop)",
                        "precisions": list(precs), "accuracy_target": 1e-11},
             "p50_ms": out["autotuned"]["p50_ms"], "p99_ms": out["autotuned"]["p99_ms"],
-            "autotuned": out["autotuned"], "classical": out["classical"], "classical_closed_loop": cap_run}
+            "autotuned": out["autotuned"], "classical": out["classical"],
+            "closed_loop": caps,
+            "capacity_ratio_autotuned_vs_classical": (caps["autotuned"]["effective_tflops"]
+                                                      / caps["classical"]["effective_tflops"]),
+            "warmup": "300 requests from a disjoint seed (2409) per server, untimed"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -605,6 +644,8 @@ def main():
     ap.add_argument("--impl", default="fmm", choices=["fmm", "reference"])
     ap.add_argument("--workload", default="square8192", choices=sorted(WORKLOADS) + ["serving", "tune", "ablation"])
     ap.add_argument("--requests", type=int, default=2000, help="serving workload: number of requests")
+    ap.add_argument("--no-group", action="store_true",
+                    help="serving workload: no grouped calls across shapes")
     ap.add_argument("--shape-pool", type=int, default=0,
                     help="serving workload: draw shapes from this many (0: every request its own shape)")
     ap.add_argument("--plan", default=None, help="NAME:LEVELS to skip the candidate trial")
@@ -622,6 +663,7 @@ def main():
                     help="headline accuracy gate: fp64 = no worse than native FP64 Strassen L1 (and --tol); "
                          "tol = --tol alone")
     ap.add_argument("--no-fp64", action="store_true", help="skip the timed native-FP64 sub-record")
+    ap.add_argument("--no-fs", action="store_true", help="no candidates with S' formed inside the GEMM")
     ap.add_argument("--precisions", default="fp64,ozaki_bf16",
                     help="comma list of leaf precisions to try: fp64, ozaki_bf16, tf32, fp32")
     args = ap.parse_args()
@@ -668,7 +710,8 @@ def main():
 
     # candidates (algorithm files that exist), plus the classical comparator
     schemes = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "wo_st": fmm.FLAG_FUSED_W,
-               "lw_st": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W, "lw": fmm.FLAG_LEVELWISE}
+               "lw_st": fmm.FLAG_LEVELWISE | fmm.FLAG_FUSED_W, "lw": fmm.FLAG_LEVELWISE,
+               "fs": fmm.FLAG_LEVELWISE | fmm.FLAG_TC_FUSED_S}
     precs = args.precisions.split(",")
     fp64_schemes = list(schemes) if args.all_schemes else ["fused", "lw"]
     cands = []
@@ -677,10 +720,13 @@ def main():
             cands += [(a, L, sc, prec) for a, L in wl["cands"] if os.path.exists(fmm.algorithm_path(a))
                       for sc in (fp64_schemes if not args.fused_only else ["fused"])]
         else:
-            # tensor-core leaves: the classical product (0 levels) and the fast plans
-            cands += [("strassen_222_7", 0, "lw", prec)]
-            cands += [(a, L, "lw", prec) for a, L in wl["cands"]
-                      if os.path.exists(fmm.algorithm_path(a)) and L <= 2]
+            # tensor-core leaves: the classical product (0 levels) and the fast plans;
+            # emulated ones at <= 1 level also with S' formed inside the GEMM
+            sch = ["lw", "fs"] if prec == "ozaki_bf16" and not args.no_fs else ["lw"]
+            cands += [("strassen_222_7", 0, sc, prec) for sc in sch]
+            cands += [(a, L, sc, prec) for a, L in wl["cands"]
+                      if os.path.exists(fmm.algorithm_path(a)) and L <= 2
+                      for sc in (sch if L <= 1 else ["lw"])]
     if args.plan:
         parts = args.plan.split(":")
         cands = [(parts[0], int(parts[1]), parts[2] if len(parts) > 2 else "fused",
@@ -831,7 +877,7 @@ def main():
                 p.precision, f"bf16 residues x {p.moduli or args.moduli} (CRT-emulated f64)"),
             "data": f"synthetic {args.data} (PCG64 seed 1410)",
             "config": {"workload": wl["desc"], "m": m, "k": k, "n": n, "plan": best["plan"],
-                       "scheme": scheme_desc(p.flags, fmm), "leaf_tile": "auto",
+                       "scheme": scheme_desc(p.flags, fmm, p.precision, p.levels), "leaf_tile": "auto",
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "accuracy_gate": {"rule": gate_rule, "value": gate},

@@ -117,6 +117,15 @@ enum {
        for STREAMING. */
     FMM_FLAG_STREAMING = 1u << 4,
     FMM_FLAG_PAIRWISE = 1u << 5,
+    /* Emulated-FP64 plans in residue space with at most one recursive level
+       (or none): form each leaf's S' inside the tensor-core GEMM from the int8
+       residues of A' (converter warps combine the leaf's one or two blocks and
+       store the fp16 operand in tensor memory, which tcgen05 reads as its A
+       operand), so no S' operand plane is written to HBM; T' comes from fp16
+       planes.  Used where every leaf's S' has at most two terms with
+       sum |c| <= 2 and the k blocks are multiples of 16; otherwise ignored.
+       Same integers, so the same result bit for bit. */
+    FMM_FLAG_TC_FUSED_S = 1u << 6,
     FMM_FLAGS_DEFAULT = FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W
 };
 
@@ -294,6 +303,29 @@ fmm_status fmm_gemm_batched(fmm_plan_t plan, int64_t count,
                             double *const *C, int64_t ldc, int64_t m, int64_t k,
                             int64_t n, void *workspace, size_t ws_bytes,
                             void *stream);
+
+/*
+ * fmm_gemm_grouped - `count` independent products C_i = A_i B_i of any
+ * shapes, each with its own plan, issued together on `stream`.  The residue
+ * GEMMs of the emulated-FP64 products whose plans run in residue space with at
+ * most one recursive level (or none) go into grouped tensor-core launches of
+ * up to 8 products each (one persistent launch over all their tiles, which
+ * fills the GPU where a single small product cannot); every other step, and
+ * every other product, runs as fmm_gemm would run it.  Each result is the
+ * same, bit for bit, as fmm_gemm's for that product alone.
+ *
+ * plans, A, lda, B, ldb, C, ldc, m, k, n, ws, ws_bytes: HOST arrays of
+ * `count` entries, each entry as the matching argument of fmm_gemm (ws[i] of
+ * at least fmm_workspace_size(plans[i], m[i], k[i], n[i]) bytes; the C_i
+ * may not overlap each other or any operand).  count 1..4096.
+ * Errors: as fmm_gemm, checked for every product before anything runs.
+ */
+fmm_status fmm_gemm_grouped(int64_t count, const fmm_plan_t *plans,
+                            const double *const *A, const int64_t *lda,
+                            const double *const *B, const int64_t *ldb,
+                            double *const *C, const int64_t *ldc,
+                            const int64_t *m, const int64_t *k, const int64_t *n,
+                            void *const *ws, const size_t *ws_bytes, void *stream);
 
 /*
  * fmm_classical_gemm - C = A B by the library's classical FP64 GEMM (the

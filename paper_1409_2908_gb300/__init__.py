@@ -30,6 +30,7 @@ FLAG_LEVELWISE = 4
 FLAG_LEAF_EMULATION = 8
 FLAG_STREAMING = 16
 FLAG_PAIRWISE = 32
+FLAG_TC_FUSED_S = 64
 FLAGS_DEFAULT = FLAG_FUSED_ST | FLAG_FUSED_W
 
 TILES = {"auto": 0, "128x128": 1, "96x96": 2, "64x64": 3, "32x32": 4, "128x64": 5, "64x128": 6}
@@ -126,6 +127,8 @@ class Plan:
         self.flags = flags
         self.name = algorithm if factors is None else "custom"
         self.precision = precision
+        self.moduli = moduli if precision == "ozaki_bf16" else None
+        self.tile = tile
         if tile != "auto":
             self.set_tile(tile)
         if moduli is not None:
@@ -141,6 +144,17 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def dims(self):
+        """(M, K, N) of the base case."""
+        inf = self.info()
+        return inf["M"], inf["K"], inf["N"]
+
+    @property
+    def rank(self):
+        """R, the base case's number of products."""
+        return self.info()["R"]
 
     def info(self):
         inf = _lib.PlanInfo()
@@ -247,6 +261,37 @@ def gemm_batched(plan, As, Bs, Cs=None, workspace=None, stream=None):
                                      workspace.numel() * workspace.element_size(),
                                      _stream_handle(stream))
     _check(st, "fmm_gemm_batched")
+    return Cs
+
+
+def gemm_grouped(plans, As, Bs, Cs=None, workspaces=None, stream=None):
+    """C_i = A_i B_i for products of any shapes, each with its own plan, issued
+    together (fmm_gemm_grouped): the emulated products' residue GEMMs share
+    grouped tensor-core launches.  Returns the C list."""
+    import torch
+    count = len(plans)
+    if count == 0 or len(As) != count or len(Bs) != count:
+        raise ValueError("need one A and one B per plan")
+    ma = [_mat(a, "A") for a in As]
+    mb = [_mat(b, "B") for b in Bs]
+    if any(x[3] != y[2] for x, y in zip(ma, mb)):
+        raise ValueError("inner dimensions differ")
+    if Cs is None:
+        Cs = [torch.empty((x[2], y[3]), dtype=torch.float64, device=a.device) for x, y, a in zip(ma, mb, As)]
+    mc = [_mat(c, "C") for c in Cs]
+    if workspaces is None:
+        workspaces = [_alloc_ws(p.workspace_size(x[2], x[3], y[3]), a.device) for p, x, y, a in zip(plans, ma, mb, As)]
+    P = ctypes.c_void_p * count
+    I64 = ctypes.c_int64 * count
+    SZ = ctypes.c_size_t * count
+    ws_ptr = P(*[w.data_ptr() if w is not None else None for w in workspaces])
+    ws_b = SZ(*[w.numel() * w.element_size() if w is not None else 0 for w in workspaces])
+    st = _lib.lib().fmm_gemm_grouped(
+        count, P(*[p.handle.value for p in plans]), P(*[x[0].value for x in ma]), I64(*[x[1] for x in ma]),
+        P(*[x[0].value for x in mb]), I64(*[x[1] for x in mb]), P(*[x[0].value for x in mc]),
+        I64(*[x[1] for x in mc]), I64(*[x[2] for x in ma]), I64(*[x[3] for x in ma]), I64(*[x[3] for x in mb]),
+        ws_ptr, ws_b, _stream_handle(stream))
+    _check(st, "fmm_gemm_grouped")
     return Cs
 
 

@@ -73,6 +73,8 @@ def _declare(L):
     L.fmm_timing_enable.restype = st
     L.fmm_timing_leaf_ms.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     L.fmm_timing_leaf_ms.restype = st
+    L.fmm_gemm_grouped.argtypes = [c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p]
+    L.fmm_gemm_grouped.restype = st
     L.fmm_set_wait_limit.argtypes = [ctypes.c_uint64]
     L.fmm_set_wait_limit.restype = st
     L.fmm_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_uint64, c_p]

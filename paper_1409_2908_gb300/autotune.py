@@ -14,6 +14,7 @@ JSON file).
 
 Nothing here computes the product: every candidate runs through the C ABI.
 """
+import functools
 import glob
 import json
 import math
@@ -175,6 +176,7 @@ def beta_for(n, k):
     return beta
 
 
+@functools.lru_cache(maxsize=4096)
 def moduli_for(tol, k):
     """Fewest moduli whose rounding error 2^-beta (with a factor 2 of slack;
     the e_F measured on uniform data is about 0.9 x 2^-beta once the scaled
@@ -225,6 +227,10 @@ class Autotuner:
         self.cache_file = cache_file
         self.measure = measure
         self.permutations = permutations
+        # model rates (this GPU's measured defaults; calibrate() re-measures them)
+        self.fp64_tflops = FP64_TFLOPS
+        self.tc_tflops = TC_TFLOPS
+        self.pass_scale = 1.0        # measured / modelled time of the emulated path's passes
         self._cache = {}
         self._plans = {}
         if cache_file and os.path.exists(cache_file):
@@ -233,33 +239,109 @@ class Autotuner:
                     self._cache[key] = Choice(**d)
 
     # ----------------------------------------------------------- model
-    def candidates(self, m, k, n):
-        """Every admissible candidate with its model time (ms), best first:
-        each shipped base case and (with permutations) each ordering of its
-        dimensions (Section 2.3), at 0..max_levels levels, every listed leaf
-        precision, with the leaf tile the model prefers."""
+    def _cases(self):
+        """(name, perm, (M, K, N, R), W nonzeros) of every case searched."""
+        if getattr(self, "_case_list", None) is None:
+            allc = cases() if self.permutations else {(nm, ""): b for nm, b in algorithms().items()}
+            self._case_list = [(nm, pm, b, self._w_terms(nm, pm)) for (nm, pm), b in allc.items()]
+        return self._case_list
+
+    def _space(self, m, k, n):
+        """(lower bound ms, name, perm, base, levels, precision, moduli) of
+        every admissible candidate: each shipped base case and (with
+        permutations) each ordering of its dimensions (Section 2.3), at
+        0..max_levels levels, every listed leaf precision.  The bound is the
+        model time with every efficiency factor set to 1 (the leaf products
+        at the precision's full rate; the emulated path's passes, CRT and
+        launches as modelled; the classical fringe): no model time can be
+        lower."""
         out = []
         nmod = moduli_for(self.tol, k) if "ozaki_bf16" in self.precisions else None
-        allc = cases() if self.permutations else {(nm, ""): b for nm, b in algorithms().items()}
+        rate = {"fp64": self.fp64_tflops, "ozaki_bf16": self.tc_tflops / (nmod or 1), **TF32_TFLOPS}
         for prec in self.precisions:
             if prec == "ozaki_bf16" and nmod is None:
                 continue
             if prec in TF32_ERR and 2 * TF32_ERR[prec][0] > self.tol:
                 continue
-            out.append(self._model(m, k, n, "strassen_222_7", "", (2, 2, 2, 7), 0, prec, nmod))
-            for (name, perm), base in allc.items():
+            work = 3.0 if prec == "fp32" else 1.0
+            entries = [("strassen_222_7", "", (2, 2, 2, 7), 0, 1)]
+            for name, perm, base, wt in self._cases():
                 M, K, N, R = base
                 for L in range(1, self.max_levels + 1):
-                    mL, kL, nL = m // M ** L, k // K ** L, n // N ** L
-                    if min(mL, kL, nL) < 64 or R ** L > 20000:
+                    if min(m // M ** L, k // K ** L, n // N ** L) < 64 or R ** L > 20000:
                         break
                     if prec == "ozaki_bf16" and R ** L * nmod > 65535:
                         break
-                    out.append(self._model(m, k, n, name, perm, base, L, prec, nmod))
+                    entries.append((name, perm, base, L, wt))
+            for name, perm, base, L, wt in entries:
+                M, K, N, R = base
+                sm, sk, sn = M ** L, K ** L, N ** L
+                mp, kp, np_ = (m // sm) * sm, (k // sk) * sk, (n // sn) * sn
+                lb = (2.0 * (R / (M * K * N)) ** L * mp * kp * np_ * work / (rate[prec] * 1e12)
+                      + 2.0 * (m * n * k - mp * np_ * kp) / (self.fp64_tflops * 1e12))
+                out.append((1e3 * lb, name, perm, base, L, prec, nmod, (mp, kp, np_, wt)))
+        out.sort(key=lambda e: e[0])
+        return out
+
+    def _bound(self, e):
+        """The tighter bound of a _space entry: its leaf and fringe bound plus,
+        for the emulated path, the modelled passes."""
+        lb, name, perm, base, L, prec, nmod, (mp, kp, np_, wt) = e
+        if prec == "ozaki_bf16":
+            M, K, N, R = base
+            lb += 1e3 * self._emulated_passes(mp, kp, np_, M, K, N, R, L, nmod, wt)
+        return lb
+
+    def _emulated_passes(self, mp, kp, np_, M, K, N, R, L, nmod, wterms):
+        """Seconds of the emulated path's passes besides the residue GEMM
+        (exponents, the fused first level, later levels, W + CRT, launches)."""
+        grow_a = R / (M * K) if L else 1.0
+        grow_b = R / (K * N) if L else 1.0
+        width = 2 if L <= 1 else 1
+        t = (mp * kp + kp * np_) * 8 * 2 / (HBM_GBS * 1e9)
+        t += (mp * kp * (8 + grow_a * nmod * width) + kp * np_ * (8 + grow_b * nmod * width)) / (SPLIT_GBS * 1e9)
+        if L and (M * K not in FUSED_BLOCKS or K * N not in FUSED_BLOCKS):
+            # no fused first level for this block grid: a residue pass first
+            t += (mp * kp + kp * np_) * (8 + 2 * nmod) / (LEVEL_GBS * 1e9)
+        for l in range(2, L + 1):
+            w = 2 if l == L else 1
+            ml, kl, nl = mp // M ** l, kp // K ** l, np_ // N ** l
+            t += R ** l * (ml * kl + kl * nl) * nmod * (2 + w) / (LEVEL_GBS * 1e9)
+            t += R ** (l - 1) * M * N * ml * nl * nmod * 3 / (LEVEL_GBS * 1e9)
+        terms = (wterms / (M * N)) if L else 1.0
+        t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12 * (1.0 + W_TERM_FACTOR * (terms - 1.0))
+        t += (6 + 3 * max(L - 1, 0)) * LAUNCH_US * 1e-6
+        return t * self.pass_scale
+
+    def candidates(self, m, k, n):
+        """Every admissible candidate with its model time (ms), best first,
+        with the leaf tile the model prefers."""
+        out = [self._model(m, k, n, name, perm, base, L, prec, nmod)
+               for _, name, perm, base, L, prec, nmod, _ in self._space(m, k, n)]
         # FP64 error grows with depth; drop plans that cannot meet the target
         out = [c for c in out if c is not None]
         out.sort(key=lambda c: c.model_ms)
         return out
+
+    def best_candidates(self, m, k, n, count=1):
+        """The `count` candidates of least model time, found by branch and
+        bound: candidates in order of their lower bound, stopping once the
+        bound exceeds the count-th best model time so far (the same answer
+        as candidates()[:count], at a fraction of the model evaluations)."""
+        best = []
+        for e in self._space(m, k, n):
+            if len(best) >= count and e[0] > best[count - 1].model_ms:
+                break
+            if len(best) >= count and self._bound(e) > best[count - 1].model_ms:
+                continue
+            _, name, perm, base, L, prec, nmod, _ = e
+            c = self._model(m, k, n, name, perm, base, L, prec, nmod)
+            if c is None:
+                continue
+            best.append(c)
+            best.sort(key=lambda c: c.model_ms)
+            best = best[:count]
+        return best
 
     def _model(self, m, k, n, name, perm, base, L, prec, nmod):
         M, K, N, R = base
@@ -277,7 +359,7 @@ class Autotuner:
             leaf_flops = 2.0 * leaves * mL * kL * nL
             best = None
             for tname, (bm, bn, speed) in FP64_TILES.items():
-                tt = leaf_flops / (FP64_TFLOPS * 1e12 * speed * classical_efficiency(mL, nL, bm, bn, leaves))
+                tt = leaf_flops / (self.fp64_tflops * 1e12 * speed * classical_efficiency(mL, nL, bm, bn, leaves))
                 if best is None or tt < best[0]:
                     best = (tt, tname)
             t, tile = best
@@ -315,30 +397,14 @@ class Autotuner:
             for tname, speed in TC_TILES.items():
                 tile_n = 256 if (nL >= 256 and tname == "auto") else 128
                 tt = 2.0 * leaves * nmod * mL * kpad * nL / (
-                    TC_TFLOPS * 1e12 * speed * classical_efficiency(mL, nL, 128, tile_n, leaves * nmod))
+                    self.tc_tflops * 1e12 * speed * classical_efficiency(mL, nL, 128, tile_n, leaves * nmod))
                 if best is None or tt < best[0]:
                     best = (tt, tname)
             t, tile = best
-            # exponents, then the fused first level: FP64 in, R/(MK) residue
-            # planes out per operand element (bfloat16 when it is the last level)
-            grow_a = R / (M * K) if L else 1.0
-            grow_b = R / (K * N) if L else 1.0
-            width = 2 if L <= 1 else 1
-            t += (mp * kp + kp * np_) * 8 * 2 / (HBM_GBS * 1e9)
-            t += (mp * kp * (8 + grow_a * nmod * width) + kp * np_ * (8 + grow_b * nmod * width)) / (SPLIT_GBS * 1e9)
-            if L and (M * K not in FUSED_BLOCKS or K * N not in FUSED_BLOCKS):
-                # no fused first level for this block grid: a residue pass first
-                t += (mp * kp + kp * np_) * (8 + 2 * nmod) / (LEVEL_GBS * 1e9)
-            for l in range(2, L + 1):
-                w = 2 if l == L else 1
-                ml, kl, nl = mp // M ** l, kp // K ** l, np_ // N ** l
-                t += R ** l * (ml * kl + kl * nl) * nmod * (2 + w) / (LEVEL_GBS * 1e9)
-                t += R ** (l - 1) * M * N * ml * nl * nmod * 3 / (LEVEL_GBS * 1e9)
-            terms = (self._w_terms(name, perm) / (M * N)) if L else 1.0
-            t += mp * np_ * nmod * CRT_PS_PER_ELEM_MOD * 1e-12 * (1.0 + W_TERM_FACTOR * (terms - 1.0))
-            t += (6 + 3 * max(L - 1, 0)) * LAUNCH_US * 1e-6
+            t += self._emulated_passes(mp, kp, np_, M, K, N, R, L, nmod,
+                                       self._w_terms(name, perm) if L else M * N)
             flags = fmm.FLAGS_DEFAULT
-        t += fringe / (FP64_TFLOPS * 1e12)
+        t += fringe / (self.fp64_tflops * 1e12)
         return Choice(name, L, flags, prec, nmod or 15, tile, 1e3 * t, perm=perm if L else "")
 
     def _w_terms(self, name, perm=""):
@@ -350,6 +416,50 @@ class Autotuner:
             self._wnnz[(name, perm)] = int((_factors(name, perm)[5] != 0).sum())
         return self._wnnz[(name, perm)]
 
+    # ----------------------------------------------------------- calibration
+    def calibrate(self, size=4096, nmod=12):
+        """Re-measure the model's rates on this GPU: the classical FP64 GEMM
+        (flops per second at size/2), the residue GEMM (the leaf launch of a
+        classical emulated product at `size`, timed with the library's event
+        pair) and the emulated path's other passes (the rest of that product,
+        as a scale on their modelled time).  Clears the choice cache; returns
+        the rates."""
+        import torch
+        n2 = size // 2
+        A = torch.rand((n2, n2), dtype=torch.float64, device="cuda")
+        fmm.classical_gemm(A, A)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fmm.classical_gemm(A, A)
+        e1.record()
+        e1.synchronize()
+        self.fp64_tflops = 2.0 * n2 ** 3 / e0.elapsed_time(e1) / 1e9
+        B = torch.rand((size, size), dtype=torch.float64, device="cuda")
+        p = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=nmod)
+        ws = torch.empty(p.workspace_size(size, size, size), dtype=torch.uint8, device="cuda")
+        C = torch.empty_like(B)
+        fmm.gemm(p, B, B, C=C, workspace=ws)
+        torch.cuda.synchronize()
+        fmm.timing_enable(True)
+        e0.record()
+        for _ in range(3):
+            fmm.gemm(p, B, B, C=C, workspace=ws)
+        e1.record()
+        e1.synchronize()
+        leaf_ms, leaf_n = fmm.timing_leaf_ms()
+        fmm.timing_enable(False)
+        step = e0.elapsed_time(e1) / 3
+        leaf = leaf_ms / max(leaf_n, 1)
+        kpad = -(-size // 64) * 64
+        self.tc_tflops = 2.0 * nmod * size * kpad * size * classical_efficiency(size, size, 128, 256, nmod) ** -1 \
+            / leaf / 1e9
+        modelled = self._emulated_passes(size, size, size, 1, 1, 1, 1, 0, nmod, 1) / self.pass_scale
+        self.pass_scale = max(step - leaf, 1e-3) * 1e-3 / modelled
+        self._cache.clear()
+        del A, B, C, ws
+        return {"fp64_tflops": self.fp64_tflops, "tc_tflops": self.tc_tflops, "pass_scale": self.pass_scale}
+
     # ----------------------------------------------------------- choice
     def choose(self, m, k, n):
         """The choice for (m, k, n).  Without measurement: the model's best.
@@ -359,9 +469,10 @@ class Autotuner:
         or down until its measured e_F meets the target with the fewest
         moduli), then timed (median of three calls); the fastest kept."""
         key = f"{m}x{k}x{n}:{self.tol:g}:{','.join(self.precisions)}"
-        if key in self._cache:
-            return self._cache[key]
-        cands = self.candidates(m, k, n)
+        c = self._cache.get(key)
+        if c is not None:
+            return c
+        cands = self.best_candidates(m, k, n, max(1, self.trials if self.measure else 1))
         best = cands[0]
         if self.measure and self.trials > 0:
             import torch

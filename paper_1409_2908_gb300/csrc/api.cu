@@ -138,6 +138,8 @@ ResPlan res_plan(const fmm_plan *p) {
     rp.vt_code = p->dev.lvt_code;
     rp.w_ptr = p->dev.lw_ptr; rp.w_r = p->dev.lw_r; rp.w_icoef = p->dev.lw_icoef;
     rp.tile = p->tile;
+    rp.fused_s = (p->flags & FMM_FLAG_TC_FUSED_S) != 0;
+    rp.hU = p->U.data();
     rp.w_absmax = 0;
     for (int q = 0; q < p->M * p->N; ++q) {
         double sum = 0;
@@ -448,7 +450,7 @@ cudaError_t w_level(const fmm_plan *p, const double *child, int64_t rows, int64_
 fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, const double *A,
                           int64_t lda, const double *B, int64_t ldb, double *C, int64_t ldc,
                           int64_t m, int64_t k, int64_t n, char *wsb, cudaStream_t s,
-                          int *launches, const HostPipe *pipe) {
+                          int *launches, const HostPipe *pipe, GemmDefer *defer = nullptr) {
     cudaError_t e;
     // the overlap hooks reach only the residue-space path without a fringe
     const bool fringe = g.mp < m || g.kp < k || g.np < n;
@@ -464,18 +466,22 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
                   : ozaki_products(S_, lds, ss, T_, ldt, ts, Out, ldo, os, leaves, mm, kk, nn, p->nmod,
                                    wsb + wl.oz, s, launches, p->tile);
     };
+    if (defer && (tf || (p->L > 0 && !residue_space(p)))) return FMM_ERR_UNSUPPORTED;
     if (p->L == 0)
         return cuda_status(tf ? leaf_products(A, lda, 0, B, ldb, 0, C, ldc, 0, 1, m, k, n)
                               : ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, m, k, n, p->nmod, 0, wsb, s,
-                                           launches, pipe));
+                                           launches, pipe, defer));
     if (!tf && residue_space(p)) {
         const bool kfr = g.kp < k;
-        if (kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
-                                         g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
+        // (two phases: the k-fringe before, the row and column fringes after the GEMM)
+        const bool first = !defer || defer->phase == 0, last = !defer || defer->phase == 1;
+        if (first && kfr && (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp,
+                                                  g.np, FMM_TILE_AUTO, s, launches)) != cudaSuccess)
             return cuda_status(e);
         if ((e = ozaki_fast(res_plan(p), A, lda, B, ldb, C, ldc, g.mp, g.kp, g.np, p->nmod,
-                            kfr ? 1 : 0, wsb + wl.oz, s, launches, pipe)) != cudaSuccess)
+                            kfr ? 1 : 0, wsb + wl.oz, s, launches, pipe, defer)) != cudaSuccess)
             return cuda_status(e);
+        if (!last) return FMM_OK;
         if (g.mp < m &&
             (e = launch_classical(A + g.mp * lda, lda, B, ldb, C + g.mp * ldc, ldc, m - g.mp, k, n,
                                   FMM_TILE_AUTO, s, launches)) != cudaSuccess)
@@ -537,9 +543,11 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
 // for B first and drop them.
 fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, int64_t ldb,
                     double *C, int64_t ldc, int64_t m, int64_t k, int64_t n, void *ws,
-                    size_t ws_bytes, cudaStream_t s, int *launches, const HostPipe *pipe = nullptr) {
+                    size_t ws_bytes, cudaStream_t s, int *launches, const HostPipe *pipe = nullptr,
+                    GemmDefer *defer = nullptr) {
     const Geometry g = geometry(p, m, k, n);
     const bool emulated = (p->prec == FMM_PREC_OZAKI_BF16 || tf32_family(p)) && (p->L == 0 || g.fast);
+    if (defer && !emulated) return FMM_ERR_UNSUPPORTED;
     if (!emulated) {
         const cudaError_t pe = settle_pipe(pipe, s);
         if (pe != cudaSuccess) return cuda_status(pe);
@@ -552,7 +560,7 @@ fmm_status run_gemm(fmm_plan *p, const double *A, int64_t lda, const double *B, 
         if (wl.total > 0 && ((uintptr_t)ws & 255)) return FMM_ERR_ARG;
         const fmm_status us = ensure_uploaded(p);
         if (us != FMM_OK) return us;
-        return run_gemm_ozaki(p, g, wl, A, lda, B, ldb, C, ldc, m, k, n, (char *)ws, s, launches, pipe);
+        return run_gemm_ozaki(p, g, wl, A, lda, B, ldb, C, ldc, m, k, n, (char *)ws, s, launches, pipe, defer);
     }
     if (!g.fast)
         return cuda_status(timed(s, [&] {
@@ -721,7 +729,8 @@ fmm_status fmm_plan_create(fmm_plan_t *out, int M, int K, int N, int R, const do
     if (prec != FMM_PREC_FP64 && prec != FMM_PREC_OZAKI_BF16 && prec != FMM_PREC_TF32 && prec != FMM_PREC_FP32)
         return FMM_ERR_UNSUPPORTED;
     if (flags & ~unsigned(FMM_FLAG_FUSED_ST | FMM_FLAG_FUSED_W | FMM_FLAG_LEVELWISE |
-                          FMM_FLAG_LEAF_EMULATION | FMM_FLAG_STREAMING | FMM_FLAG_PAIRWISE))
+                          FMM_FLAG_LEAF_EMULATION | FMM_FLAG_STREAMING | FMM_FLAG_PAIRWISE |
+                          FMM_FLAG_TC_FUSED_S))
         return FMM_ERR_ARG;
     if ((flags & FMM_FLAG_STREAMING) && (flags & FMM_FLAG_PAIRWISE)) return FMM_ERR_ARG;
     bool representable = true;
@@ -859,6 +868,79 @@ fmm_status fmm_gemm(fmm_plan_t p, const double *A, int64_t lda, const double *B,
                   &launches);
     t_launches = launches;
     return st;
+}
+
+fmm_status fmm_gemm_grouped(int64_t count, const fmm_plan_t *plans, const double *const *A, const int64_t *lda,
+                            const double *const *B, const int64_t *ldb, double *const *C, const int64_t *ldc,
+                            const int64_t *m, const int64_t *k, const int64_t *n, void *const *ws,
+                            const size_t *ws_bytes, void *stream) {
+    t_launches = 0;
+    if (count < 1 || count > 4096 || !plans || !A || !lda || !B || !ldb || !C || !ldc || !m || !k || !n ||
+        !ws_bytes || !ws)
+        return FMM_ERR_ARG;
+    std::vector<int> grouped;
+    for (int64_t i = 0; i < count; ++i) {
+        fmm_plan *p = plans[i];
+        if (!p) return FMM_ERR_ARG;
+        fmm_status st = check_operands(A[i], lda[i], B[i], ldb[i], C[i], ldc[i], m[i], k[i], n[i]);
+        if (st != FMM_OK) return st;
+        const Geometry g = geometry(p, m[i], k[i], n[i]);
+        const size_t need = ws_layout(p, g).total;
+        if (need > 0 && (!ws[i] || ws_bytes[i] < need)) return FMM_ERR_NO_MEMORY;
+        if (need > 0 && ((uintptr_t)ws[i] & 255)) return FMM_ERR_ARG;
+        // the GEMMs of emulated residue-space products (at most one recursive
+        // level) are grouped; everything else runs as fmm_gemm would
+        if (p->prec == FMM_PREC_OZAKI_BF16 && p->L <= 1 && (p->L == 0 || (g.fast && residue_space(p))) &&
+            g.kL <= 65536 && !(p->flags & FMM_FLAG_TC_FUSED_S))
+            grouped.push_back(int(i));
+    }
+    for (int64_t i = 0; i < count; ++i)
+        for (int64_t j = 0; j < count; ++j) {
+            if (j == i) continue;
+            const size_t ci = span(m[i], n[i], ldc[i]);
+            if (overlaps(C[i], ci, C[j], span(m[j], n[j], ldc[j])) ||
+                overlaps(C[i], ci, A[j], span(m[j], k[j], lda[j])) ||
+                overlaps(C[i], ci, B[j], span(k[j], n[j], ldb[j])))
+                return FMM_ERR_ARG;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    int launches = 0;
+    std::vector<char> is_grouped(count, 0);
+    for (int i : grouped) is_grouped[i] = 1;
+    for (int64_t i = 0; i < count; ++i) {
+        if (is_grouped[i]) continue;
+        const fmm_status st = run_gemm(plans[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i], m[i], k[i], n[i], ws[i],
+                                       ws_bytes[i], s, &launches);
+        if (st != FMM_OK) return st;
+    }
+    int *err = nullptr;
+    if (!grouped.empty() && device_error_flag(&err) != cudaSuccess) return FMM_ERR_CUDA;
+    for (size_t c0 = 0; c0 < grouped.size(); c0 += RG_MAX_PROBLEMS) {
+        const size_t c1 = std::min(grouped.size(), c0 + RG_MAX_PROBLEMS);
+        std::vector<GemmDefer> d(c1 - c0);
+        bool narrow = false;
+        for (size_t t = c0; t < c1; ++t) {
+            const int i = grouped[t];
+            d[t - c0].phase = 0;
+            const fmm_status st = run_gemm(plans[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i], m[i], k[i], n[i],
+                                           ws[i], ws_bytes[i], s, &launches, nullptr, &d[t - c0]);
+            if (st != FMM_OK) return st;
+            narrow = narrow || d[t - c0].narrow;
+        }
+        std::vector<RgDesc> gd;
+        for (auto &x : d) gd.push_back(x.gemm);
+        cudaError_t e = launch_residue_gemm_group(gd.data(), int(gd.size()), err, s, &launches, narrow);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (size_t t = c0; t < c1; ++t) {
+            const int i = grouped[t];
+            d[t - c0].phase = 1;
+            const fmm_status st = run_gemm(plans[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i], m[i], k[i], n[i],
+                                           ws[i], ws_bytes[i], s, &launches, nullptr, &d[t - c0]);
+            if (st != FMM_OK) return st;
+        }
+    }
+    t_launches = launches;
+    return FMM_OK;
 }
 
 fmm_status fmm_workspace_size_batched(fmm_plan_t p, int64_t count, int64_t m, int64_t k,

@@ -168,6 +168,21 @@ cudaError_t read_device_error(int *flag, bool clear);
 // time limit of the tensor-core kernels' bounded waits (fmm_set_wait_limit)
 unsigned long long wait_limit_ns();
 void set_wait_limit_ns(unsigned long long ns);
+// One problem of a grouped residue GEMM launch (launch_residue_gemm_group):
+// operand planes ra (S', plane_m x kpad bf16 per plane, rows [r0, r0 + m)
+// used) and rb (T'^T, n x kpad), products into Z (planes of m x z_pitch(n)).
+constexpr int RG_MAX_PROBLEMS = 8;   // problems per grouped residue GEMM launch
+// Device address of the tensor-core kernels' error flag (g_device_error).
+cudaError_t device_error_flag(int **out);
+struct RgDesc {
+    const void *ra, *rb;
+    int8_t *Z;
+    int64_t m, n, kpad, planes;
+    int nmod;
+    int64_t r0, plane_m;
+};
+cudaError_t launch_residue_gemm_group(const RgDesc *d, int count, int *err, cudaStream_t s, int *launches,
+                                      bool narrow);
 // kernels of the timeout tests: a wait that nothing completes runs out
 cudaError_t residue_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
 cudaError_t tf32_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
@@ -191,6 +206,8 @@ struct ResPlan {
     int w_absmax;                            // max over C blocks of sum_r |W_qr|
     int u_absmax, v_absmax;                  // max over r of sum_i |U_ir|, of sum_j |V_jr|
     int tile;                                // the plan's fmm_tile (128x128: narrow GEMM tiles)
+    bool fused_s;                            // form S' inside the residue GEMM where it can
+    const double *hU;                        // the base U on the host (MK x R), for that choice
 };
 size_t ozaki_fast_workspace(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod);
 // Overlap hooks of the host entry point.  b_ready (or null): an event the
@@ -214,10 +231,18 @@ struct HostPipe {
     cudaError_t (*band_done)(void *ctx, int64_t r0, int64_t r1, int64_t block_rows, int block_rows_count);
     void *ctx;
 };
+// A product split around its residue GEMM, for grouped launches: phase 0
+// enqueues what comes before the GEMM and fills `gemm`; phase 1 what comes
+// after it (the caller launches the GEMMs of several products in between).
+struct GemmDefer {
+    int phase;
+    RgDesc gemm;
+    bool narrow;
+};
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
                        int accumulate, void *ws, cudaStream_t s, int *launches,
-                       const HostPipe *pipe = nullptr);
+                       const HostPipe *pipe = nullptr, GemmDefer *defer = nullptr);
 
 int resolve_tile(int requested, int64_t mL, int64_t nL, int64_t kL, int64_t leaves,
                  double extra_a, double extra_b, int num_sms);

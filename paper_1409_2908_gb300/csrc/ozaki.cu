@@ -24,6 +24,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <atomic>
@@ -95,6 +96,7 @@ __device__ __forceinline__ int bal_mod_q(int x, int q) {
 }
 
 #include "residue_gemm.cuh"
+#include "residue_gemm_fa.cuh"
 
 // Exponent e with 2^e <= |x| < 2^(e+1) for normal x; subnormals go through
 // frexp.
@@ -570,7 +572,7 @@ constexpr int OZ_IMAGIC = 0x4B400000;
 // dst + q qstep as bfloat16 (FINAL, the GEMM operand; |r| <= 129 is exact and
 // keeps the GEMM's 512-long FP32 chunks exact) or int8 (a later level's input;
 // representatives that wrap stay in the same class: only p = 256 reaches 128).
-template <bool FINAL, int LB, int NLB>
+template <bool FINAL, int LB, int NLB, bool F16 = false>
 __device__ __forceinline__ void emit_child(const long long *sv, const int2 *sterm, int t0, int t1, int nmod,
                                            char *dst, int64_t qstep, int valid) {
     // LB-bit limbs, NLB of them (|S'| < 2^(LB NLB), host-checked); the
@@ -608,14 +610,22 @@ __device__ __forceinline__ void emit_child(const long long *sv, const int2 *ster
         }
         char *out = dst + q * qstep;
         if (FINAL) {
+            // small integers: bfloat16 is the top half of their FP32 bits; half
+            // precision by conversion (exact below 2^11)
             uint2 pk;
-            pk.x = __byte_perm(__float_as_uint(r[0]), __float_as_uint(r[1]), 0x7632);
-            pk.y = __byte_perm(__float_as_uint(r[2]), __float_as_uint(r[3]), 0x7632);
+            if (F16) {
+                const __half2 h01 = __floats2half2_rn(r[0], r[1]), h23 = __floats2half2_rn(r[2], r[3]);
+                pk.x = *reinterpret_cast<const unsigned *>(&h01);
+                pk.y = *reinterpret_cast<const unsigned *>(&h23);
+            } else {
+                pk.x = __byte_perm(__float_as_uint(r[0]), __float_as_uint(r[1]), 0x7632);
+                pk.y = __byte_perm(__float_as_uint(r[2]), __float_as_uint(r[3]), 0x7632);
+            }
             if (valid == 4) {
                 *reinterpret_cast<uint2 *>(out) = pk;
             } else {
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&pk);
-                for (int e = 0; e < valid; ++e) reinterpret_cast<__nv_bfloat16 *>(out)[e] = h[e];
+                const unsigned short *h = reinterpret_cast<const unsigned short *>(&pk);
+                for (int e = 0; e < valid; ++e) reinterpret_cast<unsigned short *>(out)[e] = h[e];
             }
         } else {
             unsigned word = 0;
@@ -699,7 +709,7 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
 // blocks through shared memory (dynamic: NB x 32 x 33 int64, then reused as
 // [NB][4][256]); thread: one n and 4 consecutive k.  grid (ceil(out_ld / 32),
 // ceil(ncols / 32)), 256 threads.
-template <int NB, bool FINAL, int LC>
+template <int NB, bool FINAL, int LC, bool F16 = false>
 __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_t ldb, const int *eb, int64_t krows,
                                                          int64_t ncols, int gridN, int R, int nmod, const int *ptr,
                                                          const int *code, const int *icoef, void *out,
@@ -741,7 +751,8 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
     char *dst = (char *)out + (n * out_ld + k) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
     for (int o = 0; o < R; ++o, dst += ostep)
-        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
+        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N, F16>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep,
+                                                                valid);
 }
 
 // ---------------------------------------------------------------------
@@ -1185,40 +1196,110 @@ cudaError_t make_map3d(CUtensorMap *m, void *ptr, int64_t kpad, int64_t rows, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// A 3-D tiled map of any 1- or 2-byte element type (x innermost, in
+// elements), with the given swizzle and box.
+cudaError_t make_map3d_typed(CUtensorMap *m, CUtensorMapDataType dt, int esize, void *ptr, int64_t x,
+                             int64_t y, int64_t z, int box_x, int box_y, CUtensorMapSwizzle sw) {
+    EncodeFn enc;
+    cudaError_t e = encode_fn(&enc);
+    if (e != cudaSuccess) return e;
+    cuuint64_t gdim[3] = {(cuuint64_t)x, (cuuint64_t)y, (cuuint64_t)z};
+    cuuint64_t gstr[2] = {(cuuint64_t)(x * esize), (cuuint64_t)(x * y * esize)};
+    cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = enc(m, dt, 3, ptr, gdim, gstr, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 // Row pitch of the product residues Z: n rounded up to 16 bytes, so the drain
 // always stores whole 16-byte chunks.
 int64_t z_pitch(int64_t n) { return (n + 15) / 16 * 16; }
 
-// One persistent launch over all tiles of all planes; N = 256 tiles when the
-// planes are at least 256 wide.  A band: the rows [r0, r0 + m) of planes of
-// plane_m rows (S: plane_m x kpad per plane); the band's products go to Z as
-// planes of m rows (the caller points Z at the band's own region).
+// One product's residue GEMM (a group of one).  A band: the rows [r0, r0 + m)
+// of planes of plane_m rows (S: plane_m x kpad per plane); the band's
+// products go to Z as planes of m rows (the caller points Z at the band's own
+// region).
 cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64_t m, int64_t n,
                                 int64_t kpad, int64_t planes, int nmod, int *err, cudaStream_t s,
                                 int *launches, int64_t r0 = 0, int64_t plane_m = -1, bool narrow = false) {
+    RgDesc d{ra, rb, Z, m, n, kpad, planes, nmod, r0, plane_m < 0 ? m : plane_m};
+    return launch_residue_gemm_group(&d, 1, err, s, launches, narrow);
+}
+
+// The residue GEMM with S' formed on chip (residue_gemm_fa): ra8 holds the
+// int8 residues of A' ([q][m'][k']), rb the fp16 T'^T planes (leaves x nmod
+// planes of nL x kpad); the leaves' terms come from the host copy of U.
+cudaError_t launch_residue_gemm_fa(const ResPlan &rp, const int8_t *ra8, int64_t mp, int64_t kp, const void *rb,
+                                   int8_t *Z, int64_t mL, int64_t kL, int64_t nL, int64_t kpad, int nmod, int *err,
+                                   cudaStream_t s, int *launches) {
     cudaError_t e;
-    if ((e = configure_residue_gemm()) != cudaSuccess) return e;
-    if (plane_m < 0) plane_m = m;
-    const bool wide = n >= 256 && !narrow;
-    const int bn = wide ? 256 : 128;
-    CUtensorMap ta, tb;
-    // kpad is a multiple of 64, so the band's first row starts 16-byte aligned
-    if ((e = make_map3d(&ta, (void *)((const char *)ra + r0 * kpad * 2), kpad, m, planes, OZ_BM, plane_m)) !=
-        cudaSuccess)
+    static bool configured[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 64 && !configured[dev]) {
+        if ((e = cudaFuncSetAttribute(residue_gemm_fa, cudaFuncAttributeMaxDynamicSharedMemorySize, fa_smem())) !=
+            cudaSuccess)
+            return e;
+        configured[dev] = true;
+    }
+    FaParams P;   // built on the host, passed to the kernel by value
+    std::memset(&P, 0, sizeof(P));
+    const int R = rp.L ? rp.R : 1, MK = rp.L ? rp.M * rp.K : 1, gK = rp.L ? rp.K : 1;
+    for (int r = 0; r < R; ++r) {
+        int nt = 0, a[2] = {0, 0}, b[2] = {0, 0};
+        double c[2] = {1.0, 0.0};
+        for (int i = 0; i < MK; ++i) {
+            const double cf = rp.L ? rp.hU[(size_t)i * R + r] : 1.0;
+            if (cf == 0.0) continue;
+            if (nt >= FA_TMAX) return cudaErrorInvalidValue;
+            a[nt] = i / gK;
+            b[nt] = i % gK;
+            c[nt] = cf;
+            ++nt;
+        }
+        int kind;
+        if (nt == 1) {
+            kind = c[0] == 1.0 ? FA_P : c[0] == -1.0 ? FA_N : c[0] == 2.0 ? FA_P2 : c[0] == -2.0 ? FA_N2 : -1;
+        } else if (nt == 2) {
+            if (c[0] == -1.0 && c[1] == 1.0) {   // b - a: the positive term first
+                std::swap(a[0], a[1]);
+                std::swap(b[0], b[1]);
+                std::swap(c[0], c[1]);
+            }
+            kind = (c[0] == 1.0 && c[1] == 1.0) ? FA_PP : (c[0] == 1.0 && c[1] == -1.0) ? FA_PN
+                   : (c[0] == -1.0 && c[1] == -1.0) ? FA_NN : -1;
+        } else {
+            kind = -1;
+        }
+        if (kind < 0) return cudaErrorInvalidValue;
+        P.t.n[r] = nt;
+        P.t.kind[r] = kind;
+        for (int t = 0; t < nt; ++t) {
+            P.t.a[r][t] = a[t];
+            P.t.b[r][t] = b[t];
+        }
+    }
+    const int64_t planes = int64_t(R) * nmod;
+    if ((e = make_map3d_typed(&P.tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, (void *)ra8, kp, mp, nmod, FA_BK, FA_BM,
+                              CU_TENSOR_MAP_SWIZZLE_64B)) != cudaSuccess)
         return e;
-    if ((e = make_map3d(&tb, (void *)rb, kpad, n, planes, bn, n)) != cudaSuccess) return e;
-    const int64_t tn = (n + bn - 1) / bn, tmb = (m + OZ_BM - 1) / OZ_BM;
-    const int64_t tiles = tn * tmb * planes;
-    const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
+    if ((e = make_map3d_typed(&P.tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void *)rb, kpad, nL, planes, FA_BK,
+                              FA_BN, CU_TENSOR_MAP_SWIZZLE_128B)) != cudaSuccess)
+        return e;
+    P.Z = Z;
+    P.m = mL;
+    P.ldz = z_pitch(nL);
+    P.mL = mL;
+    P.kL = kL;
+    P.kblocks = int(kpad / FA_BK);
+    P.nmod = nmod;
+    P.tiles_m = int((mL + FA_BM - 1) / FA_BM);
+    P.tiles_n = int((nL + FA_BN - 1) / FA_BN);
+    P.tiles_total = (int64_t)P.tiles_m * P.tiles_n * planes;
+    const unsigned ctas = (unsigned)std::min<int64_t>(P.tiles_total, num_sms());
     cudaEvent_t t0 = timing_mark(s);
-    const int64_t ldz = z_pitch(n);
-    const unsigned long long wns = wait_limit_ns();
-    if (wide)
-        residue_gemm<256><<<ctas, oz_threads<256>(), oz_smem<256>(), s>>>(
-            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err, wns, 0);
-    else
-        residue_gemm<128><<<ctas, oz_threads<128>(), oz_smem<128>(), s>>>(
-            ta, tb, Z, m, n, ldz, int(kpad / OZ_BK), nmod, int(tmb), int(tn), tiles, err, wns, 0);
+    residue_gemm_fa<<<ctas, FA_THREADS, fa_smem(), s>>>(P, err, wait_limit_ns());
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
@@ -1226,6 +1307,56 @@ cudaError_t launch_residue_gemm(const void *ra, const void *rb, int8_t *Z, int64
 }
 
 }  // namespace
+
+// One persistent launch over all tiles of all planes of every problem of a
+// group; N = 256 tiles when every problem's planes are at least 256 wide (and
+// narrow tiles were not asked for).
+cudaError_t launch_residue_gemm_group(const RgDesc *d, int count, int *err, cudaStream_t s, int *launches,
+                                      bool narrow) {
+    cudaError_t e;
+    if (count < 1 || count > RG_MAX) return cudaErrorInvalidValue;
+    if ((e = configure_residue_gemm()) != cudaSuccess) return e;
+    bool wide = !narrow;
+    for (int i = 0; i < count; ++i) wide = wide && d[i].n >= 256;
+    const int bn = wide ? 256 : 128;
+    RgGroup g;
+    std::memset(&g, 0, sizeof(g));
+    int64_t tiles = 0;
+    for (int i = 0; i < count; ++i) {
+        const RgDesc &q = d[i];
+        // kpad is a multiple of 64, so the band's first row starts 16-byte aligned
+        if ((e = make_map3d(&g.tmA[i], (void *)((const char *)q.ra + q.r0 * q.kpad * 2), q.kpad, q.m, q.planes,
+                            OZ_BM, q.plane_m)) != cudaSuccess)
+            return e;
+        if ((e = make_map3d(&g.tmB[i], (void *)q.rb, q.kpad, q.n, q.planes, bn, q.n)) != cudaSuccess) return e;
+        RgProblem &P = g.pr[i];
+        P.Z = q.Z;
+        P.m = q.m;
+        P.ldz = z_pitch(q.n);
+        P.kblocks = int(q.kpad / OZ_BK);
+        P.nmod = q.nmod;
+        P.tiles_m = int((q.m + OZ_BM - 1) / OZ_BM);
+        P.tiles_n = int((q.n + bn - 1) / bn);
+        P.tile_base = tiles;
+        tiles += (int64_t)P.tiles_m * P.tiles_n * q.planes;
+    }
+    g.count = count;
+    g.tiles_total = tiles;
+    if (tiles == 0) return cudaSuccess;
+    const unsigned ctas = (unsigned)std::min<int64_t>(tiles, num_sms());
+    cudaEvent_t t0 = timing_mark(s);
+    const unsigned long long wns = wait_limit_ns();
+    if (wide)
+        residue_gemm<256><<<ctas, oz_threads<256>(), oz_smem<256>(), s>>>(g, err, wns, 0);
+    else
+        residue_gemm<128><<<ctas, oz_threads<128>(), oz_smem<128>(), s>>>(g, err, wns, 0);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (t0 && !timing_mark(s)) timing_unmark();
+    return cudaSuccess;
+}
+
+cudaError_t device_error_flag(int **out) { return cudaGetSymbolAddress((void **)out, g_device_error); }
 
 cudaError_t read_device_error(int *flag, bool clear) {
     cudaError_t e = cudaDeviceSynchronize();
@@ -1251,11 +1382,14 @@ cudaError_t residue_gemm_timeout_probe(unsigned long long limit_ns, cudaStream_t
     const size_t a_bytes = 128 * 64 * 2, b_bytes = 256 * 64 * 2, z_bytes = 128 * 256;
     if ((e = cudaMalloc(&buf, a_bytes + b_bytes + z_bytes)) != cudaSuccess) return e;
     char *c = (char *)buf;
-    CUtensorMap ta, tb;
-    if ((e = make_map3d(&ta, c, 64, 128, 1, OZ_BM, 128)) == cudaSuccess &&
-        (e = make_map3d(&tb, c + a_bytes, 64, 256, 1, 256, 256)) == cudaSuccess) {
-        residue_gemm<256><<<1, oz_threads<256>(), oz_smem<256>(), s>>>(
-            ta, tb, (int8_t *)(c + a_bytes + b_bytes), 128, 256, 256, 1, 1, 1, 1, 1, err, limit_ns, 1);
+    RgGroup g;
+    std::memset(&g, 0, sizeof(g));
+    if ((e = make_map3d(&g.tmA[0], c, 64, 128, 1, OZ_BM, 128)) == cudaSuccess &&
+        (e = make_map3d(&g.tmB[0], c + a_bytes, 64, 256, 1, 256, 256)) == cudaSuccess) {
+        g.pr[0] = RgProblem{(int8_t *)(c + a_bytes + b_bytes), 128, 256, 0, 1, 1, 1, 1};
+        g.count = 1;
+        g.tiles_total = 1;
+        residue_gemm<256><<<1, oz_threads<256>(), oz_smem<256>(), s>>>(g, err, limit_ns, 1);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }
@@ -1315,8 +1449,53 @@ static bool first_level_fused(const ResPlan &rp, int nmod, int64_t kp) {
     return rp.L == 0 || (fused_nb(rp.M * rp.K) && fused_nb(rp.K * rp.N));
 }
 
+// The S side formed inside the residue GEMM (residue_gemm_fa): at most one
+// level, integer coefficients with at most two terms and sum |c| <= 2 per
+// leaf (|S'| <= 256), k blocks aligned for TMA (16 bytes) and at most 32768
+// long, and the plan asked for it.  Then the workspace holds the int8 residues of A' instead of the S'
+// operand planes, and T'^T planes in fp16.
+static bool fused_a(const ResPlan &rp, int64_t mp, int64_t kp, int nmod) {
+    if (!rp.fused_s || rp.L > 1 || !rp.hU || mp <= 0) return false;
+    const int MK = rp.L ? rp.M * rp.K : 1, R = rp.L ? rp.R : 1;
+    if (R > FA_MAX_LEAVES) return false;
+    const int64_t kL = kp / (rp.L ? rp.K : 1);
+    if (kL % 16 || kp % 16 || kp > (int64_t(1) << 31) - 64 || mp > (int64_t(1) << 31) - 256) return false;
+    // |S'| <= p - 1 and |T'| <= p / 2: the int32 drain sum k_L p^2 / 2 stays
+    // below the p 2^22 shift of the final reduction for k_L <= 2^23 / 256
+    if (kL > 32768) return false;
+    if (!first_level_fused(rp, nmod, kp)) return false;
+    for (int r = 0; r < R && rp.L; ++r) {
+        int nt = 0;
+        double sum = 0;
+        for (int i = 0; i < MK; ++i) {
+            const double c = rp.hU[(size_t)i * R + r];
+            if (c == 0.0) continue;
+            ++nt;
+            sum += std::fabs(c);
+        }
+        if (nt < 1 || nt > FA_TMAX || sum > 2.0) return false;
+    }
+    return true;
+}
+
 static ResLayout res_layout(const ResPlan &rp, int64_t mp, int64_t kp, int64_t np, int nmod) {
     ResLayout w;
+    if (fused_a(rp, mp, kp, nmod)) {
+        // exponents, int8 residues of A' ([q][m'][k']), T'^T fp16 planes, products
+        auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
+        const int64_t R = rp.L ? rp.R : 1, ml = mp / (rp.L ? rp.M : 1), kl = kp / (rp.L ? rp.K : 1),
+                      nl = np / (rp.L ? rp.N : 1);
+        const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
+        w.ea = take(size_t(mp) * 4);
+        w.eb = take(size_t(np) * 4);
+        w.la.push_back(take(size_t(nmod) * mp * kp));
+        w.lb.push_back(take(size_t(R) * nmod * nl * kpad * 2));
+        w.zres = take(size_t(R) * nmod * ml * z_pitch(nl));
+        w.total = off;
+        return w;
+    }
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = al(off + bytes); return o; };
@@ -1378,14 +1557,14 @@ static cudaError_t launch_split_form_rows(int nb, const double *A, int64_t lda, 
     return cudaGetLastError();
 }
 
-template <bool FINAL, int LC>
+template <bool FINAL, int LC, bool F16 = false>
 static cudaError_t launch_split_form_cols_t(int nb, const double *B, int64_t ldb, const int *eb, int64_t krows,
                                             int64_t ncols, int gridN, int R, int nmod, const int *ptr,
                                             const int *code, const int *icoef, void *out, int64_t out_ld,
                                             cudaStream_t s) {
     const dim3 grid((unsigned)((out_ld + 31) / 32), (unsigned)((ncols + 31) / 32));
     const size_t smem = size_t(nb) * 32 * 33 * 8;   // >= nb * 4 * 256 * 8 (reused after the transpose)
-#define FMM_SFC(NB) split_form_cols_t<NB, FINAL, LC><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
+#define FMM_SFC(NB) split_form_cols_t<NB, FINAL, LC, F16><<<grid, 256, smem, s>>>(B, ldb, eb, krows, ncols, gridN, R, nmod, ptr, code, icoef, out, out_ld)
     switch (nb) {
         case 1: FMM_SFC(1); break;
         case 4: FMM_SFC(4); break;
@@ -1412,9 +1591,14 @@ static cudaError_t configure_split_form() {
     if ((e = cudaFuncSetAttribute(split_form_rows<NB, F, LC>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
                                   NB * 4 * 256 * 8)) != cudaSuccess)                                           \
         return e;
+#define FMM_CFG16(NB, LC)                                                                                    \
+    if ((e = cudaFuncSetAttribute(split_form_cols_t<NB, true, LC, true>,                                     \
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, NB * 32 * 33 * 8)) != cudaSuccess) \
+        return e;
 #define FMM_CFG(NB) FMM_CFG1(NB, true, 0) FMM_CFG1(NB, false, 0) FMM_CFG1(NB, true, 1) FMM_CFG1(NB, false, 1) \
-                    FMM_CFG1(NB, true, 2) FMM_CFG1(NB, false, 2)
+                    FMM_CFG1(NB, true, 2) FMM_CFG1(NB, false, 2) FMM_CFG16(NB, 0) FMM_CFG16(NB, 1) FMM_CFG16(NB, 2)
     FMM_CFG(1) FMM_CFG(4) FMM_CFG(6) FMM_CFG(8) FMM_CFG(9)
+#undef FMM_CFG16
 #undef FMM_CFG1
 #undef FMM_CFG
     configured[dev] = true;
@@ -1426,7 +1610,13 @@ static cudaError_t configure_split_form() {
 // fused into the top level of the W combination.
 cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const double *B, int64_t ldb,
                        double *C, int64_t ldc, int64_t mp, int64_t kp, int64_t np, int nmod,
-                       int accumulate, void *ws, cudaStream_t s, int *launches, const HostPipe *pipe) {
+                       int accumulate, void *ws, cudaStream_t s, int *launches, const HostPipe *pipe,
+                       GemmDefer *defer) {
+    // defer (grouped products): phase 0 enqueues everything before the
+    // residue GEMM and describes that GEMM in defer->gemm; phase 1 enqueues
+    // everything after it
+    if (defer && (pipe || defer->phase < 0 || defer->phase > 1)) return cudaErrorInvalidValue;
+    const bool pre = !defer || defer->phase == 0;
     cudaError_t e = ensure_tables(nmod);
     if (e != cudaSuccess) return e;
     if ((e = configure_split_form()) != cudaSuccess) return e;
@@ -1438,6 +1628,9 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     if ((e = cudaGetSymbolAddress((void **)&id_coef, g_ident_coef)) != cudaSuccess) return e;
     const ResLayout w = res_layout(rp, mp, kp, np, nmod);
     const bool fused = first_level_fused(rp, nmod, kp);
+    // S' formed inside the GEMM (not with grouped launches: those take the
+    // ordinary operand planes)
+    const bool fa = !defer && fused_a(rp, mp, kp, nmod);
     char *b = (char *)ws;
     int *ea = (int *)(b + w.ea), *eb = (int *)(b + w.eb);
     const int beta = ozaki_beta(nmod, kp);
@@ -1519,7 +1712,37 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
                                            out_ld1, s, ar0, anr))
     // which 0: the A side, child rows [ar0, ar0 + anr); 1: the B side
     int64_t ar0 = 0, anr = ml1;
+    // with S' formed in the GEMM: the A side is the int8 residues of A' itself
+    // (the identity "level", one launch per first-level block row of the
+    // band), the B side the first level in fp16
+    int lc_id = 0;
+    {
+        const int bits = beta + 1;   // |A'| <= 2^beta
+        lc_id = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
+    }
+    auto fa_split = [&](int which) -> cudaError_t {
+        cudaError_t se = cudaSuccess;
+        if (which) {
+#define FMM_SFC16(LC) launch_split_form_cols_t<true, LC, true>(nbB, B, ldb, eb, kl1, nl1, gN, R1, nmod, vp, vc, vi, \
+                                                                 b + w.lb[0], out_ld1, s)
+            se = lc == 0 ? FMM_SFC16(0) : lc == 1 ? FMM_SFC16(1) : FMM_SFC16(2);
+#undef FMM_SFC16
+            ++*launches;
+            return se;
+        }
+        const int gM1 = rp.L ? rp.M : 1;
+        for (int a = 0; a < gM1 && se == cudaSuccess; ++a) {
+            const int64_t r0 = a * ml1 + ar0;
+#define FMM_SFR8(LC) launch_split_form_rows<false, LC>(1, A, lda, ea, mp, kp, 1, 1, nmod, id_ptr, id_code, id_coef, \
+                                                         b + w.la[0], kp, s, r0, anr)
+            se = lc_id == 0 ? FMM_SFR8(0) : lc_id == 1 ? FMM_SFR8(1) : FMM_SFR8(2);
+#undef FMM_SFR8
+            ++*launches;
+        }
+        return se;
+    };
     auto fused_split = [&](int which) -> cudaError_t {
+        if (fa) return fa_split(which);
         cudaError_t se;
         if (last1)
             se = lc == 0 ? FMM_SPLIT(which, true, 0) : lc == 1 ? FMM_SPLIT(which, true, 1) : FMM_SPLIT(which, true, 2);
@@ -1552,7 +1775,9 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         if ((be = check()) != cudaSuccess) return be;
         return form(rb0, 1, np, kp, nl1, kl1, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last1, out_ld1);
     };
-    if (pipe && pipe->a_bands > 0) {
+    if (!pre) {
+        // phase 1: the operands were formed in phase 0
+    } else if (pipe && pipe->a_bands > 0) {
         // the host copies B first, then A in bands of child rows [ml1 j / a_bands,
         // ml1 (j + 1) / a_bands) of every block row, each with an event: the B
         // side runs while A arrives, and each A band is formed once it is in
@@ -1586,12 +1811,12 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         const int64_t ml = pm / rp.M, kl = pk / rp.K, nl = pn / rp.N;
         const int64_t kpad = (kl + OZ_BK - 1) / OZ_BK * OZ_BK;
         const bool last = l == rp.L;
-        if ((e = form((const int8_t *)(b + w.la[l - 2]), parents, pm, pk, ml, kl, rp.u_ptr, rp.u_code,
-                      rp.u_icoef, b + w.la[l - 1], last, last ? kpad : kl)) != cudaSuccess)
+        if (pre && (e = form((const int8_t *)(b + w.la[l - 2]), parents, pm, pk, ml, kl, rp.u_ptr, rp.u_code,
+                             rp.u_icoef, b + w.la[l - 1], last, last ? kpad : kl)) != cudaSuccess)
             return e;
         // B^T: parent n x k, child nl x kl, block codes with rows and columns swapped
-        if ((e = form((const int8_t *)(b + w.lb[l - 2]), parents, pn, pk, nl, kl, rp.v_ptr, rp.vt_code,
-                      rp.v_icoef, b + w.lb[l - 1], last, last ? kpad : kl)) != cudaSuccess)
+        if (pre && (e = form((const int8_t *)(b + w.lb[l - 2]), parents, pn, pk, nl, kl, rp.v_ptr, rp.vt_code,
+                             rp.v_icoef, b + w.lb[l - 1], last, last ? kpad : kl)) != cudaSuccess)
             return e;
         parents *= rp.R;
         pm = ml; pk = kl; pn = nl;
@@ -1601,6 +1826,11 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int64_t kpadL = (kL + OZ_BK - 1) / OZ_BK * OZ_BK;
     const int64_t planes = leaves * nmod;
     int8_t *Z = (int8_t *)(b + w.zres);
+    if (defer && defer->phase == 0) {
+        defer->gemm = RgDesc{b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, planes, nmod, 0, mL};
+        defer->narrow = rp.tile == FMM_TILE_128x128;
+        return cudaSuccess;
+    }
 
     // top level of W fused with the CRT, straight into C: the child rows
     // [r0, r0 + nr) of every block, from z (the first of them in plane 0,
@@ -1647,7 +1877,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     // in row bands (each band of S against all of T; the band's products form
     // a region of their own in Z), each combined and handed over while the
     // next band is multiplied
-    const int gb = (pipe && pipe->band_done && rp.L <= 1)
+    const int gb = (pipe && pipe->band_done && rp.L <= 1 && !fa)
                        ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(pipe->gemm_bands, bands), mL))
                        : 1;
     if (gb > 1) {
@@ -1668,9 +1898,15 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         return cudaSuccess;
     }
 
-    if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, planes, nmod,
-                                 err, s, launches, 0, -1, rp.tile == FMM_TILE_128x128)) != cudaSuccess)
+    if (fa) {
+        if ((e = launch_residue_gemm_fa(rp, (const int8_t *)(b + w.la[0]), mp, kp, b + w.lb[0], Z, mL, kL, nL, kpadL,
+                                        nmod, err, s, launches)) != cudaSuccess)
+            return e;
+    } else if (!defer && (e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Z, mL, nL, kpadL, planes, nmod,
+                                                  err, s, launches, 0, -1, rp.tile == FMM_TILE_128x128)) !=
+               cudaSuccess) {
         return e;
+    }
     // W levels L..2 on residues, down to the level-1 products
     int64_t cm = mL, cn = nL, cld = z_pitch(nL);
     const int8_t *child = Z;

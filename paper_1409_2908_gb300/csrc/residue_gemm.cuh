@@ -6,7 +6,8 @@
 // traffic can be tied to this exact source.
 #pragma once
 
-// Z[z][row][col] (int8 balanced residues), z = leaf * nmod + modulus index.
+// Z[z][row][col] (int8 balanced residues), z = leaf * nmod + modulus index,
+// for each problem of the launch.
 // Persistent: CTA c handles tiles c, c + gridDim.x, ...; the load, MMA and
 // drain roles walk the same tile sequence, so stage and TMEM-buffer phases
 // continue across tiles and the tensor core never waits for a tile's final
@@ -33,6 +34,33 @@ __device__ __forceinline__ void tile_coords(int64_t tile, int64_t per_plane, int
     tm = tm0 + within % gsz;
 }
 
+// A launch covers a group of up to RG_MAX independent problems (one for an
+// ordinary product): each has its own operand tensor maps, product planes and
+// sizes; the persistent tile sequence runs through problem 0's tiles, then
+// problem 1's, and so on (tile_base: the first tile of each).
+constexpr int RG_MAX = RG_MAX_PROBLEMS;
+struct RgProblem {
+    int8_t *Z;                 // product residues, planes of m x ldz
+    int64_t m, ldz;
+    int64_t tile_base;         // first tile of this problem in the launch
+    int kblocks, nmod, tiles_m, tiles_n;
+};
+struct RgGroup {
+    CUtensorMap tmA[RG_MAX];   // S' planes (K-major, bf16)
+    CUtensorMap tmB[RG_MAX];   // T'^T planes
+    RgProblem pr[RG_MAX];
+    int64_t tiles_total;
+    int count;
+};
+
+// Problem of a tile of the launch (the problems' tile ranges are consecutive).
+__device__ __forceinline__ int rg_problem(const RgGroup &g, int64_t tile) {
+    int p = 0;
+#pragma unroll 1
+    while (p + 1 < g.count && tile >= g.pr[p + 1].tile_base) ++p;
+    return p;
+}
+
 template <int BN>
 struct OzCfg;
 template <>
@@ -50,9 +78,7 @@ constexpr int oz_smem() { return OzCfg<BN>::STAGES * (OZ_A_BYTES + BN * OZ_BK * 
 
 template <int BN>
 __global__ void __launch_bounds__(oz_threads<BN>(), 1)
-residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-             int8_t *Z, int64_t m, int64_t n, int64_t ldz, int kblocks, int nmod, int tiles_m, int tiles_n,
-             int64_t tiles_total, int *err, unsigned long long wait_ns, int dry) {
+residue_gemm(const __grid_constant__ RgGroup g, int *err, unsigned long long wait_ns, int dry) {
     constexpr int OZ_TBUF = OzCfg<BN>::TBUF, OZ_STAGES = OzCfg<BN>::STAGES;
     constexpr int DW = OzCfg<BN>::DRAIN_WARPS;
     constexpr int OZ_BN = BN, OZ_B_BYTES = BN * OZ_BK * 2, OZ_STAGE_BYTES = OZ_A_BYTES + OZ_B_BYTES;
@@ -65,7 +91,7 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint64_t *mdone = tempty + OZ_TBUF;   // the MMA thread's last commit
     uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int nchunks = (kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+    const int64_t tiles_total = g.tiles_total;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < OZ_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -82,32 +108,33 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const int64_t per_plane = (int64_t)tiles_m * tiles_n;
 
     if (warp == DW) {
         if (lane == 0 && !dry) {
-            int64_t g = 0;   // global k-block counter: stage and phase
+            int64_t gk = 0;   // global k-block counter: stage and phase
             bool ok = true;
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                const int p = rg_problem(g, tile);
+                const RgProblem &P = g.pr[p];
                 int z, tm, tn;
-                tile_coords(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
-                for (int kb = 0; kb < kblocks; ++kb, ++g) {
-                    const int s = int(g % OZ_STAGES);
-                    if (g >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((g / OZ_STAGES) - 1) & 1), wait_ns)) {
+                tile_coords(tile - P.tile_base, (int64_t)P.tiles_m * P.tiles_n, P.tiles_m, P.tiles_n, z, tm, tn);
+                for (int kb = 0; kb < P.kblocks; ++kb, ++gk) {
+                    const int s = int(gk % OZ_STAGES);
+                    if (gk >= OZ_STAGES && !mbar_wait(&empty[s], uint32_t(((gk / OZ_STAGES) - 1) & 1), wait_ns)) {
                         atomicExch(err, 1);
                         ok = false;
                         break;
                     }
                     unsigned char *sa = smem + s * OZ_STAGE_BYTES, *sb = sa + OZ_A_BYTES;
                     mbar_expect_tx(&full[s], OZ_STAGE_BYTES);
-                    tma_load_3d(sa, &tmA, kb * OZ_BK, tm * OZ_BM, z, &full[s]);
-                    tma_load_3d(sb, &tmB, kb * OZ_BK, tn * OZ_BN, z, &full[s]);
+                    tma_load_3d(sa, &g.tmA[p], kb * OZ_BK, tm * OZ_BM, z, &full[s]);
+                    tma_load_3d(sb, &g.tmB[p], kb * OZ_BK, tn * OZ_BN, z, &full[s]);
                 }
             }
             // no bulk copy of this CTA may still be in flight when it exits:
             // wait for the last (at most OZ_STAGES) k-blocks issued to land
             // (normally consumed long ago; after a timeout elsewhere, bounded)
-            for (int64_t j = g > OZ_STAGES ? g - OZ_STAGES : 0; j < g; ++j)
+            for (int64_t j = gk > OZ_STAGES ? gk - OZ_STAGES : 0; j < gk; ++j)
                 if (!mbar_wait(&full[j % OZ_STAGES], uint32_t((j / OZ_STAGES) & 1), wait_ns)) atomicExch(err, 1);
         }
     } else if (warp == DW + 1) {
@@ -115,8 +142,10 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
                                    ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(OZ_BM >> 4) << 24);
             bool ok = true;
-            int64_t g = 0, cg = 0;   // global k-block and chunk counters
+            int64_t gk = 0, cg = 0;   // global k-block and chunk counters
             for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+                const int kblocks = g.pr[rg_problem(g, tile)].kblocks;
+                const int nchunks = (kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
                 int kb = 0;
                 for (int c = 0; c < nchunks && ok; ++c, ++cg) {
                     const int b = int(cg % OZ_TBUF);
@@ -127,9 +156,9 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t acc_tmem = tmem + (uint32_t)(b * OZ_BN);
                     const int kend = min(kblocks, (c + 1) * OZ_CHUNK_KB);
-                    for (int first = 1; kb < kend; ++kb, ++g, first = 0) {
-                        const int s = int(g % OZ_STAGES);
-                        if (!mbar_wait(&full[s], uint32_t((g / OZ_STAGES) & 1), wait_ns)) { ok = false; break; }
+                    for (int first = 1; kb < kend; ++kb, ++gk, first = 0) {
+                        const int s = int(gk % OZ_STAGES);
+                        if (!mbar_wait(&full[s], uint32_t((gk / OZ_STAGES) & 1), wait_ns)) { ok = false; break; }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t a0 = su32(smem + s * OZ_STAGE_BYTES), b0 = a0 + OZ_A_BYTES;
 #pragma unroll
@@ -153,10 +182,14 @@ residue_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         bool ok = true;
         int64_t cg = 0;
         for (int64_t tile = blockIdx.x; tile < tiles_total && ok; tile += gridDim.x) {
+            const RgProblem &P = g.pr[rg_problem(g, tile)];
             int z, tm, tn;
-            tile_coords(tile, per_plane, tiles_m, tiles_n, z, tm, tn);
-            const int q = z % nmod;
+            tile_coords(tile - P.tile_base, (int64_t)P.tiles_m * P.tiles_n, P.tiles_m, P.tiles_n, z, tm, tn);
+            const int q = z % P.nmod;
             const int p = c_mod[q];
+            const int nchunks = (P.kblocks + OZ_CHUNK_KB - 1) / OZ_CHUNK_KB;
+            const int64_t m = P.m, ldz = P.ldz;
+            int8_t *Z = P.Z;
             int acc[128];
 #pragma unroll
             for (int j = 0; j < 128; ++j) acc[j] = 0;

@@ -12,6 +12,11 @@ throughput.
     and slot (fixed operand buffers; capture runs on the slot's stream
     without a device-wide synchronisation); a shape's first occurrence runs
     directly.
+  * With group_shapes, admitted requests of DIFFERENT shapes whose plans are
+    emulated FP64 with at most one recursive level go out together as one
+    fmm_gemm_grouped call (up to max_group per call): their residue GEMMs run
+    as one grouped tensor-core launch, which fills the GPU where a single
+    small product cannot.  Shapes with a captured graph keep the graph path.
   * Groups on different streams overlap on the device; completion is polled
     with CUDA events.
 
@@ -73,23 +78,37 @@ class Stats:
     wall_s: float = 0.0
     flops: float = 0.0
     latencies: list = field(default_factory=list)
+    waits: list = field(default_factory=list)       # admission minus arrival (queueing)
+    services: list = field(default_factory=list)    # completion minus admission
+    max_waiting: int = 0                            # most requests arrived but not admitted
     graphs_captured: int = 0
     graph_replays: int = 0
     max_inflight: int = 0
+    grouped_calls: int = 0                          # fmm_gemm_grouped calls
+    grouped_requests: int = 0                       # requests they carried
 
     def summary(self):
         lat = np.array(self.latencies) * 1e3
+        wt = np.array(self.waits) * 1e3
+        sv = np.array(self.services) * 1e3
+
+        def pct(x, q):
+            return float(np.percentile(x, q)) if len(x) else None
         return {"requests": self.completed, "wall_s": self.wall_s,
                 "effective_tflops": self.flops / self.wall_s / 1e12 if self.wall_s else 0.0,
-                "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                "wait_p50_ms": pct(wt, 50), "wait_p99_ms": pct(wt, 99),
+                "service_p50_ms": pct(sv, 50), "service_p99_ms": pct(sv, 99),
+                "max_waiting": self.max_waiting,
                 "graphs_captured": self.graphs_captured, "graph_replays": self.graph_replays,
-                "max_inflight_groups": self.max_inflight}
+                "max_inflight_groups": self.max_inflight, "grouped_calls": self.grouped_calls,
+                "grouped_requests": self.grouped_requests,
+                "mean_group_size": (self.grouped_requests / self.grouped_calls) if self.grouped_calls else None}
 
 
 class Server:
     def __init__(self, tuner, memory_budget_bytes, slots=4, graph_cache_bytes=None, use_graphs=True,
-                 keep_results=True):
+                 keep_results=True, group_shapes=False):
         import torch
         self.tuner = tuner
         self.budget = int(memory_budget_bytes)
@@ -102,6 +121,8 @@ class Server:
         self._graph_bytes = 0
         self._seen = {}
         self._slot_ws = [None] * slots     # per-slot workspace, grown on demand
+        self._slot_wss = [[] for _ in range(slots)]   # per-slot workspaces of grouped calls
+        self.group_shapes = group_shapes
         self.used = 0
         self.stats = Stats()
 
@@ -174,6 +195,54 @@ class Server:
             self._slot_ws[slot] = ws
         return ws
 
+    @staticmethod
+    def _groupable(plan, shape, sms=152):
+        """Emulated products (at most one level) whose residue GEMM alone has
+        fewer tiles than the GPU has SMs: grouping several such products into
+        one launch fills the GPU; larger products run better on their own
+        streams, where one product's memory passes overlap another's GEMM."""
+        if plan.precision != "ozaki_bf16" or plan.levels > 1 or (plan.flags & fmm.FLAG_TC_FUSED_S):
+            return False
+        m, k, n = shape
+        M, K, N = (plan.dims if plan.levels else (1, 1, 1))
+        R = plan.rank if plan.levels else 1
+        mL, nL = m // M, n // N
+        tiles = R * (plan.moduli or 15) * -(-mL // 128) * -(-nL // (256 if nL >= 256 else 128))
+        return tiles < sms
+
+    def _workspaces(self, slot, sizes):
+        """One workspace per product of a grouped call on this slot (grown on
+        demand, allocated on the slot's stream like _workspace)."""
+        import torch
+        wss = self._slot_wss[slot]
+        out = []
+        for i, nb in enumerate(sizes):
+            if not nb:
+                out.append(None)
+                continue
+            while len(wss) <= i:
+                wss.append(None)
+            if wss[i] is None or wss[i].numel() < nb:
+                with torch.cuda.stream(self.streams[slot]):
+                    wss[i] = torch.empty(nb, dtype=torch.uint8, device="cuda")
+            out.append(wss[i])
+        return out
+
+    def _launch_grouped(self, reqs, plans, slot):
+        import torch
+        stream = self.streams[slot]
+        with torch.cuda.stream(stream):
+            Cs = [torch.empty((r.shape[0], r.shape[2]), dtype=torch.float64, device="cuda") for r in reqs]
+            wss = self._workspaces(slot, [p.workspace_size(*r.shape) for p, r in zip(plans, reqs)])
+            fmm.gemm_grouped(plans, [r.A for r in reqs], [r.B for r in reqs], Cs=Cs, workspaces=wss, stream=stream)
+            for r, C in zip(reqs, Cs):
+                r.C = C
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.stats.grouped_calls += 1
+        self.stats.grouped_requests += len(reqs)
+        return _Group(reqs, ev, stream, sum(self._bytes(p, *r.shape) for p, r in zip(plans, reqs)))
+
     def _launch(self, group_reqs, plan, slot):
         import torch
         stream = self.streams[slot]
@@ -219,6 +288,7 @@ class Server:
                 queue.append(r)
                 by_shape.setdefault(r.shape, deque()).append(r)
                 waiting += 1
+                self.stats.max_waiting = max(self.stats.max_waiting, waiting)
             # retire finished groups
             still = []
             for g in inflight:
@@ -229,6 +299,8 @@ class Server:
                         if not self.keep_results:
                             r.C = None
                         self.stats.latencies.append(done - r.arrival)
+                        self.stats.waits.append(r.t_admit - r.arrival)
+                        self.stats.services.append(done - r.t_admit)
                         self.stats.flops += r.flops
                         self.stats.completed += 1
                     self.used -= g.nbytes
@@ -245,18 +317,48 @@ class Server:
                 need = self._bytes(plan, *head.shape)
                 if self.used + need > self.budget and inflight:
                     break
-                same = by_shape[head.shape]
-                group = []
-                while same and len(group) < max_group and (not group or self.used + need * (len(group) + 1)
-                                                           <= self.budget):
-                    group.append(same.popleft())
-                if not same:
-                    del by_shape[head.shape]
-                for r in group:
-                    r.t_admit = now
-                waiting -= len(group)
-                slot = self.free_slots.popleft()
-                g = self._launch(group, plan, slot)
+                graphed = self.use_graphs and self._seen.get((id(plan), head.shape), 0) >= 1
+                if self.group_shapes and self._groupable(plan, head.shape) and not graphed:
+                    # requests of any shape, in arrival order, whose plans group
+                    group, plans, total = [], [], 0
+                    for r in queue:
+                        if len(group) >= max_group:
+                            break
+                        if r.t_admit >= 0:
+                            continue
+                        pr = self._plan(*r.shape)
+                        nb = self._bytes(pr, *r.shape)
+                        if not self._groupable(pr, r.shape) or (self.use_graphs and
+                                                                self._seen.get((id(pr), r.shape), 0) >= 1):
+                            continue
+                        if group and self.used + total + nb > self.budget:
+                            break
+                        group.append(r)
+                        plans.append(pr)
+                        total += nb
+                    for r, pr in zip(group, plans):
+                        r.t_admit = now
+                        by_shape[r.shape].remove(r)
+                        if not by_shape[r.shape]:
+                            del by_shape[r.shape]
+                        key = (id(pr), r.shape)
+                        self._seen[key] = self._seen.get(key, 0) + 1
+                    waiting -= len(group)
+                    slot = self.free_slots.popleft()
+                    g = self._launch_grouped(group, plans, slot)
+                else:
+                    same = by_shape[head.shape]
+                    group = []
+                    while same and len(group) < max_group and (not group or self.used + need * (len(group) + 1)
+                                                               <= self.budget):
+                        group.append(same.popleft())
+                    if not same:
+                        del by_shape[head.shape]
+                    for r in group:
+                        r.t_admit = now
+                    waiting -= len(group)
+                    slot = self.free_slots.popleft()
+                    g = self._launch(group, plan, slot)
                 self.used += g.nbytes
                 inflight.append(g)
                 self.stats.max_inflight = max(self.stats.max_inflight, len(inflight))

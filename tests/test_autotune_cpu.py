@@ -108,3 +108,13 @@ def test_fp64_tile_follows_leaf_size():
     assert big.tile == "128x128"
     small = [c for c in t.candidates(192, 4096, 192) if c.levels == 1 and c.algorithm == "strassen_222_7"][0]
     assert small.tile in ("96x96", "64x64", "32x32")
+
+
+@pytest.mark.parametrize("shape", [(8192, 8192, 8192), (16384, 2048, 2048), (300, 5000, 700), (256, 256, 8000)])
+@pytest.mark.parametrize("precs", [("fp64", "ozaki_bf16"), ("fp64",), ("tf32", "fp32", "ozaki_bf16")])
+def test_branch_and_bound_finds_the_model_optimum(shape, precs):
+    t = autotune.Autotuner(tol=1e-11 if "tf32" not in precs else 1e-3, precisions=precs, measure=False)
+    full = t.candidates(*shape)
+    for count in (1, 3):
+        got = t.best_candidates(*shape, count)
+        assert [c.model_ms for c in got] == [c.model_ms for c in full[:count]]

@@ -57,3 +57,15 @@ def test_narrow_tensor_tiles_same_result():
     torch.cuda.synchronize()
     assert np.array_equal(out[0], out[2])
     assert np.allclose(out[1], out[3], rtol=0, atol=1e-3 * np.abs(out[1]).max())
+
+
+def test_calibration_measures_this_gpu():
+    # the model's rates re-measured: the classical DFMA GEMM, the residue GEMM
+    # and the emulated passes, each within a factor two of the defaults
+    t = autotune.Autotuner(tol=1e-11, measure=False)
+    r = t.calibrate(size=2048, nmod=12)
+    assert 0.5 * autotune.FP64_TFLOPS < r["fp64_tflops"] < 2 * autotune.FP64_TFLOPS
+    assert 0.5 * autotune.TC_TFLOPS < r["tc_tflops"] < 2 * autotune.TC_TFLOPS
+    assert 0.25 < r["pass_scale"] < 4.0
+    c = t.choose(3000, 3000, 3000)
+    assert c.model_ms > 0

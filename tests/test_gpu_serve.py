@@ -13,18 +13,26 @@ from paper_1409_2908_gb300 import autotune, serve
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precisions", [("fp64",), ("ozaki_bf16",)])
+@pytest.mark.parametrize("precisions,group_shapes", [(("fp64",), False), (("ozaki_bf16",), False),
+                                                    (("ozaki_bf16",), True)])
 @pytest.mark.parametrize("use_graphs", [True, False])
-def test_results_same_alone_and_in_the_mix(precisions, use_graphs):
+def test_results_same_alone_and_in_the_mix(precisions, use_graphs, group_shapes):
     import torch
     tuner = autotune.Autotuner(tol=1e-11, precisions=precisions, measure=False)
-    reqs = serve.poisson_requests(18, rate_per_s=2000.0, lo=128, hi=700, seed=7)
+    # grouping across shapes takes the small products (whose residue GEMM
+    # underfills the GPU) that wait together: let them arrive at once
+    reqs = serve.poisson_requests(18, rate_per_s=1e6 if group_shapes else 2000.0, lo=128,
+                                  hi=400 if group_shapes else 700, seed=7)
     # repeat a few shapes so that graphs are replayed
     for i in range(6):
         r = reqs[i]
         reqs.append(serve.Request(100 + i, r.A.clone(), r.B.clone(), r.arrival + 0.002))
-    srv = serve.Server(tuner, memory_budget_bytes=1 << 30, slots=3, use_graphs=use_graphs)
+    srv = serve.Server(tuner, memory_budget_bytes=1 << 30, slots=3, use_graphs=use_graphs,
+                       group_shapes=group_shapes)
     stats = srv.run(reqs)
+    if group_shapes:
+        # requests of different shapes went out together in grouped calls
+        assert stats["grouped_calls"] >= 1 and stats["mean_group_size"] > 1
     torch.cuda.synchronize()
     assert stats["requests"] == len(reqs)
     assert stats["p50_ms"] is not None and stats["p99_ms"] >= stats["p50_ms"]
