@@ -145,6 +145,7 @@ def fp64_pass_bytes(name, levels, m, k, n):
 def roofline(p, info, m, k, n, leaf_avg, ms_step, region_s, clocks, args):
     """Roofline record of the dominant kernel of the timed plan: the leaf
     products (FP64 DFMA, TF32 or the emulated residue GEMM)."""
+    import paper_1409_2908_gb300 as fmm
     Lv = info["levels"]
     mL, kL, nL = m // info["M"] ** Lv, k // info["K"] ** Lv, n // info["N"] ** Lv
     common = {"leaf_ms_avg": leaf_avg, "leaf_share_of_step": leaf_avg / ms_step}
@@ -800,6 +801,8 @@ def main():
     # precision and accuracy (an emulated classical product with the same
     # moduli gives the same integers, hence the same error)
     best = fastest([r for r in results if r["levels"] >= 1 and meets(r, gate)])
+    if best is None and args.plan:
+        best = fastest(results)   # a plan named with --plan is timed as given
     if best is None:
         raise SystemExit("no fast-algorithm plan meets the accuracy gate for this workload")
     p = plans[best["plan"]]

@@ -165,15 +165,16 @@ def cases():
     return out
 
 
+MODULI = (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)
+_PRODUCTS = tuple(math.prod(MODULI[:n]) for n in range(len(MODULI) + 1))
+
+
 def beta_for(n, k):
-    """Width of the scaled integers with n moduli (the library's rule)."""
-    P = 1
-    for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
-        P *= p
-    beta = 62
-    while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
-        beta -= 1
-    return beta
+    """Width of the scaled integers with n moduli (the library's rule: the
+    largest beta <= 62 with k 2^(2 beta + 1) < P).  k 2^e < P holds exactly
+    when 2^e <= (P - 1) div k, so 2 beta + 1 <= bitlength((P - 1) div k) - 1."""
+    e = ((_PRODUCTS[n] - 1) // int(k)).bit_length() - 1
+    return max(0, min(62, (e - 1) // 2))
 
 
 @functools.lru_cache(maxsize=4096)
@@ -183,13 +184,7 @@ def moduli_for(tol, k):
     operands are rounded to nearest) meets the relative tolerance: the prior
     that measured trials then correct."""
     for n in range(6, 17):
-        P = 1
-        for p in (256, 255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211, 199, 197, 193)[:n]:
-            P *= p
-        beta = 62
-        while beta > 0 and k * 2 ** (2 * beta + 1) >= P:
-            beta -= 1
-        if 2 * 2.0 ** (-beta) <= tol:
+        if 2 * 2.0 ** (-beta_for(n, k)) <= tol:
             return n
     return None
 
@@ -323,24 +318,148 @@ class Autotuner:
         out.sort(key=lambda c: c.model_ms)
         return out
 
+    def _levels(self):
+        """The recursive cases as arrays (computed once): for each (case, L),
+        L >= 1, in increasing rho^L (rho = R / (M K N), the fraction of the
+        classical flops one level keeps): rho^L, M^L, K^L, N^L, R^L and the
+        coefficients of the emulated passes' model time (seconds before the
+        pass scale) as a + b nmod per unit of the block areas mp kp, kp np and
+        mp np, plus a constant (the launches)."""
+        if getattr(self, "_level_tab", None) is None:
+            import numpy as np
+            rows, info = [], []
+            for name, perm, base, wt in self._cases():
+                M, K, N, R = base
+                for L in range(1, self.max_levels + 1):
+                    if R ** L > 20000:
+                        break
+                    rows.append([(R / (M * K * N)) ** L, M ** L, K ** L, N ** L, R ** L]
+                                + self._pass_coeffs(M, K, N, R, L, wt))
+                    info.append((name, perm, base, L, wt))
+            order = sorted(range(len(rows)), key=lambda i: rows[i][0])
+            self._level_tab = (np.array([rows[i] for i in order], dtype=np.float64).reshape(-1, 12),
+                               [info[i] for i in order])
+            # per depth L: the least rho^L and the least of each pass
+            # coefficient over the cases (a bound for every case of that depth)
+            self._level_min = {}
+            for L in range(1, self.max_levels + 1):
+                sel = [r for r, inf in zip(rows, info) if inf[3] == L]
+                if sel:
+                    self._level_min[L] = [min(r[0] for r in sel)] + [min(r[5 + j] for r in sel) for j in range(7)]
+        return self._level_tab
+
+    def _recursion_excluded(self, m, k, n, precs, rate, work, nmod, limit):
+        """True when no recursive candidate can beat `limit` (ms), by a bound
+        over all cases of each depth at once: rho^L is at least its least
+        value at that depth, the leaves and fringe cost at least
+        2 rho^L m k n min(work / leaf rate, 1 / FP64 rate), and an admissible
+        case (leaves at least 64 on a side) peels at most 1/64 of each
+        dimension, so every block area is at least (63/64)^2 of the full one
+        and the emulated passes at least the least coefficients times those
+        areas."""
+        self._levels()
+        flops = 2.0 * m * k * n
+        q2 = (63.0 / 64.0) ** 2
+        for L, (rho, amk, bmk, akn, bkn, amn, bmn, c) in self._level_min.items():
+            for prec in precs:
+                lb = rho * flops * min(work[prec] / (rate[prec] * 1e12), 1.0 / (self.fp64_tflops * 1e12))
+                if prec == "ozaki_bf16":
+                    lb += self.pass_scale * (q2 * ((amk + bmk * nmod) * m * k + (akn + bkn * nmod) * k * n
+                                                   + (amn + bmn * nmod) * m * n) + c)
+                if 1e3 * lb <= limit:
+                    return False
+        return True
+
+    @staticmethod
+    def _pass_coeffs(M, K, N, R, L, wterms):
+        """_emulated_passes as a linear form (L >= 1): [a_mk, b_mk, a_kn, b_kn,
+        a_mn, b_mn, c], time = sum_x (a_x + b_x nmod) area_x + c."""
+        ga, gb = R / (M * K), R / (K * N)
+        width = 2 if L <= 1 else 1
+        H, S, V = HBM_GBS * 1e9, SPLIT_GBS * 1e9, LEVEL_GBS * 1e9
+        a_mk = a_kn = 16.0 / H + 8.0 / S
+        b_mk, b_kn = ga * width / S, gb * width / S
+        if M * K not in FUSED_BLOCKS or K * N not in FUSED_BLOCKS:
+            a_mk += 8.0 / V
+            a_kn += 8.0 / V
+            b_mk += 2.0 / V
+            b_kn += 2.0 / V
+        b_mn = 0.0
+        for l in range(2, L + 1):
+            w = 2 if l == L else 1
+            b_mk += R ** l * (2 + w) / ((M * K) ** l * V)
+            b_kn += R ** l * (2 + w) / ((K * N) ** l * V)
+            b_mn += R ** (l - 1) * M * N * 3 / ((M * N) ** l * V)
+        b_mn += CRT_PS_PER_ELEM_MOD * 1e-12 * (1.0 + W_TERM_FACTOR * (wterms / (M * N) - 1.0))
+        c = (6 + 3 * (L - 1)) * LAUNCH_US * 1e-6
+        return [a_mk, b_mk, a_kn, b_kn, 0.0, b_mn, c]
+
+    def _recursive_bounds(self, m, k, n, precs, rate, work, nmod, limit=float("inf")):
+        """(bound ms, index into the level table, precision) of every
+        admissible recursive candidate whose bound is at most `limit`, in
+        increasing bound: the _space bound plus, for the emulated path, the
+        modelled passes (the same numbers as _bound), computed for all cases
+        at once."""
+        import numpy as np
+        tab, _ = self._levels()
+        if not len(tab):
+            return []
+        rho, sm, sk, sn, RL = tab[:, 0], tab[:, 1], tab[:, 2], tab[:, 3], tab[:, 4]
+        mb, kb, nb = m // sm, k // sk, n // sn
+        ok = np.minimum(np.minimum(mb, kb), nb) >= 64
+        mp, kp, np_ = mb * sm, kb * sk, nb * sn
+        core = mp * kp * np_
+        fringe = 2.0 * (float(m) * n * k - core) / (self.fp64_tflops * 1e12)
+        out = []
+        for prec in precs:
+            lb = 1e3 * (2.0 * rho * core * work[prec] / (rate[prec] * 1e12) + fringe)
+            mask = ok
+            if prec == "ozaki_bf16":
+                mask = ok & (RL * nmod <= 65535)
+                c = tab[:, 5:]
+                t = ((c[:, 0] + c[:, 1] * nmod) * mp * kp + (c[:, 2] + c[:, 3] * nmod) * kp * np_
+                     + (c[:, 4] + c[:, 5] * nmod) * mp * np_ + c[:, 6])
+                lb = lb + 1e3 * t * self.pass_scale
+            out += [(float(lb[i]), int(i), prec) for i in np.nonzero(mask & (lb <= limit))[0]]
+        out.sort(key=lambda e: e[0])
+        return out
+
     def best_candidates(self, m, k, n, count=1):
         """The `count` candidates of least model time, found by branch and
-        bound: candidates in order of their lower bound, stopping once the
-        bound exceeds the count-th best model time so far (the same answer
-        as candidates()[:count], at a fraction of the model evaluations)."""
+        bound (the same model times as candidates()[:count], at a fraction of
+        the work): the classical candidates are modelled first; the recursive
+        ones are taken in increasing order of their _space + pass bound
+        (computed for all of them at once) and modelled until the bound
+        exceeds the count-th best model time so far."""
+        nmod = moduli_for(self.tol, k) if "ozaki_bf16" in self.precisions else None
+        rate = {"fp64": self.fp64_tflops, "ozaki_bf16": self.tc_tflops / (nmod or 1), **TF32_TFLOPS}
+        precs = []
+        for prec in self.precisions:
+            if prec == "ozaki_bf16" and nmod is None:
+                continue
+            if prec in TF32_ERR and 2 * TF32_ERR[prec][0] > self.tol:
+                continue
+            precs.append(prec)
+        work = {p: (3.0 if p == "fp32" else 1.0) for p in precs}
         best = []
-        for e in self._space(m, k, n):
-            if len(best) >= count and e[0] > best[count - 1].model_ms:
+
+        def add(c):
+            if c is not None:
+                best.append(c)
+                best.sort(key=lambda c: c.model_ms)
+                del best[count:]
+
+        for prec in precs:
+            add(self._model(m, k, n, "strassen_222_7", "", (2, 2, 2, 7), 0, prec, nmod))
+        _, info = self._levels()
+        limit = best[count - 1].model_ms if len(best) >= count else float("inf")
+        if self._recursion_excluded(m, k, n, precs, rate, work, nmod, limit):
+            return best
+        for lb, i, prec in self._recursive_bounds(m, k, n, precs, rate, work, nmod, limit):
+            if len(best) >= count and lb > best[count - 1].model_ms:
                 break
-            if len(best) >= count and self._bound(e) > best[count - 1].model_ms:
-                continue
-            _, name, perm, base, L, prec, nmod, _ = e
-            c = self._model(m, k, n, name, perm, base, L, prec, nmod)
-            if c is None:
-                continue
-            best.append(c)
-            best.sort(key=lambda c: c.model_ms)
-            best = best[:count]
+            name, perm, base, L, _ = info[i]
+            add(self._model(m, k, n, name, perm, base, L, prec, nmod))
         return best
 
     def _model(self, m, k, n, name, perm, base, L, prec, nmod):
@@ -468,6 +587,7 @@ class Autotuner:
         operands of the shape (the emulated candidates' moduli count moved up
         or down until its measured e_F meets the target with the fewest
         moduli), then timed (median of three calls); the fastest kept."""
+        m, k, n = int(m), int(k), int(n)   # numpy integers would overflow the exact bounds
         key = f"{m}x{k}x{n}:{self.tol:g}:{','.join(self.precisions)}"
         c = self._cache.get(key)
         if c is not None:

@@ -60,23 +60,79 @@ __device__ __forceinline__ void mma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem,
 // terms held in the 16-bit lanes of la / lb (lane value = byte): the integer
 // L = combination + bias lies in [0, 1023], so 0x6400 + L is the fp16 1024 + L
 // and one half2 subtraction leaves the exact value.
-__device__ __forceinline__ unsigned fa_combine(int kind, unsigned la, unsigned lb) {
+template <int KIND>
+__device__ __forceinline__ unsigned fa_combine(unsigned la, unsigned lb) {
+    // bias of L and sign of the result for each kind
+    constexpr unsigned short B = KIND == FA_P || KIND == FA_N ? 0x6480 : KIND == FA_PN ? 0x64ff : 0x6500;
+    constexpr bool NEG = KIND == FA_N || KIND == FA_NN || KIND == FA_N2;
     unsigned w;
-    __half2 base;
-    bool neg;
-    switch (kind) {
-        case FA_P: w = la; base = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)); neg = false; break;   // L - 128
-        case FA_N: w = la; base = __halves2half2(__ushort_as_half(0x6480), __ushort_as_half(0x6480)); neg = true; break;    // 128 - L
-        case FA_PP: w = la + lb; base = __halves2half2(__ushort_as_half(0x6500), __ushort_as_half(0x6500)); neg = false; break;   // L - 256
-        case FA_PN: w = la + 0x00ff00ffu - lb; base = __halves2half2(__ushort_as_half(0x64ff), __ushort_as_half(0x64ff)); neg = false; break;   // L - 255
-        case FA_NN: w = la + lb; base = __halves2half2(__ushort_as_half(0x6500), __ushort_as_half(0x6500)); neg = true; break;    // 256 - L
-        case FA_P2: w = la + la; base = __halves2half2(__ushort_as_half(0x6500), __ushort_as_half(0x6500)); neg = false; break;   // 2a = L - 256
-        default: w = la + la; base = __halves2half2(__ushort_as_half(0x6500), __ushort_as_half(0x6500)); neg = true; break;       // -2a
-    }
+    if constexpr (KIND == FA_P || KIND == FA_N) w = la;                          // L = a + 128
+    else if constexpr (KIND == FA_PP || KIND == FA_NN) w = la + lb;              // L = a + b + 256
+    else if constexpr (KIND == FA_PN) w = la + 0x00ff00ffu - lb;                 // L = a - b + 255
+    else w = la + la;                                                            // L = 2a + 256
     w += 0x64006400u;
     const __half2 x = *reinterpret_cast<const __half2 *>(&w);
-    const __half2 r = neg ? __hsub2(base, x) : __hsub2(x, base);
+    const __half2 base = __halves2half2(__ushort_as_half(B), __ushort_as_half(B));
+    const __half2 r = NEG ? __hsub2(base, x) : __hsub2(x, base);
     return *reinterpret_cast<const unsigned *>(&r);
+}
+
+// The converter warps' work on one tile: for every k-block, wait for its
+// term tiles and for the tensor-memory stage to be free, form the 128 x 64
+// block of S' (this thread: one row, 64 k-elements) and store it.  KIND and
+// the term count are compile-time, so the loop is straight-line code.
+template <int KIND>
+__device__ __forceinline__ bool fa_convert_tile(const unsigned char *smem, uint64_t *full, uint64_t *afull,
+                                                uint64_t *aempty, uint32_t tmem, int warp, int row, int kblocks,
+                                                int64_t kL, int64_t &gk, unsigned long long wait_ns) {
+    constexpr bool TWO = KIND == FA_PP || KIND == FA_PN || KIND == FA_NN;
+    for (int kb = 0; kb < kblocks; ++kb, ++gk) {
+        const int s = int(gk % FA_STAGES), j = int(gk % FA_ASTAGES);
+        if (!mbar_wait(&full[s], uint32_t((gk / FA_STAGES) & 1), wait_ns) ||
+            (gk >= FA_ASTAGES && !mbar_wait(&aempty[j], uint32_t(((gk / FA_ASTAGES) - 1) & 1), wait_ns)))
+            return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned char *ta = smem + s * FA_STAGE_BYTES + FA_B_BYTES + row * 64;
+        uint32_t v[32];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            // 16-byte chunk c of the row, 64-byte swizzle: chunk c ^ ((row / 2) % 4)
+            const int off = 16 * (c ^ ((row >> 1) & 3));
+            const uint4 x = *reinterpret_cast<const uint4 *>(ta + off);
+            uint4 y = x;
+            if constexpr (TWO) y = *reinterpret_cast<const uint4 *>(ta + FA_A_BYTES + off);
+            const unsigned xa[4] = {x.x ^ 0x80808080u, x.y ^ 0x80808080u, x.z ^ 0x80808080u, x.w ^ 0x80808080u};
+            const unsigned ya[4] = {y.x ^ 0x80808080u, y.y ^ 0x80808080u, y.z ^ 0x80808080u, y.w ^ 0x80808080u};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                v[8 * c + 2 * w] = fa_combine<KIND>(__byte_perm(xa[w], 0u, 0x4140), __byte_perm(ya[w], 0u, 0x4140));
+                v[8 * c + 2 * w + 1] =
+                    fa_combine<KIND>(__byte_perm(xa[w], 0u, 0x4342), __byte_perm(ya[w], 0u, 0x4342));
+            }
+        }
+        const int kvalid = (int)min((int64_t)FA_BK, kL - (int64_t)kb * FA_BK);
+        if (kvalid < FA_BK) {
+            // past the block's k range: zero (the tile reaches into the next block)
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (2 * e >= kvalid) v[e] = 0u;
+                else if (2 * e + 1 >= kvalid) v[e] &= 0xffffu;
+            }
+        }
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(FA_A_COL0 + j * 32);
+        asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                     "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                     ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
+                       "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+                       "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]),
+                       "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]),
+                       "r"(v[31])
+                     : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&afull[j]);
+    }
+    return true;
 }
 
 __global__ void __launch_bounds__(FA_THREADS, 1)
@@ -191,57 +247,18 @@ residue_gemm_fa(const __grid_constant__ FaParams P, int *err, unsigned long long
         for (int64_t tile = blockIdx.x; tile < P.tiles_total && ok; tile += gridDim.x) {
             int z, tm, tn;
             tile_coords(tile, per_plane, P.tiles_m, P.tiles_n, z, tm, tn);
-            const int leaf = z / P.nmod, kind = P.t.kind[leaf], two = P.t.n[leaf] > 1;
-            for (int kb = 0; kb < P.kblocks; ++kb, ++gk) {
-                const int s = int(gk % FA_STAGES), j = int(gk % FA_ASTAGES);
-                if (!mbar_wait(&full[s], uint32_t((gk / FA_STAGES) & 1), wait_ns) ||
-                    (gk >= FA_ASTAGES &&
-                     !mbar_wait(&aempty[j], uint32_t(((gk / FA_ASTAGES) - 1) & 1), wait_ns))) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const unsigned char *ta = smem + s * FA_STAGE_BYTES + FA_B_BYTES + row * 64;
-                const int kvalid = (int)min((int64_t)FA_BK, P.kL - (int64_t)kb * FA_BK);
-                uint32_t v[32];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    // 16-byte chunk c of the row, 64-byte swizzle: chunk c ^ ((row / 2) % 4)
-                    const int off = 16 * (c ^ ((row >> 1) & 3));
-                    const uint4 x = *reinterpret_cast<const uint4 *>(ta + off);
-                    const uint4 y = two ? *reinterpret_cast<const uint4 *>(ta + FA_A_BYTES + off) : x;
-                    const unsigned xa[4] = {x.x ^ 0x80808080u, x.y ^ 0x80808080u, x.z ^ 0x80808080u,
-                                            x.w ^ 0x80808080u};
-                    const unsigned ya[4] = {y.x ^ 0x80808080u, y.y ^ 0x80808080u, y.z ^ 0x80808080u,
-                                            y.w ^ 0x80808080u};
-#pragma unroll
-                    for (int w = 0; w < 4; ++w) {
-                        v[8 * c + 2 * w] = fa_combine(kind, __byte_perm(xa[w], 0u, 0x4140), __byte_perm(ya[w], 0u, 0x4140));
-                        v[8 * c + 2 * w + 1] =
-                            fa_combine(kind, __byte_perm(xa[w], 0u, 0x4342), __byte_perm(ya[w], 0u, 0x4342));
-                    }
-                }
-                if (kvalid < FA_BK) {
-                    // past the block's k range: zero (the tile reaches into the next block)
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        if (2 * e >= kvalid) v[e] = 0u;
-                        else if (2 * e + 1 >= kvalid) v[e] &= 0xffffu;
-                    }
-                }
-                const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(FA_A_COL0 + j * 32);
-                asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-                             "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
-                             ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
-                               "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-                               "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]),
-                               "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]),
-                               "r"(v[31])
-                             : "memory");
-                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(&afull[j]);
+            const int leaf = z / P.nmod;
+#define FA_CONV(K) ok = fa_convert_tile<K>(smem, full, afull, aempty, tmem, warp, row, P.kblocks, P.kL, gk, wait_ns)
+            switch (P.t.kind[leaf]) {
+                case FA_P: FA_CONV(FA_P); break;
+                case FA_N: FA_CONV(FA_N); break;
+                case FA_PP: FA_CONV(FA_PP); break;
+                case FA_PN: FA_CONV(FA_PN); break;
+                case FA_NN: FA_CONV(FA_NN); break;
+                case FA_P2: FA_CONV(FA_P2); break;
+                default: FA_CONV(FA_N2); break;
             }
+#undef FA_CONV
         }
         if (!ok && lane == 0) atomicExch(err, 1);
     } else {

@@ -118,3 +118,31 @@ def test_branch_and_bound_finds_the_model_optimum(shape, precs):
     for count in (1, 3):
         got = t.best_candidates(*shape, count)
         assert [c.model_ms for c in got] == [c.model_ms for c in full[:count]]
+
+
+def test_fast_search_matches_the_full_ranking_on_the_serving_mix():
+    # the pruned search (vectorised bounds, per-depth exclusion) returns the
+    # model optimum of the full ranking on shapes of the serving mix
+    from paper_1409_2908_gb300 import serve
+    for precs in (("fp64", "ozaki_bf16"), ("fp64",)):
+        t = autotune.Autotuner(tol=1e-11, precisions=precs, measure=False)
+        for m, k, n in serve.request_shapes(150, seed=77):
+            m, k, n = int(m), int(k), int(n)
+            full = t.candidates(m, k, n)
+            got = t.best_candidates(m, k, n, 2)
+            assert [c.model_ms for c in got] == [c.model_ms for c in full[:2]], (m, k, n)
+
+
+def test_vectorised_bounds_equal_the_scalar_bounds():
+    t = autotune.Autotuner(tol=1e-11, measure=False)
+    m, k, n = 6000, 5000, 7000
+    nmod = autotune.moduli_for(t.tol, k)
+    rate = {"fp64": t.fp64_tflops, "ozaki_bf16": t.tc_tflops / nmod}
+    work = {"fp64": 1.0, "ozaki_bf16": 1.0}
+    _, info = t._levels()
+    vec = {(info[i][0], info[i][1], info[i][3], p): lb
+           for lb, i, p in t._recursive_bounds(m, k, n, ("fp64", "ozaki_bf16"), rate, work, nmod)}
+    scal = {(e[1], e[2], e[4], e[5]): t._bound(e) for e in t._space(m, k, n) if e[4] > 0}
+    assert vec.keys() == scal.keys()
+    for key in vec:
+        assert abs(vec[key] - scal[key]) <= 1e-9 * scal[key]
