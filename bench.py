@@ -664,7 +664,9 @@ def main():
                     help="headline accuracy gate: fp64 = no worse than native FP64 Strassen L1 (and --tol); "
                          "tol = --tol alone")
     ap.add_argument("--no-fp64", action="store_true", help="skip the timed native-FP64 sub-record")
-    ap.add_argument("--no-fs", action="store_true", help="no candidates with S' formed inside the GEMM")
+    ap.add_argument("--fs", action="store_true",
+                    help="also try emulated plans with S' formed inside the GEMM (FLAG_TC_FUSED_S; "
+                         "1.9x slower on this GPU, so not searched by default)")
     ap.add_argument("--precisions", default="fp64,ozaki_bf16",
                     help="comma list of leaf precisions to try: fp64, ozaki_bf16, tf32, fp32")
     args = ap.parse_args()
@@ -723,7 +725,7 @@ def main():
         else:
             # tensor-core leaves: the classical product (0 levels) and the fast plans;
             # emulated ones at <= 1 level also with S' formed inside the GEMM
-            sch = ["lw", "fs"] if prec == "ozaki_bf16" and not args.no_fs else ["lw"]
+            sch = ["lw", "fs"] if prec == "ozaki_bf16" and args.fs else ["lw"]
             cands += [("strassen_222_7", 0, sc, prec) for sc in sch]
             cands += [(a, L, sc, prec) for a, L in wl["cands"]
                       if os.path.exists(fmm.algorithm_path(a)) and L <= 2
