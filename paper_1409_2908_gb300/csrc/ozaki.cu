@@ -64,6 +64,7 @@ __constant__ unsigned c_r32[OZ_MAX_MOD];                  // 2^32 mod p
 __constant__ unsigned c_r21[OZ_MAX_MOD], c_r42[OZ_MAX_MOD];  // 2^21 and 2^42 mod p
 __constant__ float c_modf[OZ_MAX_MOD], c_invp[OZ_MAX_MOD];  // p and 1/p as floats
 __constant__ float c_klimb[2][OZ_MAX_MOD][5];              // 2^(13 i), 2^(14 i) mod p as floats
+__constant__ float c_klimbw[OZ_MAX_MOD][3];                // 2^0, 2^22, 2^37 mod p, balanced (|w| <= p/2)
 constexpr int OZ_MAX_TERMS = 512, OZ_MAX_R = 64;           // limits of the staged term lists
 // CRT by a weighted sum: X = sum_q r_q c_q (mod P), c_q = (P/p_q) ((P/p_q)^-1 mod p_q)
 // mod P, held as eight 16-bit limbs so every limb sum fits an int32.
@@ -572,12 +573,16 @@ constexpr int OZ_IMAGIC = 0x4B400000;
 // dst + q qstep as bfloat16 (FINAL, the GEMM operand; |r| <= 129 is exact and
 // keeps the GEMM's 512-long FP32 chunks exact) or int8 (a later level's input;
 // representatives that wrap stay in the same class: only p = 256 reaches 128).
-template <bool FINAL, int LB, int NLB, bool F16 = false>
+template <bool FINAL, int LB, int NLB, bool F16 = false, int LB0 = LB>
 __device__ __forceinline__ void emit_child(const long long *sv, const int2 *sterm, int t0, int t1, int nmod,
                                            char *dst, int64_t qstep, int valid) {
-    // LB-bit limbs, NLB of them (|S'| < 2^(LB NLB), host-checked); the
-    // weighted limb sum stays below NLB 2^LB 2^8 <= 2^24, exact in float
-    static_assert(LB == 13 || LB == 14, "limb width");
+    // Uniform layouts: NLB limbs of LB bits (|S'| < 2^(LB NLB), host-checked),
+    // weights 2^(LB i) mod p in [0, p): the weighted sum stays below
+    // NLB 2^LB 2^8 <= 2^24, exact in float.  The wide layout (LB0 = 22):
+    // limbs of 22, 15 and 15 bits (|S'| < 2^52) with balanced weights
+    // (|w| <= 128), so |x| < 2^22 + 2 2^15 2^7 = 1.5 2^23, exact too, with one
+    // multiply-add fewer per residue than four 14-bit limbs.
+    static_assert((LB0 == LB && (LB == 13 || LB == 14)) || (LB0 == 22 && LB == 15 && NLB == 3), "limb layout");
     long long S[4] = {0, 0, 0, 0};
     for (int t = t0; t < t1; ++t) {
         const int2 tm = sterm[t];
@@ -592,7 +597,8 @@ __device__ __forceinline__ void emit_child(const long long *sv, const int2 *ster
         const unsigned long long u = neg ? (unsigned long long)(-S[e]) : (unsigned long long)S[e];
 #pragma unroll
         for (int i = 0; i < NLB; ++i) {
-            const float f = __int_as_float(OZ_IMAGIC + (int)((u >> (LB * i)) & ((1ull << LB) - 1))) - OZ_FMAGIC;
+            const int sh = i == 0 ? 0 : LB0 + LB * (i - 1), wd = i == 0 ? LB0 : LB;
+            const float f = __int_as_float(OZ_IMAGIC + (int)((u >> sh) & ((1ull << wd) - 1))) - OZ_FMAGIC;
             d[e][i] = neg ? -f : f;
         }
     }
@@ -604,7 +610,9 @@ __device__ __forceinline__ void emit_child(const long long *sv, const int2 *ster
         for (int e = 0; e < 4; ++e) {
             float x = d[e][0];
 #pragma unroll
-            for (int i = 1; i < NLB; ++i) x = fmaf(d[e][i], c_klimb[LB - 13][q][i], x);
+            for (int i = 1; i < NLB; ++i)
+                x = fmaf(d[e][i], LB0 == LB ? c_klimb[LB - 13 < 0 ? 0 : (LB - 13 > 1 ? 1 : LB - 13)][q][i]
+                                            : c_klimbw[q][i < 3 ? i : 2], x);
             const float tq = fmaf(x, c_invp[q], OZ_FMAGIC) - OZ_FMAGIC;
             r[e] = fmaf(-tq, c_modf[q], x);
         }
@@ -657,11 +665,13 @@ __device__ __forceinline__ void stage_terms(int R, int gridC, const int *ptr, co
 // A' = round(A_ij 2^ea_i).  Thread: one row of the child blocks and 4
 // consecutive columns of out_ld (columns >= cols are the zero padding of the
 // GEMM operand).  256 threads; dynamic shared memory NB x 4 x 256 int64.
-// Limb layouts of the combined integers: LC 0 = 3 x 14 bits, 1 = 4 x 14, 2 = 5 x 13.
+// Limb layouts of the combined integers: LC 0 = 3 x 14 bits, 1 = 4 x 14, 2 = 5 x 13,
+// 3 = 22 + 15 + 15 (balanced weights).
 template <int LC> struct LimbCfg;
-template <> struct LimbCfg<0> { static constexpr int LB = 14, N = 3; };
-template <> struct LimbCfg<1> { static constexpr int LB = 14, N = 4; };
-template <> struct LimbCfg<2> { static constexpr int LB = 13, N = 5; };
+template <> struct LimbCfg<0> { static constexpr int LB = 14, N = 3, LB0 = 14; };
+template <> struct LimbCfg<1> { static constexpr int LB = 14, N = 4, LB0 = 14; };
+template <> struct LimbCfg<2> { static constexpr int LB = 13, N = 5, LB0 = 13; };
+template <> struct LimbCfg<3> { static constexpr int LB = 15, N = 3, LB0 = 22; };   // 22 + 15 + 15 bits
 
 template <int NB, bool FINAL, int LC>
 __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t lda, const int *ea, int64_t rows,
@@ -700,7 +710,8 @@ __global__ void __launch_bounds__(256) split_form_rows(const double *A, int64_t 
     char *dst = (char *)out + (i * out_ld + j0) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
     for (int o = 0; o < R; ++o, dst += ostep)
-        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep, valid);
+        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N, false, LimbCfg<LC>::LB0>(sv, sterm, sptr[o], sptr[o + 1],
+                                                                                  nmod, dst, qstep, valid);
 }
 
 // T side, transposed: B (peeled core, ld ldb) as a grid of K x N blocks of
@@ -751,7 +762,7 @@ __global__ void __launch_bounds__(256) split_form_cols_t(const double *B, int64_
     char *dst = (char *)out + (n * out_ld + k) * ES;
     const int64_t qstep = plane * ES, ostep = (int64_t)nmod * plane * ES;
     for (int o = 0; o < R; ++o, dst += ostep)
-        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N, F16>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep,
+        emit_child<FINAL, LimbCfg<LC>::LB, LimbCfg<LC>::N, F16, LimbCfg<LC>::LB0>(sv, sterm, sptr[o], sptr[o + 1], nmod, dst, qstep,
                                                                 valid);
 }
 
@@ -1170,6 +1181,17 @@ cudaError_t ensure_tables(int nmod) {
                     klimb[wdt][i][l] = (float)w;
                 }
         if ((e = cudaMemcpyToSymbol(c_klimb, klimb, sizeof(klimb))) != cudaSuccess) return e;
+        float klimbw[OZ_MAX_MOD][3];
+        for (int i = 0; i < OZ_MAX_MOD; ++i) {
+            const int shifts[3] = {0, 22, 37};
+            for (int l = 0; l < 3; ++l) {
+                long long w = 1;
+                for (int t = 0; t < shifts[l]; ++t) w = (w * 2) % mods[i];
+                if (2 * w > mods[i]) w -= mods[i];   // balanced: |w| <= p / 2
+                klimbw[i][l] = (float)w;
+            }
+        }
+        if ((e = cudaMemcpyToSymbol(c_klimbw, klimbw, sizeof(klimbw))) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyToSymbol(c_crt16, crt16, sizeof(crt16))) != cudaSuccess) return e;
     if ((e = cudaMemcpyToSymbol(c_P16, P16, sizeof(P16))) != cudaSuccess) return e;
@@ -1596,7 +1618,8 @@ static cudaError_t configure_split_form() {
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, NB * 32 * 33 * 8)) != cudaSuccess) \
         return e;
 #define FMM_CFG(NB) FMM_CFG1(NB, true, 0) FMM_CFG1(NB, false, 0) FMM_CFG1(NB, true, 1) FMM_CFG1(NB, false, 1) \
-                    FMM_CFG1(NB, true, 2) FMM_CFG1(NB, false, 2) FMM_CFG16(NB, 0) FMM_CFG16(NB, 1) FMM_CFG16(NB, 2)
+                    FMM_CFG1(NB, true, 2) FMM_CFG1(NB, false, 2) FMM_CFG1(NB, true, 3) FMM_CFG1(NB, false, 3) \
+                    FMM_CFG16(NB, 0) FMM_CFG16(NB, 1) FMM_CFG16(NB, 2) FMM_CFG16(NB, 3)
     FMM_CFG(1) FMM_CFG(4) FMM_CFG(6) FMM_CFG(8) FMM_CFG(9)
 #undef FMM_CFG16
 #undef FMM_CFG1
@@ -1696,14 +1719,14 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int gK = rp.L ? rp.K : 1, gN = rp.L ? rp.N : 1, nbA = rp.L ? rp.M * rp.K : 1, nbB = rp.L ? rp.K * rp.N : 1;
     const int *up = rp.L ? rp.u_ptr : id_ptr, *uc = rp.L ? rp.u_code : id_code, *ui = rp.L ? rp.u_icoef : id_coef;
     const int *vp = rp.L ? rp.v_ptr : id_ptr, *vc = rp.L ? rp.v_code : id_code, *vi = rp.L ? rp.v_icoef : id_coef;
-    // limbs of |S'| < 2^(beta + ceil(log2 max sum|c|)): 3 x 14, 4 x 14 or 5 x 13 bits
+    // limbs of |S'| < 2^(beta + ceil(log2 max sum|c|)): 3 x 14, 22 + 15 + 15, 4 x 14 or 5 x 13 bits
     int lc = 0;
     {
         const int cmax = rp.L ? std::max(rp.u_absmax, rp.v_absmax) : 1;
         // |A'| <= 2^beta (rounded), so |S'| <= cmax 2^beta < 2^(beta + floor(log2 cmax) + 1)
         int bits = beta + 1;
         while ((2 << (bits - beta - 1)) <= cmax) ++bits;
-        lc = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
+        lc = bits <= 42 ? 0 : bits <= 52 ? 3 : (bits <= 56 ? 1 : 2);
     }
 #define FMM_SPLIT(WHICH, F, LC)                                                                                     \
     (WHICH ? launch_split_form_cols_t<F, LC>(nbB, B, ldb, eb, kl1, nl1, gN, R1, nmod, vp, vc, vi, b + w.lb[0],      \
@@ -1718,14 +1741,14 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     int lc_id = 0;
     {
         const int bits = beta + 1;   // |A'| <= 2^beta
-        lc_id = bits <= 42 ? 0 : (bits <= 56 ? 1 : 2);
+        lc_id = bits <= 42 ? 0 : bits <= 52 ? 3 : (bits <= 56 ? 1 : 2);
     }
     auto fa_split = [&](int which) -> cudaError_t {
         cudaError_t se = cudaSuccess;
         if (which) {
 #define FMM_SFC16(LC) launch_split_form_cols_t<true, LC, true>(nbB, B, ldb, eb, kl1, nl1, gN, R1, nmod, vp, vc, vi, \
                                                                  b + w.lb[0], out_ld1, s)
-            se = lc == 0 ? FMM_SFC16(0) : lc == 1 ? FMM_SFC16(1) : FMM_SFC16(2);
+            se = lc == 0 ? FMM_SFC16(0) : lc == 3 ? FMM_SFC16(3) : lc == 1 ? FMM_SFC16(1) : FMM_SFC16(2);
 #undef FMM_SFC16
             ++*launches;
             return se;
@@ -1735,7 +1758,7 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
             const int64_t r0 = a * ml1 + ar0;
 #define FMM_SFR8(LC) launch_split_form_rows<false, LC>(1, A, lda, ea, mp, kp, 1, 1, nmod, id_ptr, id_code, id_coef, \
                                                          b + w.la[0], kp, s, r0, anr)
-            se = lc_id == 0 ? FMM_SFR8(0) : lc_id == 1 ? FMM_SFR8(1) : FMM_SFR8(2);
+            se = lc_id == 0 ? FMM_SFR8(0) : lc_id == 3 ? FMM_SFR8(3) : lc_id == 1 ? FMM_SFR8(1) : FMM_SFR8(2);
 #undef FMM_SFR8
             ++*launches;
         }
@@ -1745,9 +1768,11 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         if (fa) return fa_split(which);
         cudaError_t se;
         if (last1)
-            se = lc == 0 ? FMM_SPLIT(which, true, 0) : lc == 1 ? FMM_SPLIT(which, true, 1) : FMM_SPLIT(which, true, 2);
+            se = lc == 0 ? FMM_SPLIT(which, true, 0) : lc == 3 ? FMM_SPLIT(which, true, 3)
+                 : lc == 1 ? FMM_SPLIT(which, true, 1) : FMM_SPLIT(which, true, 2);
         else
-            se = lc == 0 ? FMM_SPLIT(which, false, 0) : lc == 1 ? FMM_SPLIT(which, false, 1) : FMM_SPLIT(which, false, 2);
+            se = lc == 0 ? FMM_SPLIT(which, false, 0) : lc == 3 ? FMM_SPLIT(which, false, 3)
+                 : lc == 1 ? FMM_SPLIT(which, false, 1) : FMM_SPLIT(which, false, 2);
         ++*launches;
         return se;
     };
