@@ -494,7 +494,25 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     }
     const double *pa = A, *pb = B;
     int64_t pld_a = lda, pld_b = ldb, pst_a = 0, pst_b = 0, parents = 1;
-    for (int l = 1; l <= p->L; ++l) {
+    double *prod = (double *)(wsb + wl.lvP.back());
+    // TF32-family leaves one level deep: the level fused with the conversion
+    // (each operand read once, S and T formed in FP32), no FP64 S/T levels
+    auto nnz = [](const std::vector<double> &F) {
+        size_t c = 0;
+        for (double x : F) c += x != 0.0;
+        return c;
+    };
+    auto grid_ok = [](int nb) { return nb == 4 || nb == 6 || nb == 8 || nb == 9; };
+    const bool tf_fused = tf && p->L == 1 && p->R <= 64 && grid_ok(p->M * p->K) && grid_ok(p->K * p->N) &&
+                          nnz(p->U) <= 512 && nnz(p->V) <= 512;
+    if (tf_fused) {
+        if ((e = tf32_first_level_products(A, lda, B, ldb, g.mL, g.kL, g.nL, p->M, p->K, p->N, p->R, p->dev.lu_ptr,
+                                           p->dev.lu_code, p->dev.lu_coef, p->dev.lv_ptr, p->dev.lv_code,
+                                           p->dev.lv_coef, prod, g.nL, g.mL * g.nL, wsb + wl.oz, s, launches,
+                                           tf32_split(p), p->tile)) != cudaSuccess)
+            return cuda_status(e);
+    }
+    for (int l = 1; l <= p->L && !tf_fused; ++l) {
         const int64_t ml = g.mp / ipow(p->M, l), kl = g.kp / ipow(p->K, l), nl = g.np / ipow(p->N, l);
         double *oa = (double *)(wsb + wl.lvS[l - 1]);
         double *ob = (double *)(wsb + wl.lvT[l - 1]);
@@ -506,9 +524,8 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
         pb = ob; pld_b = nl; pst_b = kl * nl;
         parents *= p->R;
     }
-    double *prod = (double *)(wsb + wl.lvP.back());
-    if ((e = leaf_products(pa, g.kL, g.mL * g.kL, pb, g.nL, g.kL * g.nL, prod, g.nL, g.mL * g.nL,
-                           p->leaves, g.mL, g.kL, g.nL)) != cudaSuccess)
+    if (!tf_fused && (e = leaf_products(pa, g.kL, g.mL * g.kL, pb, g.nL, g.kL * g.nL, prod, g.nL, g.mL * g.nL,
+                                        p->leaves, g.mL, g.kL, g.nL)) != cudaSuccess)
         return cuda_status(e);
     const bool kfringe = g.kp < k;
     if (kfringe &&

@@ -196,6 +196,15 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
                           int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
                           int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
                           int split = 1, int tile = FMM_TILE_AUTO);
+// One recursive level fused with the TF32 conversion (csrc/tf32.cu): the R
+// leaf products of A (gM x gK blocks of mL x kL) and B (gK x gN blocks of
+// kL x nL) from the level's term lists, S and T formed in FP32 while each
+// operand is read once.  Block grids of 4, 6, 8 or 9; R <= 64.
+cudaError_t tf32_first_level_products(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t mL,
+                                      int64_t kL, int64_t nL, int gM, int gK, int gN, int R, const int *u_ptr,
+                                      const int *u_code, const double *u_coef, const int *v_ptr,
+                                      const int *v_code, const double *v_coef, double *Out, int64_t ldo,
+                                      int64_t os, void *ws, cudaStream_t s, int *launches, int split, int tile);
 // residue-space recursion (integer base coefficients only)
 struct ResPlan {
     int M, K, N, R, L;

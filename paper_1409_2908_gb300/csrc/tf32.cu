@@ -342,6 +342,133 @@ __global__ void tf32_cols_t(const double *Y, int64_t ldy, int64_t ys, int64_t ro
     }
 }
 
+// ---------------------------------------------------------------------
+// First recursive level fused with the conversion (TF32-family leaves, one
+// level): each FP64 operand is read once and every child S_r = sum_t c_t A_t
+// (Section 3.1's S formation) is formed in FP32 from the block values rounded
+// to FP32 once, then written as leaf r's TF32 operand (split 1) or its hi/lo
+// pair segments (split 3), exactly the layout tf32_rows / tf32_cols_t write.
+// The FP32 sums add at most a few units of 2^-24 relative to the operand,
+// far below TF32's 2^-11 and the pair's 2^-22.  Term lists: CSR over the
+// children, code = (block row << 16) | block column, FP64 coefficients.
+
+constexpr int TF_MAX_TERMS = 512, TF_MAX_R = 64;
+
+__device__ __forceinline__ void tf_stage_terms(int R, int gC, const int *ptr, const int *code, const double *coef,
+                                               int *sb, float *sc, int *sp) {
+    const int nt = __ldg(ptr + R);
+    for (int t = threadIdx.x + blockDim.x * threadIdx.y; t < nt; t += blockDim.x * blockDim.y) {
+        const int cd = __ldg(code + t);
+        sb[t] = (cd >> 16) * gC + (cd & 0xffff);
+        sc[t] = (float)__ldg(coef + t);
+    }
+    for (int o = threadIdx.x + blockDim.x * threadIdx.y; o <= R; o += blockDim.x * blockDim.y) sp[o] = __ldg(ptr + o);
+}
+
+// S side: A (ld lda) as a gR x gC grid of blocks rows x cols.  Thread: one row
+// i of the child blocks and 4 consecutive columns j of the padded k (columns
+// >= cols are zero).  out: R planes of rows x (split kpad) floats.
+template <int NB>
+__global__ void __launch_bounds__(256) tf32_form_rows(const double *A, int64_t lda, int64_t rows, int64_t cols,
+                                                      int gC, int R, const int *ptr, const int *code,
+                                                      const double *coef, int64_t kpad, int split, float *out) {
+    __shared__ int sb[TF_MAX_TERMS];
+    __shared__ float sc[TF_MAX_TERMS];
+    __shared__ int sp[TF_MAX_R + 1];
+    tf_stage_terms(R, gC, ptr, code, coef, sb, sc, sp);
+    __syncthreads();
+    const int64_t groups = kpad / 4;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= rows * groups) return;
+    const int64_t i = pos / groups, j0 = (pos % groups) * 4;
+    float v[NB][4];
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+        const double *x = A + ((int64_t)(b / gC) * rows + i) * lda + (int64_t)(b % gC) * cols + j0;
+        if (j0 + 4 <= cols && ((uintptr_t)x & 15) == 0) {
+            const double2 x0 = reinterpret_cast<const double2 *>(x)[0], x1 = reinterpret_cast<const double2 *>(x)[1];
+            v[b][0] = (float)x0.x; v[b][1] = (float)x0.y; v[b][2] = (float)x1.x; v[b][3] = (float)x1.y;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[b][e] = (j0 + e < cols) ? (float)x[e] : 0.0f;
+        }
+    }
+    const int64_t kk = kpad * split;
+    for (int r = 0; r < R; ++r) {
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int t = sp[r]; t < sp[r + 1]; ++t) {
+            const int bt = sb[t];
+            const float c = sc[t];
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (b == bt) {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[e] = fmaf(c, v[b][e], a[e]);
+                }
+        }
+        float *o = out + ((int64_t)r * rows + i) * kk + j0;
+        float4 hi, lo;
+        hi.x = to_tf32(a[0]); hi.y = to_tf32(a[1]); hi.z = to_tf32(a[2]); hi.w = to_tf32(a[3]);
+        *reinterpret_cast<float4 *>(o) = hi;
+        if (split == 3) {
+            lo.x = to_tf32(a[0] - hi.x); lo.y = to_tf32(a[1] - hi.y); lo.z = to_tf32(a[2] - hi.z);
+            lo.w = to_tf32(a[3] - hi.w);
+            *reinterpret_cast<float4 *>(o + kpad) = hi;      // segments hi | hi | lo
+            *reinterpret_cast<float4 *>(o + 2 * kpad) = lo;
+        }
+    }
+}
+
+// T side, transposed: B (ld ldb) as a gR x gC grid of blocks krows x ncols;
+// child r's T_r^T (ncols x split kpad, K-major).  CTA: 32 k x 32 n positions
+// of the child blocks through shared memory (NB tiles of 32 x 33 floats);
+// thread (tx, ty): loads rows ty, ty + 8, ..; writes k = k0 + tx.
+template <int NB>
+__global__ void __launch_bounds__(256) tf32_form_cols_t(const double *B, int64_t ldb, int64_t krows, int64_t ncols,
+                                                        int gC, int R, const int *ptr, const int *code,
+                                                        const double *coef, int64_t kpad, int split, float *out) {
+    __shared__ int sb[TF_MAX_TERMS];
+    __shared__ float sc[TF_MAX_TERMS];
+    __shared__ int sp[TF_MAX_R + 1];
+    __shared__ float tile[NB][32][33];
+    tf_stage_terms(R, gC, ptr, code, coef, sb, sc, sp);
+    const int64_t k0 = (int64_t)blockIdx.x * 32, n0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+#pragma unroll
+    for (int b = 0; b < NB; ++b)
+        for (int r = ty; r < 32; r += 8) {
+            const int64_t kr = k0 + r, nc = n0 + tx;
+            tile[b][r][tx] = (kr < krows && nc < ncols)
+                                 ? (float)B[((int64_t)(b / gC) * krows + kr) * ldb + (int64_t)(b % gC) * ncols + nc]
+                                 : 0.0f;
+        }
+    __syncthreads();
+    const int64_t kk = kpad * split;
+    const int64_t kc = k0 + tx;
+    if (kc >= kpad) return;
+    for (int rr = ty; rr < 32; rr += 8) {
+        const int64_t nc = n0 + rr;
+        if (nc >= ncols) continue;
+        for (int r = 0; r < R; ++r) {
+            float a = 0.0f;
+            for (int t = sp[r]; t < sp[r + 1]; ++t) {
+                const int bt = sb[t];
+                const float c = sc[t];
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    if (b == bt) a = fmaf(c, tile[b][tx][rr], a);
+            }
+            float *o = out + ((int64_t)r * ncols + nc) * kk + kc;
+            const float hi = to_tf32(a);
+            o[0] = hi;
+            if (split == 3) {
+                o[kpad] = to_tf32(a - hi);   // segments hi | lo | hi
+                o[2 * kpad] = hi;
+            }
+        }
+    }
+}
+
 typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                              CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -417,35 +544,16 @@ cudaError_t read_tf32_error(int *flag, bool clear) {
     return e;
 }
 
-// Out[leaf] (m x n, ldo, leaf stride os) (+)= tf32(S[leaf]) tf32(T[leaf]);
-// split 3: the FP32-accurate sum of the three TF32 pair products.
-cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
-                          int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
-                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
-                          int split, int tile) {
-    if (split != 1 && split != 3) return cudaErrorInvalidValue;
-    cudaError_t e = tf32_prepare();
-    if (e != cudaSuccess) return e;
+// The TF32 GEMM over operand planes already in the leaves' layout: fa
+// (leaves x m x split kpad), fb (leaves x n x split kpad), both 256-byte
+// aligned; Out[leaf] (m x n, ldo, leaf stride os) (+)= fa fb^T.
+static cudaError_t tf32_gemm_planes(float *fa, float *fb, double *Out, int64_t ldo, int64_t os, int64_t leaves,
+                                    int64_t m, int64_t n, int64_t kpad, int accumulate, cudaStream_t s,
+                                    int *launches, int split, int tile) {
+    cudaError_t e;
     int *err = nullptr;
     if ((e = cudaGetSymbolAddress((void **)&err, g_tf32_error)) != cudaSuccess) return e;
-    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K, kk = kpad * split;
-    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    float *fa = (float *)ws;
-    float *fb = (float *)((char *)ws + al(size_t(leaves) * m * kk * 4));
-    {
-        const int64_t total = leaves * m * kk;
-        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
-        tf32_rows<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, split, fa);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    {
-        if (leaves > 65535) return cudaErrorInvalidValue;
-        dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
-        tf32_cols_t<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, split, fb);
-        ++*launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    const int64_t kk = kpad * split;
     CUtensorMap ta, tb;
     // the chunked sums (FP32-accurate products) keep 64 running sums per drain
     // thread: 128-wide tiles with 8 drain warps fit them in registers
@@ -473,6 +581,87 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (t0 && !timing_mark(s)) timing_unmark();
     return cudaSuccess;
+}
+
+static size_t tf_al(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Out[leaf] (m x n, ldo, leaf stride os) (+)= tf32(S[leaf]) tf32(T[leaf]);
+// split 3: the FP32-accurate sum of the three TF32 pair products.
+cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double *T, int64_t ldt,
+                          int64_t ts, double *Out, int64_t ldo, int64_t os, int64_t leaves, int64_t m,
+                          int64_t k, int64_t n, int accumulate, void *ws, cudaStream_t s, int *launches,
+                          int split, int tile) {
+    if (split != 1 && split != 3) return cudaErrorInvalidValue;
+    cudaError_t e = tf32_prepare();
+    if (e != cudaSuccess) return e;
+    const int64_t kpad = (k + TB_K - 1) / TB_K * TB_K, kk = kpad * split;
+    float *fa = (float *)ws;
+    float *fb = (float *)((char *)ws + tf_al(size_t(leaves) * m * kk * 4));
+    {
+        const int64_t total = leaves * m * kk;
+        const unsigned blocks = (unsigned)std::min<int64_t>((total + 255) / 256, 152 * 32);
+        tf32_rows<<<blocks, 256, 0, s>>>(S, lds, ss, m, k, kpad, leaves, split, fa);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        if (leaves > 65535) return cudaErrorInvalidValue;
+        dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((n + 31) / 32), (unsigned)leaves);
+        tf32_cols_t<<<grid, dim3(32, 8), 0, s>>>(T, ldt, ts, k, n, kpad, split, fb);
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return tf32_gemm_planes(fa, fb, Out, ldo, os, leaves, m, n, kpad, accumulate, s, launches, split, tile);
+}
+
+// One recursive level fused with the conversion: A (ld lda) as an gM x gK
+// grid of mL x kL blocks and B (ld ldb) as gK x gN blocks of kL x nL; the
+// level's term lists (u: S side, v: T side); the R leaf products into Out
+// (mL x nL each, ldo, leaf stride os).  ws: the same operand planes as
+// tf32_products for R leaves of mL x kL x nL.
+cudaError_t tf32_first_level_products(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t mL,
+                                      int64_t kL, int64_t nL, int gM, int gK, int gN, int R, const int *u_ptr,
+                                      const int *u_code, const double *u_coef, const int *v_ptr,
+                                      const int *v_code, const double *v_coef, double *Out, int64_t ldo,
+                                      int64_t os, void *ws, cudaStream_t s, int *launches, int split, int tile) {
+    if (split != 1 && split != 3) return cudaErrorInvalidValue;
+    if (R > TF_MAX_R || R > 65535) return cudaErrorInvalidValue;
+    cudaError_t e = tf32_prepare();
+    if (e != cudaSuccess) return e;
+    const int64_t kpad = (kL + TB_K - 1) / TB_K * TB_K, kk = kpad * split;
+    float *fa = (float *)ws;
+    float *fb = (float *)((char *)ws + tf_al(size_t(R) * mL * kk * 4));
+    const int nbA = gM * gK, nbB = gK * gN;
+    {
+        const int64_t threads = mL * (kpad / 4);
+        const unsigned blocks = (unsigned)((threads + 255) / 256);
+#define FMM_TFR(NB) tf32_form_rows<NB><<<blocks, 256, 0, s>>>(A, lda, mL, kL, gK, R, u_ptr, u_code, u_coef, kpad, split, fa)
+        switch (nbA) {
+            case 4: FMM_TFR(4); break;
+            case 6: FMM_TFR(6); break;
+            case 8: FMM_TFR(8); break;
+            case 9: FMM_TFR(9); break;
+            default: return cudaErrorNotSupported;
+        }
+#undef FMM_TFR
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        const dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((nL + 31) / 32));
+#define FMM_TFC(NB) tf32_form_cols_t<NB><<<grid, dim3(32, 8), 0, s>>>(B, ldb, kL, nL, gN, R, v_ptr, v_code, v_coef, kpad, split, fb)
+        switch (nbB) {
+            case 4: FMM_TFC(4); break;
+            case 6: FMM_TFC(6); break;
+            case 8: FMM_TFC(8); break;
+            case 9: FMM_TFC(9); break;
+            default: return cudaErrorNotSupported;
+        }
+#undef FMM_TFC
+        ++*launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return tf32_gemm_planes(fa, fb, Out, ldo, os, R, mL, nL, kpad, 0, s, launches, split, tile);
 }
 
 // The timeout path of the TF32 GEMM (see residue_gemm_timeout_probe): one

@@ -27,7 +27,10 @@ def run(plan, A, B):
                                                ("strassen_222_7", 0, (1, 1, 1)),
                                                ("strassen_222_7", 1, (257, 515, 259)),
                                                ("strassen_222_7", 2, (300, 260, 290)),
-                                               ("fmm_323_15", 1, (301, 200, 303))])
+                                               ("fmm_323_15", 1, (301, 200, 303)),
+                                               # one level fused with the conversion: block grids of 8 and 9
+                                               ("fmm_424_26", 1, (516, 202, 390)),
+                                               ("fmm_333_23", 1, (301, 330, 299))])
 def test_tf32_integer_exact(name, levels, shape):
     p = fmm.Plan(name, levels=levels, precision="tf32")
     A, B = synth.operands(*shape, 61, kind="integer")
@@ -55,7 +58,9 @@ def test_tf32_uniform_within_rounding_bound(name, levels):
                                                ("strassen_222_7", 0, (1, 1, 1)),
                                                ("strassen_222_7", 1, (257, 515, 259)),
                                                ("winograd_222_7", 2, (300, 260, 290)),
-                                               ("fmm_323_15", 1, (301, 200, 303))])
+                                               ("fmm_323_15", 1, (301, 200, 303)),
+                                               ("fmm_424_26", 1, (516, 202, 390)),
+                                               ("fmm_333_23", 1, (301, 330, 299))])
 def test_fp32_integer_exact(name, levels, shape):
     # small integers are their own hi part (lo = 0) and every sum is exact in FP32
     p = fmm.Plan(name, levels=levels, precision="fp32")
