@@ -501,12 +501,18 @@ class Autotuner:
                 if best is None or tt < best[0]:
                     best = (tt, tname)
             t, tile = best
-            # FP64 operands to TF32 (8 bytes in, 4 split bytes out per element)
-            t += leaves * (mL * kL + kL * nL) * (8 + 4 * split) / (HBM_GBS * 1e9)
             adds = 0.0
-            for l in range(1, L + 1):
-                adds += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
-                                  + (mp // M ** l) * (np_ // N ** l)) * 8 * 3
+            if L == 1 and M * K in FUSED_BLOCKS and K * N in FUSED_BLOCKS and R <= 64:
+                # the level fused with the conversion: each operand read once,
+                # the leaves' TF32 operands written; W in FP64 from the products
+                t += (8 * (mp * kp + kp * np_) + 4 * split * leaves * (mL + nL) * kpad) / (HBM_GBS * 1e9)
+                adds = R * mL * nL * 8 * 3
+            else:
+                # FP64 operands to TF32 (8 bytes in, 4 split bytes out per element)
+                t += leaves * (mL * kL + kL * nL) * (8 + 4 * split) / (HBM_GBS * 1e9)
+                for l in range(1, L + 1):
+                    adds += R ** l * ((mp // M ** l) * (kp // K ** l) + (kp // K ** l) * (np_ // N ** l)
+                                      + (mp // M ** l) * (np_ // N ** l)) * 8 * 3
             t += adds / (HBM_GBS * 1e9)
             t += (3 + 3 * L) * LAUNCH_US * 1e-6
             flags = fmm.FLAG_LEVELWISE if L > 0 else fmm.FLAGS_DEFAULT
