@@ -449,6 +449,9 @@ __global__ void __launch_bounds__(256) tf32_form_cols_t(const double *B, int64_t
     for (int rr = ty; rr < 32; rr += 8) {
         const int64_t nc = n0 + rr;
         if (nc >= ncols) continue;
+        float v[NB];   // this position's value in every block, read from shared memory once
+#pragma unroll
+        for (int b = 0; b < NB; ++b) v[b] = tile[b][tx][rr];
         for (int r = 0; r < R; ++r) {
             float a = 0.0f;
             for (int t = sp[r]; t < sp[r + 1]; ++t) {
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(256) tf32_form_cols_t(const double *B, int64_t
                 const float c = sc[t];
 #pragma unroll
                 for (int b = 0; b < NB; ++b)
-                    if (b == bt) a = fmaf(c, tile[b][tx][rr], a);
+                    if (b == bt) a = fmaf(c, v[b], a);
             }
             float *o = out + ((int64_t)r * ncols + nc) * kk + kc;
             const float hi = to_tf32(a);
