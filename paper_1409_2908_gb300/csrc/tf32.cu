@@ -446,26 +446,34 @@ __global__ void __launch_bounds__(256) tf32_form_cols_t(const double *B, int64_t
     const int64_t kk = kpad * split;
     const int64_t kc = k0 + tx;
     if (kc >= kpad) return;
-    for (int rr = ty; rr < 32; rr += 8) {
-        const int64_t nc = n0 + rr;
-        if (nc >= ncols) continue;
-        float v[NB];   // this position's value in every block, read from shared memory once
+    // this thread's four n positions (ty, ty + 8, ty + 16, ty + 24): every
+    // block's values read from shared memory once, one walk over the terms
+    float v[NB][4];
 #pragma unroll
-        for (int b = 0; b < NB; ++b) v[b] = tile[b][tx][rr];
-        for (int r = 0; r < R; ++r) {
-            float a = 0.0f;
-            for (int t = sp[r]; t < sp[r + 1]; ++t) {
-                const int bt = sb[t];
-                const float c = sc[t];
+    for (int b = 0; b < NB; ++b)
 #pragma unroll
-                for (int b = 0; b < NB; ++b)
-                    if (b == bt) a = fmaf(c, v[b], a);
-            }
+        for (int q = 0; q < 4; ++q) v[b][q] = tile[b][tx][ty + 8 * q];
+    for (int r = 0; r < R; ++r) {
+        float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        for (int t = sp[r]; t < sp[r + 1]; ++t) {
+            const int bt = sb[t];
+            const float c = sc[t];
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (b == bt) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) a[q] = fmaf(c, v[b][q], a[q]);
+                }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t nc = n0 + ty + 8 * q;
+            if (nc >= ncols) continue;
             float *o = out + ((int64_t)r * ncols + nc) * kk + kc;
-            const float hi = to_tf32(a);
+            const float hi = to_tf32(a[q]);
             o[0] = hi;
             if (split == 3) {
-                o[kpad] = to_tf32(a - hi);   // segments hi | lo | hi
+                o[kpad] = to_tf32(a[q] - hi);   // segments hi | lo | hi
                 o[2 * kpad] = hi;
             }
         }
