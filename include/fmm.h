@@ -70,7 +70,10 @@ typedef enum {
     FMM_PREC_OZAKI_BF16 = 3,
     /* Leaf products on the tensor cores in TF32 (operands rounded to a
        10-bit significand, FP32 accumulation), widened to FP64 for the W
-       combination; S/T formation and the fringe stay FP64.  Relative error
+       combination.  With one recursive level (block grids of 4, 6, 8 or 9
+       blocks, R <= 64) S and T are formed in FP32 while each FP64 operand
+       is read once (each block value rounded to FP32, a few units of 2^-24);
+       deeper plans form S/T in FP64.  The fringe is FP64.  Relative error
        of order 2^-11 per leaf operand. */
     FMM_PREC_TF32 = 2,
     /* FP32-accurate leaf products on the same TF32 tensor path: each leaf
@@ -78,7 +81,8 @@ typedef enum {
        tf32(x - x_hi), and one product over three K segments sums
        S_hi T_hi + S_hi T_lo + S_lo T_hi with FP32 accumulation (three times
        the TF32 work; the dropped S_lo T_lo is 2^-22 relative).  S/T
-       formation, the W combination and the fringe stay FP64. */
+       formation as for FMM_PREC_TF32 (FP32 with one level, else FP64); the
+       W combination and the fringe stay FP64. */
     FMM_PREC_FP32 = 1
 } fmm_precision;
 
@@ -106,8 +110,8 @@ enum {
        is an integer: the bilinear algorithm is then exact modulo p). */
     FMM_FLAG_LEAF_EMULATION = 1u << 3,
     /* Addition schemes of the level-by-level passes (Section 3.2), for the
-       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 and TF32
-       plans): by default each child S_r, T_r or C block is written once from
+       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 plans, and
+       TF32 plans deeper than one level): by default each child S_r, T_r or C block is written once from
        all its terms ("write-once").  STREAMING reads each parent element
        once and writes it into every child that uses it; PAIRWISE forms each
        child by one pass per term (child = c x, then child += c x).  All three
