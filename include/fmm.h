@@ -110,8 +110,9 @@ enum {
        is an integer: the bilinear algorithm is then exact modulo p). */
     FMM_FLAG_LEAF_EMULATION = 1u << 3,
     /* Addition schemes of the level-by-level passes (Section 3.2), for the
-       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 plans, and
-       TF32 plans deeper than one level): by default each child S_r, T_r or C block is written once from
+       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 plans; for
+       TF32 plans the W levels, and the S/T levels of plans deeper than one
+       level): by default each child S_r, T_r or C block is written once from
        all its terms ("write-once").  STREAMING reads each parent element
        once and writes it into every child that uses it; PAIRWISE forms each
        child by one pass per term (child = c x, then child += c x).  All three
