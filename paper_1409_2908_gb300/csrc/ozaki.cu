@@ -1800,30 +1800,44 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
         if ((be = check()) != cudaSuccess) return be;
         return form(rb0, 1, np, kp, nl1, kl1, rp.v_ptr, rp.vt_code, rp.v_icoef, b + w.lb[0], last1, out_ld1);
     };
+    // band j of A as the host copies it in: child rows [ml1 j / a_bands,
+    // ml1 (j + 1) / a_bands) of every block row, exponents and the fused split
+    auto a_band = [&](int j) -> cudaError_t {
+        cudaError_t ae;
+        if ((ae = cudaStreamWaitEvent(s, pipe->a_ready[j], 0)) != cudaSuccess) return ae;
+        ar0 = ml1 * j / pipe->a_bands;
+        anr = ml1 * (j + 1) / pipe->a_bands - ar0;
+        if (anr > 0) {
+            const int64_t rows = anr * (rp.L ? rp.M : 1);
+            row_exp_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(A, lda, rows, kp, beta, ea, anr, ml1, ar0);
+            if ((ae = check()) != cudaSuccess) return ae;
+            ae = fused_split(0);
+        }
+        ar0 = 0;
+        anr = ml1;
+        return ae;
+    };
+    // With the products made in row bands, each A band is formed just before
+    // the first product band that reads its rows (below), so the products
+    // start once the first band of A is in rather than all of it.
+    const int gb_pipe = (pipe && pipe->band_done && rp.L <= 1 && !fa)
+                            ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(pipe->gemm_bands,
+                                                                                   std::max(1, pipe->bands)), ml1))
+                            : 1;
+    const bool a_deferred = pre && pipe && pipe->a_bands > 0 && fused && !fa && !defer && gb_pipe > 1;
+    int a_next = 0;   // the next A band still to be formed (a_deferred)
     if (!pre) {
         // phase 1: the operands were formed in phase 0
     } else if (pipe && pipe->a_bands > 0) {
-        // the host copies B first, then A in bands of child rows [ml1 j / a_bands,
-        // ml1 (j + 1) / a_bands) of every block row, each with an event: the B
+        // the host copies B first, then A in bands, each with an event: the B
         // side runs while A arrives, and each A band is formed once it is in
-        const int gM = rp.L ? rp.M : 1;
         if ((e = b_side()) != cudaSuccess) return e;
         if (!fused) {
             if ((e = cudaStreamWaitEvent(s, pipe->a_ready[pipe->a_bands - 1], 0)) != cudaSuccess) return e;
             if ((e = a_side()) != cudaSuccess) return e;
-        } else {
-            for (int j = 0; j < pipe->a_bands; ++j) {
-                if ((e = cudaStreamWaitEvent(s, pipe->a_ready[j], 0)) != cudaSuccess) return e;
-                ar0 = ml1 * j / pipe->a_bands;
-                anr = ml1 * (j + 1) / pipe->a_bands - ar0;
-                if (anr == 0) continue;
-                const int64_t rows = anr * gM;
-                row_exp_kernel<<<(unsigned)((rows + 7) / 8), 256, 0, s>>>(A, lda, rows, kp, beta, ea, anr, ml1, ar0);
-                if ((e = check()) != cudaSuccess) return e;
-                if ((e = fused_split(0)) != cudaSuccess) return e;
-            }
-            ar0 = 0;
-            anr = ml1;
+        } else if (!a_deferred) {
+            for (int j = 0; j < pipe->a_bands; ++j)
+                if ((e = a_band(j)) != cudaSuccess) return e;
         }
     } else {
         if ((e = a_side()) != cudaSuccess) return e;
@@ -1905,11 +1919,16 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
     const int gb = (pipe && pipe->band_done && rp.L <= 1 && !fa)
                        ? (int)std::max<int64_t>(1, std::min<int64_t>(std::min(pipe->gemm_bands, bands), mL))
                        : 1;
+    if (a_deferred && gb != gb_pipe) return cudaErrorInvalidValue;   // the two counts are the same rule
     if (gb > 1) {
         const int64_t cld = z_pitch(nL);
         const int sub = std::max(1, bands / gb);
         for (int g = 0; g < gb; ++g) {
             const int64_t R0 = mL * g / gb, NR = mL * (g + 1) / gb - R0;
+            // every A band with rows below R0 + NR formed first (their S' rows
+            // and row exponents are this band's inputs)
+            while (a_deferred && a_next < pipe->a_bands && ml1 * a_next / pipe->a_bands < R0 + NR)
+                if ((e = a_band(a_next++)) != cudaSuccess) return e;
             int8_t *Zb = Z + planes * R0 * cld;
             if ((e = launch_residue_gemm(b + w.la.back(), b + w.lb.back(), Zb, NR, nL, kpadL, planes, nmod, err,
                                          s, launches, R0, mL, rp.tile == FMM_TILE_128x128)) != cudaSuccess)
@@ -1920,8 +1939,12 @@ cudaError_t ozaki_fast(const ResPlan &rp, const double *A, int64_t lda, const do
                 if ((e = w_crt(Zb + (r0 - R0) * cld, NR, r0, nr, mL, nL, cld)) != cudaSuccess) return e;
             }
         }
+        while (a_deferred && a_next < pipe->a_bands)   // (none left: the bands cover all rows)
+            if ((e = a_band(a_next++)) != cudaSuccess) return e;
         return cudaSuccess;
     }
+    while (a_deferred && a_next < pipe->a_bands)
+        if ((e = a_band(a_next++)) != cudaSuccess) return e;
 
     if (fa) {
         if ((e = launch_residue_gemm_fa(rp, (const int8_t *)(b + w.la[0]), mp, kp, b + w.lb[0], Z, mL, kL, nL, kpadL,
