@@ -351,8 +351,9 @@ fmm_status fmm_classical_gemm(const double *A, int64_t lda, const double *B,
  * Work is issued on `stream` and on one internal stream per calling thread
  * and device, which copies B in first and then A in row bands.  For the
  * emulated-FP64 residue path without a fringe, the kernels that read B run
- * while A arrives, each band of A is formed once it is in, and C is copied
- * out in row bands while the following bands are computed.  On return
+ * while A arrives, each band of A is formed once it is in (with the products
+ * made in row bands: just before the first product band that reads it), and
+ * C is copied out in row bands while the following bands are computed.  On return
  * (success or error) nothing the call issued is still in flight.
  */
 fmm_status fmm_host_workspace_size(fmm_plan_t plan, int64_t m, int64_t k,
