@@ -96,3 +96,14 @@ def test_fp32_loguniform():
     C = run(fmm.Plan("strassen_222_7", levels=1, precision="fp32"), A, B)
     ref = oracle.gemm(A, B)
     assert np.all(np.abs(C - ref) <= (1e-5 + 512 * 2.0 ** -22) * (np.abs(A) @ np.abs(B)))
+
+
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
+def test_fused_level_with_non_integer_coefficients(precision):
+    # Strassen with U doubled and W halved (still exact: every product doubles
+    # and its weight halves): the fused level forms S in FP32 with the
+    # coefficient 2, the W pass in FP64 with 1/2; small integers stay exact
+    M, K, N, U, V, W = fmm.algorithm_factors("strassen_222_7")
+    p = fmm.Plan(factors=(M, K, N, 2.0 * U, V, 0.5 * W), levels=1, precision=precision)
+    A, B = synth.operands(258, 260, 262, 66, kind="integer")
+    assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
