@@ -146,3 +146,14 @@ def test_vectorised_bounds_equal_the_scalar_bounds():
     assert vec.keys() == scal.keys()
     for key in vec:
         assert abs(vec[key] - scal[key]) <= 1e-9 * scal[key]
+
+
+def test_beta_rule_matches_the_oracle():
+    # the tuner's closed form (one integer division) against the oracle's
+    # definition of beta, for every moduli count and k across 1..2^40
+    from oracle import ozaki
+    ks = list(range(1, 3000)) + [2 ** e + d for e in range(11, 41) for d in (-1, 0, 1)] + [6912, 8191, 16384, 65536]
+    for n in range(6, 17):
+        assert autotune.MODULI[:n] == tuple(ozaki.moduli(n))
+        for k in ks:
+            assert autotune.beta_for(n, k) == ozaki.beta_bits(n, k), (n, k)

@@ -107,3 +107,22 @@ def test_fused_level_with_non_integer_coefficients(precision):
     p = fmm.Plan(factors=(M, K, N, 2.0 * U, V, 0.5 * W), levels=1, precision=precision)
     A, B = synth.operands(258, 260, 262, 66, kind="integer")
     assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
+
+
+@pytest.mark.parametrize("precision", ["tf32", "fp32"])
+def test_host_entry_point_tf32_family(precision):
+    # fmm_gemm_host with TF32-family leaves (no overlap: the path waits for
+    # all inputs) gives the device entry point's result bit for bit
+    import torch
+    p = fmm.Plan("strassen_222_7", levels=1, precision=precision)
+    m, k, n = 1030, 770, 900
+    A, B = synth.operands(m, k, n, 67)
+    Cd = run(p, A, B)
+    ws = torch.empty(fmm.host_workspace_size(p, m, k, n), dtype=torch.uint8, device="cuda")
+    Ah, Bh = torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory()
+    Ch = torch.zeros((m, n), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        fmm.gemm_host(p, Ah, Bh, Ch, ws)
+        assert np.array_equal(Ch.numpy(), Cd)
+        Ch.zero_()
+    fmm.check_device_error()
