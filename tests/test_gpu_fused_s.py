@@ -64,3 +64,13 @@ def test_fused_s_full_size_sampled():
     rows, cols = synth.sample_indices(m, n, 256, 103)
     got = C[torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()].cpu().numpy()
     assert np.array_equal(got, ozaki.emulated_entries(A, B, rows, cols, 14))
+
+
+@pytest.mark.parametrize("k", [32768, 32832])
+def test_fused_s_k_boundary(k):
+    # k_L up to 32768 takes the fused kernel (its drain sums stay below the
+    # final reduction's shift); beyond, the plan falls back to the ordinary
+    # path: the same integers either way
+    A, B = synth.operands(48, k, 40, 104)
+    fused = run(fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=14, flags=FUSED), A, B)
+    assert np.array_equal(fused, ozaki.emulated_gemm(A, B, 14))

@@ -1,7 +1,7 @@
 """GPU parity of the emulated-FP64 precision variant (tensor-core residue
 products + CRT) against the oracle: exact on integer inputs (the scaled
-operands are not truncated, so the CRT rebuilds A B exactly), within the
-truncation bound and close to the oracle's own emulation on random inputs,
+operands need no rounding, so the CRT rebuilds A B exactly), within the
+rounding bound and equal to the oracle's own emulation on random inputs,
 and combined with the fast recursion."""
 import numpy as np
 import pytest
@@ -156,3 +156,20 @@ def test_emulated_rounding_ties(name, levels):
     assert np.all(np.abs(A).max(axis=1) < 2) and np.all(np.abs(B).max(axis=0) < 2)
     p = fmm.Plan(name, levels=levels, precision="ozaki_bf16", moduli=nmod)
     assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, nmod))
+
+
+def test_longest_supported_k():
+    # k_L = 65536 is the longest k the emulated product takes (the drain's
+    # int32 sums); integer inputs stay exact and random ones equal the
+    # oracle's emulation; one more is refused before anything is enqueued
+    import torch
+    p = fmm.Plan("strassen_222_7", levels=0, precision="ozaki_bf16", moduli=14)
+    A, B = synth.operands(40, 65536, 24, 43, kind="integer")
+    assert np.array_equal(run(p, A, B), oracle.gemm(A, B))
+    A, B = synth.operands(40, 65536, 24, 44)
+    assert np.array_equal(run(p, A, B), ozaki.emulated_gemm(A, B, 14))
+    A = torch.zeros((8, 65537), dtype=torch.float64, device="cuda")
+    B = torch.zeros((65537, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(fmm.FmmError) as ei:
+        fmm.gemm(p, A, B)
+    assert ei.value.status == fmm.FMM_ERR_UNSUPPORTED
