@@ -69,20 +69,22 @@ typedef enum {
        FP64.  The fringe (Section 3.5) is a classical FP64 product. */
     FMM_PREC_OZAKI_BF16 = 3,
     /* Leaf products on the tensor cores in TF32 (operands rounded to a
-       10-bit significand, FP32 accumulation), widened to FP64 for the W
-       combination.  With one recursive level (block grids of 4, 6, 8 or 9
-       blocks, R <= 64) S and T are formed in FP32 while each FP64 operand
-       is read once (each block value rounded to FP32, a few units of 2^-24);
-       deeper plans form S/T in FP64.  The fringe is FP64.  Relative error
-       of order 2^-11 per leaf operand. */
+       10-bit significand, FP32 accumulation).  With one recursive level
+       (block grids of 4, 6, 8 or 9 blocks, R <= 64) S and T are formed in
+       FP32 while each FP64 operand is read once (each block value rounded
+       to FP32), the leaf products are kept in FP32 and the W combination is
+       summed in FP32 into C (a few units of 2^-24 in all; small integers
+       stay exact while every sum stays below 2^24); deeper plans form S/T
+       and W in FP64 from FP64 products.  The fringe is FP64.  Relative
+       error of order 2^-11 per leaf operand. */
     FMM_PREC_TF32 = 2,
     /* FP32-accurate leaf products on the same TF32 tensor path: each leaf
        operand x (taken in FP32) is split into x_hi = tf32(x) and x_lo =
        tf32(x - x_hi), and one product over three K segments sums
        S_hi T_hi + S_hi T_lo + S_lo T_hi with FP32 accumulation (three times
        the TF32 work; the dropped S_lo T_lo is 2^-22 relative).  S/T
-       formation as for FMM_PREC_TF32 (FP32 with one level, else FP64); the
-       W combination and the fringe stay FP64. */
+       formation, the products' precision and the W combination as for
+       FMM_PREC_TF32 (FP32 with one level, else FP64); the fringe is FP64. */
     FMM_PREC_FP32 = 1
 } fmm_precision;
 
@@ -110,9 +112,8 @@ enum {
        is an integer: the bilinear algorithm is then exact modulo p). */
     FMM_FLAG_LEAF_EMULATION = 1u << 3,
     /* Addition schemes of the level-by-level passes (Section 3.2), for the
-       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 plans; for
-       TF32 plans the W levels, and the S/T levels of plans deeper than one
-       level): by default each child S_r, T_r or C block is written once from
+       parts FMM_FLAG_LEVELWISE forms outside the leaf kernel (FP64 plans, and
+       TF32 plans deeper than one level): by default each child S_r, T_r or C block is written once from
        all its terms ("write-once").  STREAMING reads each parent element
        once and writes it into every child that uses it; PAIRWISE forms each
        child by one pass per term (child = c x, then child += c x).  All three

@@ -504,9 +504,9 @@ class Autotuner:
             adds = 0.0
             if L == 1 and M * K in FUSED_BLOCKS and K * N in FUSED_BLOCKS and R <= 64:
                 # the level fused with the conversion: each operand read once,
-                # the leaves' TF32 operands written; W in FP64 from the products
+                # the leaves' TF32 operands written; FP32 products, W in FP32
                 t += (8 * (mp * kp + kp * np_) + 4 * split * leaves * (mL + nL) * kpad) / (HBM_GBS * 1e9)
-                adds = R * mL * nL * 8 * 3
+                adds = R * mL * nL * 4 * 2 + mp * np_ * 8
             else:
                 # FP64 operands to TF32 (8 bytes in, 4 split bytes out per element)
                 t += leaves * (mL * kL + kL * nL) * (8 + 4 * split) / (HBM_GBS * 1e9)

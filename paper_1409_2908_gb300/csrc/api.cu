@@ -508,8 +508,8 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
     if (tf_fused) {
         if ((e = tf32_first_level_products(A, lda, B, ldb, g.mL, g.kL, g.nL, p->M, p->K, p->N, p->R, p->dev.lu_ptr,
                                            p->dev.lu_code, p->dev.lu_coef, p->dev.lv_ptr, p->dev.lv_code,
-                                           p->dev.lv_coef, prod, g.nL, g.mL * g.nL, wsb + wl.oz, s, launches,
-                                           tf32_split(p), p->tile)) != cudaSuccess)
+                                           p->dev.lv_coef, (float *)prod, g.nL, g.mL * g.nL, wsb + wl.oz, s,
+                                           launches, tf32_split(p), p->tile)) != cudaSuccess)
             return cuda_status(e);
     }
     for (int l = 1; l <= p->L && !tf_fused; ++l) {
@@ -532,8 +532,12 @@ fmm_status run_gemm_ozaki(fmm_plan *p, const Geometry &g, const WsLayout &wl, co
         (e = launch_classical(A + g.kp, lda, B + g.kp * ldb, ldb, C, ldc, g.mp, k - g.kp, g.np,
                               FMM_TILE_AUTO, s, launches)) != cudaSuccess)
         return cuda_status(e);
+    // the fused level's FP32 products: W in FP32 straight into C
+    if (tf_fused && (e = tf32_w_level((const float *)prod, g.mL, g.nL, p->M, p->N, p->dev.lw_ptr, p->dev.lw_r,
+                                      p->dev.lw_coef, C, ldc, kfringe ? 1 : 0, s, launches)) != cudaSuccess)
+        return cuda_status(e);
     int64_t lparents = ipow(p->R, p->L - 1);
-    for (int l = p->L; l >= 1; --l) {
+    for (int l = p->L; l >= 1 && !tf_fused; --l) {
         const int64_t ml = g.mp / ipow(p->M, l), nl = g.np / ipow(p->N, l);
         const double *child = (const double *)(wsb + wl.lvP[l - 1]);
         double *parent = l == 1 ? C : (double *)(wsb + wl.lvP[l - 2]);

@@ -203,8 +203,13 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
 cudaError_t tf32_first_level_products(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t mL,
                                       int64_t kL, int64_t nL, int gM, int gK, int gN, int R, const int *u_ptr,
                                       const int *u_code, const double *u_coef, const int *v_ptr,
-                                      const int *v_code, const double *v_coef, double *Out, int64_t ldo,
+                                      const int *v_code, const double *v_coef, float *Out, int64_t ldo,
                                       int64_t os, void *ws, cudaStream_t s, int *launches, int split, int tile);
+// ... and the W combination of that level from its FP32 products, summed in
+// FP32, into C (FP64; added when accumulate).
+cudaError_t tf32_w_level(const float *P, int64_t mL, int64_t nL, int gM, int gN, const int *w_ptr, const int *w_r,
+                         const double *w_coef, double *C, int64_t ldc, int accumulate, cudaStream_t s,
+                         int *launches);
 // residue-space recursion (integer base coefficients only)
 struct ResPlan {
     int M, K, N, R, L;

@@ -70,10 +70,12 @@ __device__ __forceinline__ void tf_tile(int64_t tile, int64_t per_plane, int til
     tm = tm0 + within % gsz;
 }
 
-template <int BN, bool CH>
+// OT: the products' element type (double, or float for the fused one-level
+// path, whose W combination runs in FP32)
+template <int BN, bool CH, typename OT = double>
 __global__ void __launch_bounds__(tf_threads<BN, CH>(), 1)
 tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          double *Out, int64_t m, int64_t n, int kblocks, int chunk_kb, int tiles_m, int tiles_n,
+          OT *Out, int64_t m, int64_t n, int kblocks, int chunk_kb, int tiles_m, int tiles_n,
           int64_t tiles_total, int64_t ldo, int64_t out_stride, int accumulate, int *err,
           unsigned long long wait_ns, int dry) {
     constexpr int DW = tf_dw<BN, CH>(), STAGES = TfCfg<BN>::STAGES;
@@ -182,17 +184,37 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int64_t row = (int64_t)tm * TB_M + lg * 32 + lane;
             const int64_t col0 = (int64_t)tn * BN + ch * CW;
             const int64_t cols = min((int64_t)CW, n - col0);
-            double *out = Out + (int64_t)z * out_stride + row * ldo + col0;
+            OT *out = Out + (int64_t)z * out_stride + row * ldo + col0;
             const bool pairs = ((((uintptr_t)out) & 15) == 0);
-            // 16 accumulated columns from c0 on, widened to FP64 and stored (added)
+            // 16 accumulated columns from c0 on, widened to FP64 (or kept in
+            // FP32) and stored (added)
             auto store16 = [&](int c0, const float *v16) {
                 if (row >= m || c0 >= cols) return;
+                if constexpr (sizeof(OT) == 4) {
+                    if (pairs && c0 + 16 <= cols) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) {
+                            float4 v = make_float4(v16[j], v16[j + 1], v16[j + 2], v16[j + 3]);
+                            float4 *dst = reinterpret_cast<float4 *>(out + c0 + j);
+                            if (accumulate) {
+                                const float4 o = *dst;
+                                v.x += o.x; v.y += o.y; v.z += o.z; v.w += o.w;
+                            }
+                            *dst = v;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < cols) out[c0 + j] = accumulate ? out[c0 + j] + v16[j] : v16[j];
+                    }
+                    return;
+                }
                 if (pairs && c0 + 16 <= cols) {
                     // 16 consecutive columns as eight 16-byte stores
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         double2 v = make_double2((double)v16[j], (double)v16[j + 1]);
-                        double2 *dst = reinterpret_cast<double2 *>(out + c0 + j);
+                        double2 *dst = reinterpret_cast<double2 *>(reinterpret_cast<double *>(out) + c0 + j);
                         if (accumulate) {
                             const double2 o = *dst;
                             v.x += o.x;
@@ -205,7 +227,8 @@ tf32_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     for (int j = 0; j < 16; ++j) {
                         if (c0 + j < cols) {
                             const double v = (double)v16[j];
-                            out[c0 + j] = accumulate ? out[c0 + j] + v : v;
+                            double *od = reinterpret_cast<double *>(out);
+                            od[c0 + j] = accumulate ? od[c0 + j] + v : v;
                         }
                     }
                 }
@@ -537,6 +560,12 @@ cudaError_t tf32_prepare() {
             (e = cudaFuncSetAttribute(tf32_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       tf_smem<128>())) != cudaSuccess ||
             (e = cudaFuncSetAttribute(tf32_gemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<128>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tf32_gemm<256, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<256>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tf32_gemm<128, false, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      tf_smem<128>())) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tf32_gemm<128, true, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       tf_smem<128>())) != cudaSuccess)
             return e;
         configured[dev] = true;
@@ -558,7 +587,8 @@ cudaError_t read_tf32_error(int *flag, bool clear) {
 // The TF32 GEMM over operand planes already in the leaves' layout: fa
 // (leaves x m x split kpad), fb (leaves x n x split kpad), both 256-byte
 // aligned; Out[leaf] (m x n, ldo, leaf stride os) (+)= fa fb^T.
-static cudaError_t tf32_gemm_planes(float *fa, float *fb, double *Out, int64_t ldo, int64_t os, int64_t leaves,
+template <typename OT>
+static cudaError_t tf32_gemm_planes(float *fa, float *fb, OT *Out, int64_t ldo, int64_t os, int64_t leaves,
                                     int64_t m, int64_t n, int64_t kpad, int accumulate, cudaStream_t s,
                                     int *launches, int split, int tile) {
     cudaError_t e;
@@ -581,7 +611,7 @@ static cudaError_t tf32_gemm_planes(float *fa, float *fb, double *Out, int64_t l
     const unsigned ctas = (unsigned)std::min<int64_t>(tiles, sm_count());
     cudaEvent_t t0 = timing_mark(s);
 #define FMM_TF32_GEMM(BN_, CH_)                                                                                \
-    tf32_gemm<BN_, CH_><<<ctas, tf_threads<BN_, CH_>(), tf_smem<BN_>(), s>>>(ta, tb, Out, m, n, kblocks, chunk_kb, \
+    tf32_gemm<BN_, CH_, OT><<<ctas, tf_threads<BN_, CH_>(), tf_smem<BN_>(), s>>>(ta, tb, Out, m, n, kblocks, chunk_kb, \
                                                                           int(tm), int(tn), tiles, ldo, os,    \
                                                                           accumulate, err, wait_limit_ns(), 0)
     if (chunked) FMM_TF32_GEMM(128, true);
@@ -627,13 +657,14 @@ cudaError_t tf32_products(const double *S, int64_t lds, int64_t ss, const double
 
 // One recursive level fused with the conversion: A (ld lda) as an gM x gK
 // grid of mL x kL blocks and B (ld ldb) as gK x gN blocks of kL x nL; the
-// level's term lists (u: S side, v: T side); the R leaf products into Out
-// (mL x nL each, ldo, leaf stride os).  ws: the same operand planes as
-// tf32_products for R leaves of mL x kL x nL.
+// level's term lists (u: S side, v: T side); the R leaf products into Out in
+// FP32 (mL x nL each, ldo, leaf stride os; their W combination is
+// tf32_w_level).  ws: the same operand planes as tf32_products for R leaves
+// of mL x kL x nL.
 cudaError_t tf32_first_level_products(const double *A, int64_t lda, const double *B, int64_t ldb, int64_t mL,
                                       int64_t kL, int64_t nL, int gM, int gK, int gN, int R, const int *u_ptr,
                                       const int *u_code, const double *u_coef, const int *v_ptr,
-                                      const int *v_code, const double *v_coef, double *Out, int64_t ldo,
+                                      const int *v_code, const double *v_coef, float *Out, int64_t ldo,
                                       int64_t os, void *ws, cudaStream_t s, int *launches, int split, int tile) {
     if (split != 1 && split != 3) return cudaErrorInvalidValue;
     if (R > TF_MAX_R || R > 65535) return cudaErrorInvalidValue;
@@ -673,6 +704,52 @@ cudaError_t tf32_first_level_products(const double *A, int64_t lda, const double
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return tf32_gemm_planes(fa, fb, Out, ldo, os, R, mL, nL, kpad, 0, s, launches, split, tile);
+}
+
+// The W combination of one level from FP32 leaf products (TF32-family leaves,
+// the fused path above): C block q = (a, c) of the gM x gN grid,
+// C_q (+)= sum_t w_t P[r_t], the sum in FP32 (a few units of 2^-24 relative,
+// below the products' own 2^-11 or 2^-22) and stored in FP64.  Thread: four
+// consecutive columns of one row of one block.
+__global__ void __launch_bounds__(256) tf32_w_kernel(const float *P, int64_t mL, int64_t nL, int gN, int MN,
+                                                     const int *w_ptr, const int *w_r, const double *w_coef,
+                                                     double *C, int64_t ldc, int accumulate) {
+    const int64_t groups = (nL + 3) / 4;
+    const int64_t pos = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (pos >= (int64_t)MN * mL * groups) return;
+    const int64_t j0 = (pos % groups) * 4;
+    const int64_t rest = pos / groups;
+    const int64_t i = rest % mL;
+    const int q = int(rest / mL);
+    float a[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int t = __ldg(w_ptr + q); t < __ldg(w_ptr + q + 1); ++t) {
+        const float w = (float)__ldg(w_coef + t);
+        const float *src = P + ((int64_t)__ldg(w_r + t) * mL + i) * nL + j0;
+        if (j0 + 4 <= nL && ((uintptr_t)src & 15) == 0) {
+            const float4 v = *reinterpret_cast<const float4 *>(src);
+            a[0] = fmaf(w, v.x, a[0]); a[1] = fmaf(w, v.y, a[1]); a[2] = fmaf(w, v.z, a[2]); a[3] = fmaf(w, v.w, a[3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (j0 + e < nL) a[e] = fmaf(w, src[e], a[e]);
+        }
+    }
+    double *out = C + ((int64_t)(q / gN) * mL + i) * ldc + (int64_t)(q % gN) * nL + j0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (j0 + e < nL) out[e] = accumulate ? out[e] + (double)a[e] : (double)a[e];
+}
+
+cudaError_t tf32_w_level(const float *P, int64_t mL, int64_t nL, int gM, int gN, const int *w_ptr, const int *w_r,
+                         const double *w_coef, double *C, int64_t ldc, int accumulate, cudaStream_t s,
+                         int *launches) {
+    const int MN = gM * gN;
+    const int64_t threads = (int64_t)MN * mL * ((nL + 3) / 4);
+    if (threads <= 0) return cudaSuccess;
+    tf32_w_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(P, mL, nL, gN, MN, w_ptr, w_r, w_coef, C, ldc,
+                                                                    accumulate);
+    ++*launches;
+    return cudaGetLastError();
 }
 
 // The timeout path of the TF32 GEMM (see residue_gemm_timeout_probe): one
