@@ -707,11 +707,19 @@ def main():
     if rank == 0:
         base_rec, rows, Cs = cpu_baseline(A, B, 2.0 if args.quick else args.cpu_budget)
 
-    def rel_err_rows(Cdev):
+    # e_max's scale: max|A| max|B| k (the normwise error of a k-term dot product)
+    emax_scale = float(np.abs(A).max()) * float(np.abs(B).max()) * k if rank == 0 else 0.0
+
+    def rel_err_rows(Cdev, both=False):
+        """e_F on the sampled rows; with both, also e_max = max|C^ - C| /
+        (max|A| max|B| k) on the same rows."""
         if rows is None:
-            return None
+            return (None, None) if both else None
         got = Cdev[torch.from_numpy(rows).cuda()].cpu().numpy()
-        return float(np.linalg.norm(got - Cs) / np.linalg.norm(Cs))
+        ef = float(np.linalg.norm(got - Cs) / np.linalg.norm(Cs))
+        if not both:
+            return ef
+        return ef, (float(np.abs(got - Cs).max()) / emax_scale if emax_scale > 0 else 0.0)
 
     # candidates (algorithm files that exist), plus the classical comparator
     schemes = {"fused": fmm.FLAG_FUSED_ST | fmm.FLAG_FUSED_W, "wo_st": fmm.FLAG_FUSED_W,
@@ -762,21 +770,23 @@ def main():
         # a second-long FP64 product is timed once; the fast ones, median of three
         reps = 1 if prec == "fp64" else 3
         ms = statistics.median(time_steps(torch, f, 1, stream) for _ in range(reps))
-        err = rel_err_rows(Cd)
+        err, emax = rel_err_rows(Cd, True)
         label = f"{a} L{L} {sc}" + ("" if prec == "fp64" else f" {prec}") + (f" x{nmod}" if nmod else "")
         p.moduli = nmod
         plans[label] = p
         results.append({"plan": label, "algorithm": a, "levels": L, "precision": prec, "moduli": nmod,
-                        "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err, "workspace_bytes": wsz})
+                        "tflops": flops / ms / 1e9, "ms": ms, "rel_err_F": err, "rel_err_max": emax,
+                        "workspace_bytes": wsz})
         del f, wsb
     fc = (lambda: fmm.classical_gemm(Ad, Bd, C=Cd, stream=stream))
     if not args.no_classical:
         fc()
         torch.cuda.synchronize()
         ms_c1 = time_steps(torch, fc, 1, stream)
-        err_c = rel_err_rows(Cd)
+        err_c, emax_c = rel_err_rows(Cd, True)
         results.append({"plan": "classical", "algorithm": None, "levels": 0, "precision": "fp64",
-                        "moduli": None, "tflops": flops / ms_c1 / 1e9, "ms": ms_c1, "rel_err_F": err_c})
+                        "moduli": None, "tflops": flops / ms_c1 / 1e9, "ms": ms_c1, "rel_err_F": err_c,
+                        "rel_err_max": emax_c})
     else:
         err_c = None
 
@@ -840,7 +850,7 @@ def main():
     ms = max_over_ranks(torch, ws, ms)
     ms_step = ms / args.steps
     value = ws * flops / ms_step / 1e9
-    err = rel_err_rows(Cd)
+    err, emax = rel_err_rows(Cd, True)
     region_s = ms / 1e3
     del wsb
 
@@ -888,7 +898,9 @@ def main():
                        "l2": "inputs larger than L2 (A, B, C 512 MiB+ each), no flush",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "accuracy_gate": {"rule": gate_rule, "value": gate},
-            "rel_err_F": err, "rel_err_note": "e_F over the cpu_baseline's sampled rows vs the FP64 oracle",
+            "rel_err_F": err, "rel_err_max": emax,
+            "rel_err_note": ("e_F = |C^ - C|_F / |C|_F and e_max = max|C^ - C| / (max|A| max|B| k) over the "
+                             "cpu_baseline's sampled rows vs the FP64 oracle"),
             "classical_same_accuracy": (
                 {"plan": classical_same["plan"], "value": flops / classical_same["ms"] / 1e9,
                  "ms": classical_same["ms"], "rel_err_F": classical_same["rel_err_F"],
