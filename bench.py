@@ -918,7 +918,7 @@ def main():
             "cublas_dgemm": dgemm,
             "plans": results,
             "roofline": roof,
-            "cpu_baseline": base_rec,
+            "cpu_baseline": base_rec if ws == 1 else None,   # reported at N = 1 only
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
