@@ -586,7 +586,8 @@ cudaError_t read_tf32_error(int *flag, bool clear) {
 
 // The TF32 GEMM over operand planes already in the leaves' layout: fa
 // (leaves x m x split kpad), fb (leaves x n x split kpad), both 256-byte
-// aligned; Out[leaf] (m x n, ldo, leaf stride os) (+)= fa fb^T.
+// aligned; Out[leaf] (m x n, ldo, leaf stride os) (+)= fa fb^T, stored as OT
+// (double, or float for the fused one-level path).
 template <typename OT>
 static cudaError_t tf32_gemm_planes(float *fa, float *fb, OT *Out, int64_t ldo, int64_t os, int64_t leaves,
                                     int64_t m, int64_t n, int64_t kpad, int accumulate, cudaStream_t s,
