@@ -89,6 +89,9 @@ def scheme_desc(flags, fmm, precision="fp64", levels=1):
              "S' and T' as bf16 operand planes in HBM")
         return ("residue space: exponents, then scaling, residues and the first level in one pass per operand; "
                 + s + "; W level 1 fused with the CRT" + ("; later levels on int8 residues" if levels > 1 else ""))
+    if precision in ("tf32", "fp32") and levels == 1:
+        return ("S and T formed in FP32 while each FP64 operand is read once (the leaves' TF32 operand planes); "
+                "FP32 leaf products; W summed in FP32 into C (base cases with 4, 6, 8 or 9 blocks per operand)")
     lw = "level by level" if flags & fmm.FLAG_LEVELWISE else "from unrolled chains"
     st = ("S/T fused into operand staging" if flags & fmm.FLAG_FUSED_ST
           else f"S/T written once to workspace ({lw})")
